@@ -1,0 +1,300 @@
+"""Benchmark: LTS octant-node updates/s on one GB300 (wave equation, levels 4..9).
+
+A step is one LTS macro step (Alg. 2): 2^(l_max - l_min) = 32 substeps of the
+finest timestep, each running the RK stages of the active levels (Fig. blk_loop),
+followed by the shared-node reconcile.  The metric counts one node of one
+octant advanced one full RK step on its own level (eq. w_nuts times 343 nodes).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the CPU oracle on a bounded sample of the same workload
+(the paper has no GPU implementation; the oracle is the reference arm).  Under
+torchrun (N > 1) every rank runs an independent replica (the solve is not sharded
+across GPUs) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LTS octant-node updates/s"
+UNIT = "node-updates/s"
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x flops/FMA x max clock
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def oracle_sample(w, threads=None):
+    """Times the oracle on one LTS substep of the workload in which every level is
+    active (substep 0), after a warm call that builds its padding maps.  Returns
+    (node-updates/s, seconds, octants, threads)."""
+    import oracle
+    if threads:
+        oracle.set_threads(threads)
+    tree = oracle.Tree.build(w["spec"])
+    sol = oracle.Solver(tree, w["spec"], w["prob"])
+    sol.set_initial(0.0)
+    sol.lts_substeps(1)              # warm: padding maps are built on first use
+    sol.set_initial(0.0)
+    t0 = time.perf_counter()
+    sol.lts_substeps(1)
+    dt = time.perf_counter() - t0
+    n = len(tree)
+    return n * 343 / dt, dt, n
+
+
+def host_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, w, world, rank, pg):
+    if rank != 0:
+        return
+    threads = host_threads()
+    vals, times = [], []
+    for _ in range(args.warmup):
+        oracle_sample(w, threads)
+    for _ in range(args.steps):
+        v, dt, n = oracle_sample(w, threads)
+        vals.append(v)
+        times.append(dt)
+    value = len(vals) / sum(1.0 / v for v in vals)
+    sample = ("one LTS substep with every level active (substep 0: %d octants x 343 nodes, one RK4 step each) "
+              "of the wave workload, per step" % n)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["name"], "octants": n, "levels": "4..9", "fields": 2, "rk": 4,
+                   "parallelism": "replicas", "l2": "state arrays (847 MB each) larger than L2"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lts", choices=["lts", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--gts", action="store_true", help="also time GTS over the same physical time")
+    args = ap.parse_args()
+
+    from paper_2011_10570_gb300 import workloads
+    w = workloads.wave_shell()
+    world, rank, local, pg = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, w, world, rank, pg)
+        if pg:
+            pg.barrier()
+            pg.destroy_process_group()
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_2011_10570_gb300 import build, ltsoct
+    build.build()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    tree = ltsoct.Octree(w["spec"])
+    plan = ltsoct.Plan(tree, w["prob"], stream=stream)
+    st = plan.stats()
+    n = st["n_octants"]
+    L = st["l_max"] - st["l_min"]
+    nsub = 2 ** L
+    work_nodes = st["lts_work_per_macro"] * 343          # node-updates per macro step
+    plan.set_initial(0.0)
+    for _ in range(args.warmup):
+        plan.run_substeps(nsub)
+    torch.cuda.synchronize()
+
+    # device-resident timed region (CUDA events on the plan's stream)
+    plan.set_profiling(True)
+    plan.kernel_stats(reset=True)
+    launches0 = plan.stats()["kernel_launches"]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            plan.run_substeps(nsub)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = plan.stats()["kernel_launches"] - launches0
+    ks = plan.kernel_stats(reset=True)
+    plan.set_profiling(False)
+    if pg:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps * work_nodes / (ms / 1e3)
+
+    # end to end through the C ABI with host buffers: H2D of the state, one macro
+    # step, D2H of the result, every step
+    host_t = torch.empty((st["nf"], n, 343), dtype=torch.float64, pin_memory=True)
+    out_t = torch.empty((st["nf"], n, 343), dtype=torch.float64, pin_memory=True)
+    host, out = host_t.numpy(), out_t.numpy()
+    plan.get_state(host)
+    e2e_steps = max(1, args.steps)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan.set_state(host, 0.0)
+        plan.run_substeps(nsub)
+        plan.get_state(out)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if pg:
+        t = torch.tensor([e2e_s], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * e2e_steps * work_nodes / e2e_s
+    state_bytes = host.nbytes
+
+    # GTS over the same physical time (2^L global steps per macro step)
+    gts = None
+    if args.gts:
+        plan.set_initial(0.0)
+        plan.gts_steps(2)
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        plan.gts_steps(nsub)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        gms = g0.elapsed_time(g1)
+        gts = {"ms_per_macro_step": gms, "lts_ms_per_macro_step": ms / args.steps,
+               "lts_speedup_measured": gms / (ms / args.steps), "lts_speedup_model": st["model_speedup"]}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["name"], "octants": n, "levels": "%d..%d" % (st["l_min"], st["l_max"]),
+                   "fields": st["nf"], "rk": 4, "substeps_per_step": nsub, "parallelism": "replicas",
+                   "l2": "inputs larger than L2 (state arrays 847 MB each, 6 resident)"},
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+                "d2h_bytes_per_step": state_bytes},
+        "clocks": clk.summary(),
+        "lts_model_speedup": st["model_speedup"],
+    }
+    if ks["launches"]:
+        avg_ms = ks["ms"] / ks["launches"]
+        flops_per_launch = ks["flops"] / ks["launches"]
+        achieved = flops_per_launch / (avg_ms / 1e3) / 1e12
+        line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                            "kernel": "stage_kernel<2>", "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 x 2.07 GHz",
+                            "hbm_gbs_algorithmic": ks["bytes"] / (ks["ms"] / 1e3) / 1e9,
+                            "hbm_peak_gbs": measured_peaks().get("hbm_gbs"),
+                            "stage_share_of_step": ks["ms"] / ms}
+    if gts:
+        line["gts"] = gts
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, dt, nn = oracle_sample(w, host_threads())
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": host_threads(), "kind": "oracle",
+                                "sample": "one LTS substep with every level active (%d octants, one RK4 step each), "
+                                          "%.1f s" % (nn, dt)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,187 @@
+/*
+ * ltsoct.h -- C ABI of libltsoct: local timestepping (LTS) for explicit RK solves
+ * on 2:1-balanced, Morton-ordered octrees, on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Fernando & Sundar, "Scalable Local Timestepping on Octree Grids"
+ * (arXiv 2011.10570).  The hot path is the per-level LTS substep: unzip every
+ * active octant into a padded 13^3 block (Sec. 3.3, Fig. unzip) with ghost values
+ * from same-level, coarser (Lagrange interpolation) and finer (injection)
+ * neighbours, corrected in time by the stage relations of eqs. rk_crrection,
+ * fc_1 and fc_2; evaluate the finite-difference right-hand side; apply the RK
+ * stage update (eq. rk_schemes); zip back (Sec. 3.3, Fig. dg_to_cg).
+ *
+ * Conventions used by every entry point
+ *  - Octants are stored in "level order": ascending (level, Morton key).
+ *  - Node layout: 7 nodes per axis (element order 6); node (i,j,k) has index
+ *    i + 7 j + 49 k.  A state array is [nf][N][343] FP64, nf = 1 (advection: u)
+ *    or 2 (wave: chi, phi), in level order ("DG" layout: every octant keeps
+ *    its own copy of shared face nodes, Fig. dg_to_cg).
+ *  - Lattice: anchors are integers in [0, 2^20)^3; an octant of level l has edge
+ *    2^(20-l).  Physical x = lo + (hi - lo) * X / 2^20 on every axis.
+ *  - Every call returns an lts_status.  No call aborts or throws across the ABI.
+ *    On failure, lts_last_error() returns a thread-local message.
+ *  - Work is enqueued on the plan's CUDA stream (lts_problem.stream, NULL = the
+ *    legacy default stream).  Calls that return host data synchronise it.
+ *  - Device memory is allocated through lts_problem.dev_alloc/dev_free when given
+ *    (e.g. PyTorch's caching allocator), else with cudaMalloc/cudaFree.  The
+ *    library owns all device state; the caller owns every buffer it passes in.
+ *  - A plan is not thread-safe: one host thread drives it at a time.
+ */
+#ifndef LTSOCT_H
+#define LTSOCT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LTS_OK = 0,
+  LTS_EINVAL = 1,      /* invalid argument (size, level range, time not on the step grid, ...) */
+  LTS_ENOMEM = 2,      /* host or device allocation failed */
+  LTS_ECUDA = 3,       /* a CUDA runtime call failed (message in lts_last_error) */
+  LTS_ETIMEOUT = 4,    /* a bounded device-side wait gave up */
+  LTS_EUNBALANCED = 5, /* octree violates the 2:1 balance the method needs */
+  LTS_ESTATE = 6,      /* call not valid in the plan's current state */
+  LTS_EINTERNAL = 7    /* a device-side consistency check failed */
+} lts_status;
+
+typedef struct lts_octree lts_octree;
+typedef struct lts_plan lts_plan;
+
+/* Refinement (Sec. 3.2.2).  The paper refines by a wavelet criterion; this
+ * library uses an integer geometric predicate so that trees are reproducible
+ * bit for bit: an octant of level l < l_max is split if
+ *   kind 0: its closed box comes within `radius` of any of the n_centers points;
+ *   kind 1: its closed box meets the shell radius-band <= |x - centers[0]| <= radius+band.
+ * Octants of level < l_min are always split.  Centers and radii are mapped to
+ * lattice units as llround((c - lo)/(hi - lo) * 2^20) and floor/ceil of
+ * (r/(hi - lo) * 2^20)^2; the tests are exact int64 comparisons. */
+typedef struct {
+  double lo, hi;
+  int l_min, l_max; /* 0 <= l_min <= l_max <= 18 */
+  int kind;
+  int n_centers;    /* 1..8 */
+  double centers[8][3];
+  double radius, band;
+} lts_refine_spec;
+
+enum { LTS_PDE_ADVECTION = 0, LTS_PDE_WAVE = 1 };
+enum { LTS_BC_EXACT = 0, LTS_BC_RADIATIVE = 1 };
+enum {
+  LTS_IC_ADV_GAUSS = 0,   /* ic_params[0..2] x0, [3] w: u = exp(-|x - x0 - a t|^2 / w) */
+  LTS_IC_WAVE_SHELL = 2,  /* [0] R, [1] w, [2] amp, [3] nmodes (<= 4), [4] kscale, [5+5m..] eps, kx, ky, kz, theta:
+                             chi = exp(-(r-R)^2/w) (1 + amp sum eps sin(kscale k.x + theta)), phi = 0 */
+  LTS_IC_WAVE_PLANAR = 3  /* [0] s0, [1] w: chi = (f(x-t) + f(x+t))/2, f(s) = exp(-(s-s0)^2/w), phi = chi_t */
+};
+
+/* The problem (Sec. 4.2).  pde 0: u_t + adv . grad u = 0.  pde 1: chi_t = phi,
+ * phi_t = lap chi (eqs. chi, phi with c = 0).  Both add Kreiss-Oliger dissipation
+ * (ko_sigma / (64 h)) sum_d delta_d^6.  bc 0 (exact): exterior ghosts are the
+ * RK stage values of the closed-form solution named by `ic`; bc 1 (radiative,
+ * wave only): exterior ghosts by cubic extrapolation and, at nodes on the domain
+ * boundary, df/dt = -(x/r) . grad f - k f / r with k = 1 for chi, 2 for phi. */
+typedef struct {
+  int pde;
+  double adv[3];
+  double cfl;          /* dt_finest = cfl * h_finest, h = node spacing (Sec. 3.4 CFL) */
+  double ko_sigma;
+  int rk;              /* 4: classical RK4; 3: SSPRK3 */
+  int bc;
+  int ic;
+  double ic_params[32];
+  void* stream;        /* cudaStream_t; NULL = default stream */
+  void* (*dev_alloc)(size_t bytes, void* ctx);  /* optional device allocator */
+  void (*dev_free)(void* ptr, void* ctx);
+  void* alloc_ctx;
+} lts_problem;
+
+typedef struct {
+  int64_t n_octants;
+  int nf, p;                    /* fields, RK stages */
+  int l_min, l_max;             /* levels present in the tree */
+  int64_t octants_per_level[32];
+  double dt_finest;             /* dt of the finest level */
+  double dt_coarsest;           /* one LTS macro step = 2^(l_max - l_min) * dt_finest */
+  double time;                  /* current time of the plan (synchronised time + substeps) */
+  int64_t substep;              /* substep index within the current macro step */
+  double model_speedup;         /* eqs. w_nuts, w_uts, invS: W_gts / W_lts */
+  double lts_work_per_macro;    /* octant-steps of one macro step (eq. w_nuts) */
+  double gts_work_per_macro;    /* octant-steps of 2^(l_max-l_min) global steps (eq. w_uts) */
+  size_t device_bytes;          /* device memory held by the plan */
+  int64_t kernel_launches;      /* kernels the plan has launched so far */
+} lts_stats;
+
+/* ---- octree: Sec. 3.2.2 construction, Sec. 3.2.3 2:1 balance -------------- */
+/* Refine from the root by the predicate, balance 2:1 across faces, edges and
+ * corners (the unique coarsest balanced refinement), sort in level order.
+ * Host-side; *out is owned by the caller and freed with octree_destroy. */
+lts_status octree_build(const lts_refine_spec* spec, lts_octree** out);
+lts_status octree_size(const lts_octree* tree, int64_t* n);
+/* Copies the leaves in level order into caller host buffers xyz[3n], level[n]. */
+lts_status octree_export(const lts_octree* tree, int32_t* xyz, int32_t* level);
+void octree_destroy(lts_octree* tree);
+
+/* ---- plan: Sec. 3.2.4 meshing (o2o), Sec. 3.6 per-level schedule ---------- */
+/* Builds the neighbour tables, the time-correction tables of eqs. fc_1 / fc_2,
+ * uploads them and allocates the state (u double-buffered per level, RK stages).
+ * The tree must outlive nothing: the plan copies what it needs. */
+lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_plan** out);
+void lts_plan_destroy(lts_plan* plan);
+lts_status lts_plan_stats(const lts_plan* plan, lts_stats* out);
+
+/* ---- state ---------------------------------------------------------------- */
+/* Initial data of prob->ic at every node at time t0 (device kernel). */
+lts_status lts_set_initial(lts_plan* plan, double t0);
+/* u: [nf][N][343] FP64, host memory (on_device = 0) or device memory (1). */
+lts_status lts_set_state(lts_plan* plan, const double* u, double t0, int on_device);
+/* Copies the current DG state; synchronises the stream.  t (optional) gets the time. */
+lts_status lts_get_state(lts_plan* plan, double* u, double* t, int on_device);
+/* RK stage j (0-based) of every octant's most recent step, [nf][N][343]. */
+lts_status lts_get_stage(lts_plan* plan, int j, double* k, int on_device);
+
+/* ---- time stepping ------------------------------------------------------------ */
+/* Alg. 2 substeps of dt_finest (Fig. blk_loop): in substep n of a macro step the
+ * levels l >= l*(n) step, l* the smallest l with n % 2^(l_max - l) == 0.  After
+ * the last substep of a macro step the duplicated DG nodes are reconciled
+ * (shared-node sync).  Asynchronous. */
+lts_status lts_run_substeps(lts_plan* plan, int64_t n);
+/* LTS to t_end: (t_end - time) must be a whole number of macro steps (to 1e-9
+ * relative), and the plan must be at a macro-step boundary; else LTS_EINVAL. */
+lts_status lts_advance(lts_plan* plan, double t_end);
+/* Alg. 1: n global steps of dt_finest with the shared-node sync of every stage. */
+lts_status gts_steps(lts_plan* plan, int64_t n);
+/* GTS to t_end: (t_end - time) must be a whole number of dt_finest. */
+lts_status gts_advance(lts_plan* plan, double t_end);
+
+/* ---- maps for parity checks ---------------------------------------------------- */
+/* o2o (Sec. 3.2.4): out[N][27][8] int32 host buffer; direction d = (dx+1) +
+ * 3(dy+1) + 9(dz+1); entry 0 = the leaf covering the same-size box in direction d
+ * (same size or coarser), or -2 if the box lies outside the domain; if the box is
+ * split, the 8 entries are its children in Morton child order (-1: not a leaf). */
+lts_status lts_export_o2o(const lts_plan* plan, int32_t* out);
+/* Padding sources computed by the device resolver the stage kernel uses, for the
+ * n octants listed in octs (host int32): src[n][2197] (leaf index, -1 outside the
+ * domain) and r[n][2197][3] (half-node coordinates in the source). */
+lts_status lts_export_pad_map(lts_plan* plan, const int32_t* octs, int64_t n, int32_t* src, int32_t* r);
+/* Same for the 343 nodes of each listed octant (the shared-node owners). */
+lts_status lts_export_node_map(lts_plan* plan, const int32_t* octs, int64_t n, int32_t* src, int32_t* r);
+
+/* ---- measurement ------------------------------------------------------------------- */
+/* When on, every stage-kernel launch is bracketed by CUDA events on the plan's
+ * stream; lts_kernel_stats synchronises and reports, since the last reset, the
+ * number of stage launches, their summed device time (ms), and the algorithmic
+ * FP64 flops and HBM bytes of those launches (per-node figures of the design notes). */
+lts_status lts_set_profiling(lts_plan* plan, int on);
+lts_status lts_kernel_stats(lts_plan* plan, int64_t* launches, double* ms, double* flops, double* bytes,
+                            int64_t* node_stages, int reset);
+
+const char* lts_strerror(lts_status s);
+const char* lts_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,672 @@
+// C ABI of libltsoct (include/ltsoct.h): plan lifecycle, the LTS substep
+// schedule (Alg. 2, Fig. blk_loop), GTS (Alg. 1), the shared-node sync and the
+// parity exports.  All device work is enqueued on the plan's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "ltsoct_internal.h"
+
+namespace ltsoct {
+const char* last_error_cstr();
+}
+
+using ltsoct::kNV;
+
+// Algorithmic work of one node-stage (FMA = 2 flops), counted from the formulas of
+// the stage kernel: RHS stencils + own stage input + the share of the RK update.
+static double flops_per_node_stage(int pde) { return pde == LTS_PDE_ADVECTION ? 49.0 : 65.0; }
+// Algorithmic HBM bytes of one node-stage per field: own u (8), stage inputs
+// (0.75 K reads), the stage write (8), and the update's share (K reads + u write).
+static double bytes_per_node_stage(int nf) { return 30.0 * nf; }
+
+struct lts_plan {
+  lts_problem prob;
+  lts_refine_spec spec;
+  ltsoct::Tables tab;
+  int scheme = 0;
+  int64_t N = 0;
+  int nf = 1, p = 4, lmin = 0, lmax = 0;
+  int64_t count[33] = {};
+  int64_t off[34] = {};
+  double dt_f = 0.0, t_macro = 0.0;
+  int64_t n_sub = 0;
+  unsigned cur_mask = 0;
+  std::vector<ltsoct::Oct> octs;
+  ltsoct::Neighbours nb;
+  std::vector<int32_t> hang;           // octants with hanging nodes, level order
+  int64_t hang_off[34] = {};           // per level ranges in hang
+  int4* d_oct = nullptr;
+  int* d_nbr = nullptr;
+  int* d_fine = nullptr;
+  int* d_hang = nullptr;
+  double* d_u[2] = {nullptr, nullptr};
+  double* d_K = nullptr;
+  int* d_err = nullptr;
+  int64_t launches = 0;               // every kernel launched by the plan
+  size_t bytes = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<void*> allocations;
+  bool profiling = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+  std::vector<int64_t> event_nodes;
+  int64_t prof_launches = 0, prof_node_stages = 0;
+  double prof_ms = 0.0;
+  double w_lts = 0.0, w_gts = 0.0;
+};
+
+namespace {
+
+lts_status fail(lts_status s, const std::string& msg) {
+  ltsoct::set_last_error(msg);
+  return s;
+}
+
+lts_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(LTS_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, where)                       \
+  do {                                        \
+    cudaError_t e_ = (call);                  \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+void* dev_alloc(lts_plan* P, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* ptr = nullptr;
+  if (P->prob.dev_alloc) {
+    ptr = P->prob.dev_alloc(bytes, P->prob.alloc_ctx);
+  } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    ptr = nullptr;
+  }
+  if (ptr) {
+    P->allocations.push_back(ptr);
+    P->bytes += bytes;
+  }
+  return ptr;
+}
+
+void release(lts_plan* P) {
+  if (P->stream) cudaStreamSynchronize(P->stream);
+  for (auto& ev : P->events) {
+    cudaEventDestroy(ev.first);
+    cudaEventDestroy(ev.second);
+  }
+  P->events.clear();
+  for (void* ptr : P->allocations) {
+    if (P->prob.dev_free)
+      P->prob.dev_free(ptr, P->prob.alloc_ctx);
+    else
+      cudaFree(ptr);
+  }
+  P->allocations.clear();
+}
+
+ltsoct::DevTree dev_tree(const lts_plan* P) {
+  return ltsoct::DevTree{P->d_oct, P->d_nbr, P->d_fine, int(P->N)};
+}
+
+int cur_of(const lts_plan* P, int l) { return (P->cur_mask >> l) & 1; }
+
+// in-place shared-node sync of the arrays vb (level l uses vb[(sel >> l) & 1])
+lts_status sync_fields(lts_plan* P, double* vb0, double* vb1, unsigned sel) {
+  ltsoct::SyncArgs a{};
+  a.tree = dev_tree(P);
+  a.vb[0] = vb0;
+  a.vb[1] = vb1;
+  a.sel_mask = sel;
+  a.fstride = P->N * kNV;
+  a.nf = P->nf;
+  a.list = nullptr;
+  a.count = int(P->N);
+  a.err = P->d_err;
+  CK(ltsoct::launch_sync_zip(a, P->stream), "sync (zip)");
+  P->launches++;
+  for (int l = P->lmin + 1; l <= P->lmax; ++l) {
+    const int64_t n = P->hang_off[l + 1] - P->hang_off[l];
+    if (!n) continue;
+    a.list = P->d_hang + P->hang_off[l];
+    a.count = int(n);
+    CK(ltsoct::launch_sync_hanging(a, P->stream), "sync (hanging nodes)");
+    P->launches++;
+  }
+  return LTS_OK;
+}
+
+ltsoct::StageArgs stage_args(const lts_plan* P, int stage, int first, int lstar, int gts) {
+  ltsoct::StageArgs a{};
+  a.tree = dev_tree(P);
+  a.u[0] = P->d_u[0];
+  a.u[1] = P->d_u[1];
+  a.K = P->d_K;
+  a.fstride = P->N * kNV;
+  a.nf = P->nf;
+  a.p = P->p;
+  a.scheme = P->scheme;
+  a.stage = stage;
+  a.first = first;
+  a.lstar = lstar;
+  a.lmax = P->lmax;
+  a.cur_mask = P->cur_mask;
+  a.gts = gts;
+  a.write_update = gts ? 0 : 1;
+  a.dt_f = P->dt_f;
+  a.t_b = P->t_macro + double(P->n_sub) * P->dt_f;
+  a.lo = P->spec.lo;
+  a.ext = P->spec.hi - P->spec.lo;
+  a.pde = P->prob.pde;
+  a.bc = P->prob.bc;
+  a.ic = P->prob.ic;
+  for (int d = 0; d < 3; ++d) a.adv[d] = P->prob.adv[d];
+  a.ko_sigma = P->prob.ko_sigma;
+  for (int i = 0; i < 32; ++i) a.icp.v[i] = P->prob.ic_params[i];
+  a.err = P->d_err;
+  return a;
+}
+
+lts_status launch_stage_timed(lts_plan* P, const ltsoct::StageArgs& a, int count) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (P->profiling) {
+    CK(cudaEventCreate(&e0), "cudaEventCreate");
+    CK(cudaEventCreate(&e1), "cudaEventCreate");
+    CK(cudaEventRecord(e0, P->stream), "cudaEventRecord");
+  }
+  CK(ltsoct::launch_stage(a, count, P->stream), "stage kernel launch");
+  if (count > 0) P->launches++;
+  if (P->profiling) {
+    CK(cudaEventRecord(e1, P->stream), "cudaEventRecord");
+    P->events.emplace_back(e0, e1);
+    P->event_nodes.push_back(int64_t(count) * kNV);
+  }
+  return LTS_OK;
+}
+
+int active_level(const lts_plan* P, int64_t n) {
+  for (int l = P->lmin; l <= P->lmax; ++l)
+    if (n % (int64_t(1) << (P->lmax - l)) == 0) return l;
+  return P->lmax;
+}
+
+lts_status lts_substep(lts_plan* P) {
+  const int lstar = active_level(P, P->n_sub);
+  const int first = int(P->off[lstar]);
+  const int count = int(P->N - first);
+  for (int s = 0; s < P->p; ++s) {
+    lts_status st = launch_stage_timed(P, stage_args(P, s, first, lstar, 0), count);
+    if (st != LTS_OK) return st;
+  }
+  // the active levels completed a step: their state now lives in the other buffer
+  for (int l = lstar; l <= P->lmax; ++l) P->cur_mask ^= 1u << l;
+  P->n_sub++;
+  if (P->n_sub == (int64_t(1) << (P->lmax - P->lmin))) {
+    lts_status st = sync_fields(P, P->d_u[0], P->d_u[1], P->cur_mask);
+    if (st != LTS_OK) return st;
+    P->t_macro += double(P->n_sub) * P->dt_f;
+    P->n_sub = 0;
+  }
+  return LTS_OK;
+}
+
+lts_status gts_step(lts_plan* P) {
+  const long long kstride = (long long)P->nf * P->N * kNV;
+  for (int s = 0; s < P->p; ++s) {
+    lts_status st = launch_stage_timed(P, stage_args(P, s, 0, P->lmin, 1), int(P->N));
+    if (st != LTS_OK) return st;
+    double* Ks = P->d_K + s * kstride;
+    st = sync_fields(P, Ks, Ks, 0u);
+    if (st != LTS_OK) return st;
+  }
+  ltsoct::UpdateArgs ua{};
+  ua.u[0] = P->d_u[0];
+  ua.u[1] = P->d_u[1];
+  ua.K = P->d_K;
+  ua.fstride = P->N * kNV;
+  ua.nf = P->nf;
+  ua.p = P->p;
+  ua.scheme = P->scheme;
+  ua.n = int(P->N);
+  ua.oct = P->d_oct;
+  ua.cur_mask = P->cur_mask;
+  ua.dt_f = P->dt_f;
+  CK(ltsoct::launch_update(ua, P->stream), "update kernel launch");
+  P->launches++;
+  for (int l = P->lmin; l <= P->lmax; ++l) P->cur_mask ^= 1u << l;
+  lts_status st = sync_fields(P, P->d_u[0], P->d_u[1], P->cur_mask);
+  if (st != LTS_OK) return st;
+  P->n_sub++;
+  if (P->n_sub == (int64_t(1) << (P->lmax - P->lmin))) {
+    P->t_macro += double(P->n_sub) * P->dt_f;
+    P->n_sub = 0;
+  }
+  return LTS_OK;
+}
+
+bool supported(const lts_problem& p, std::string* why) {
+  if (p.pde != LTS_PDE_ADVECTION && p.pde != LTS_PDE_WAVE) return *why = "pde must be 0 or 1", false;
+  if (p.rk != 4 && p.rk != 3) return *why = "rk must be 4 or 3", false;
+  if (!(p.cfl > 0.0) || !(p.ko_sigma >= 0.0)) return *why = "cfl must be > 0 and ko_sigma >= 0", false;
+  if (p.bc == LTS_BC_EXACT) {
+    if (p.pde == LTS_PDE_ADVECTION && p.ic != LTS_IC_ADV_GAUSS)
+      return *why = "exact boundary data for advection needs ic = LTS_IC_ADV_GAUSS", false;
+    if (p.pde == LTS_PDE_WAVE && p.ic != LTS_IC_WAVE_PLANAR)
+      return *why = "exact boundary data for the wave equation needs ic = LTS_IC_WAVE_PLANAR", false;
+  } else if (p.bc == LTS_BC_RADIATIVE) {
+    if (p.pde != LTS_PDE_WAVE) return *why = "radiative boundary is for the wave equation", false;
+    if (p.ic != LTS_IC_WAVE_SHELL && p.ic != LTS_IC_WAVE_PLANAR)
+      return *why = "wave initial data must be LTS_IC_WAVE_SHELL or LTS_IC_WAVE_PLANAR", false;
+  } else {
+    return *why = "bc must be 0 or 1", false;
+  }
+  if (p.ic == LTS_IC_WAVE_SHELL && (p.ic_params[3] < 0 || p.ic_params[3] > 4))
+    return *why = "shell initial data takes at most 4 modes", false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lts_strerror(lts_status s) {
+  switch (s) {
+    case LTS_OK: return "ok";
+    case LTS_EINVAL: return "invalid argument";
+    case LTS_ENOMEM: return "out of memory";
+    case LTS_ECUDA: return "CUDA error";
+    case LTS_ETIMEOUT: return "device wait timed out";
+    case LTS_EUNBALANCED: return "octree is not 2:1 balanced";
+    case LTS_ESTATE: return "invalid plan state";
+    case LTS_EINTERNAL: return "internal consistency check failed";
+  }
+  return "unknown status";
+}
+
+const char* lts_last_error(void) { return ltsoct::last_error_cstr(); }
+
+lts_status octree_build(const lts_refine_spec* spec, lts_octree** out) {
+  if (!spec || !out) return fail(LTS_EINVAL, "octree_build: null argument");
+  *out = nullptr;
+  try {
+    auto* t = new lts_octree();
+    t->spec = *spec;
+    std::string err;
+    if (!ltsoct::build_octree(*spec, &t->leaves, &err)) {
+      delete t;
+      return fail(LTS_EINVAL, err);
+    }
+    *out = t;
+    return LTS_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(LTS_ENOMEM, "octree_build: out of host memory");
+  }
+}
+
+lts_status octree_size(const lts_octree* tree, int64_t* n) {
+  if (!tree || !n) return fail(LTS_EINVAL, "octree_size: null argument");
+  *n = int64_t(tree->leaves.size());
+  return LTS_OK;
+}
+
+lts_status octree_export(const lts_octree* tree, int32_t* xyz, int32_t* level) {
+  if (!tree || !xyz || !level) return fail(LTS_EINVAL, "octree_export: null argument");
+  for (size_t i = 0; i < tree->leaves.size(); ++i) {
+    xyz[3 * i] = tree->leaves[i].x;
+    xyz[3 * i + 1] = tree->leaves[i].y;
+    xyz[3 * i + 2] = tree->leaves[i].z;
+    level[i] = tree->leaves[i].l;
+  }
+  return LTS_OK;
+}
+
+void octree_destroy(lts_octree* tree) { delete tree; }
+
+lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_plan** out) {
+  if (!tree || !prob || !out) return fail(LTS_EINVAL, "lts_plan_create: null argument");
+  *out = nullptr;
+  std::string why;
+  if (!supported(*prob, &why)) return fail(LTS_EINVAL, "lts_plan_create: " + why);
+  if (tree->leaves.empty()) return fail(LTS_EINVAL, "lts_plan_create: empty octree");
+  lts_plan* P = nullptr;
+  try {
+    P = new lts_plan();
+  } catch (const std::bad_alloc&) {
+    return fail(LTS_ENOMEM, "lts_plan_create: out of host memory");
+  }
+  P->prob = *prob;
+  P->spec = tree->spec;
+  P->stream = static_cast<cudaStream_t>(prob->stream);
+  P->scheme = prob->rk == 4 ? 0 : 1;
+  ltsoct::Tables rk4, rk3;
+  ltsoct::make_tables(4, &rk4);
+  ltsoct::make_tables(3, &rk3);
+  P->tab = prob->rk == 4 ? rk4 : rk3;
+  P->p = P->tab.p;
+  P->nf = prob->pde == LTS_PDE_WAVE ? 2 : 1;
+  P->octs = tree->leaves;
+  P->N = int64_t(P->octs.size());
+  if (P->N * 27 > INT32_MAX || P->N * kNV * 4 > (int64_t(1) << 46)) {
+    delete P;
+    return fail(LTS_EINVAL, "lts_plan_create: octree too large");
+  }
+  P->lmin = 99;
+  P->lmax = -1;
+  for (const auto& o : P->octs) {
+    P->count[o.l]++;
+    P->lmin = std::min(P->lmin, int(o.l));
+    P->lmax = std::max(P->lmax, int(o.l));
+  }
+  for (int l = 0; l <= 32; ++l) P->off[l + 1] = P->off[l] + P->count[l];
+  std::string err;
+  lts_status st = ltsoct::build_neighbours(P->octs, &P->nb, &err);
+  if (st != LTS_OK) {
+    delete P;
+    return fail(st, err);
+  }
+  // octants with a coarser neighbour carry hanging nodes
+  for (int64_t b = 0; b < P->N; ++b) {
+    bool h = false;
+    for (int d = 0; d < 27 && !h; ++d) {
+      const int e = P->nb.nbr[b * 27 + d];
+      h = e >= 0 && P->octs[e].l == P->octs[b].l - 1;
+    }
+    if (h) P->hang.push_back(int32_t(b));
+  }
+  for (int l = 0; l <= 32; ++l) {
+    P->hang_off[l + 1] = P->hang_off[l];
+    while (P->hang_off[l + 1] < int64_t(P->hang.size()) && P->octs[P->hang[P->hang_off[l + 1]]].l == l)
+      P->hang_off[l + 1]++;
+  }
+  // reading of the CFL condition (Sec. 3.4): dt_f = cfl * node spacing of the finest level
+  const double h_f = (P->spec.hi - P->spec.lo) / (6.0 * double(int64_t(1) << P->lmax));
+  P->dt_f = prob->cfl * h_f;
+  // work model (eqs. w_nuts, w_uts)
+  const int L = P->lmax - P->lmin;
+  for (int l = P->lmin; l <= P->lmax; ++l) {
+    P->w_lts += std::ldexp(double(P->count[l]), l - P->lmin);
+    P->w_gts += std::ldexp(double(P->count[l]), L);
+  }
+  double W[13][7], E[4][4];
+  ltsoct::lagrange_7_to_13(W);
+  ltsoct::cubic_extrapolation(E);
+  cudaError_t ce = ltsoct::upload_tables(&rk4, &rk3, W, E);
+  if (ce != cudaSuccess) {
+    delete P;
+    return cuda_fail(ce, "lts_plan_create: table upload");
+  }
+  const size_t fbytes = size_t(P->N) * kNV * sizeof(double) * P->nf;
+  P->d_oct = static_cast<int4*>(dev_alloc(P, sizeof(int4) * P->N));
+  P->d_nbr = static_cast<int*>(dev_alloc(P, sizeof(int) * P->N * 27));
+  P->d_fine = static_cast<int*>(dev_alloc(P, sizeof(int) * std::max<size_t>(P->nb.fine.size(), 8)));
+  P->d_hang = static_cast<int*>(dev_alloc(P, sizeof(int) * std::max<size_t>(P->hang.size(), 1)));
+  P->d_u[0] = static_cast<double*>(dev_alloc(P, fbytes));
+  P->d_u[1] = static_cast<double*>(dev_alloc(P, fbytes));
+  P->d_K = static_cast<double*>(dev_alloc(P, fbytes * P->p));
+  P->d_err = static_cast<int*>(dev_alloc(P, sizeof(int) * 4));
+  if (!P->d_oct || !P->d_nbr || !P->d_fine || !P->d_hang || !P->d_u[0] || !P->d_u[1] || !P->d_K || !P->d_err) {
+    release(P);
+    delete P;
+    return fail(LTS_ENOMEM, "lts_plan_create: device allocation failed");
+  }
+  std::vector<int4> hoct(P->N);
+  for (int64_t i = 0; i < P->N; ++i) hoct[i] = make_int4(P->octs[i].x, P->octs[i].y, P->octs[i].z, P->octs[i].l);
+  cudaError_t e1 = cudaMemcpyAsync(P->d_oct, hoct.data(), sizeof(int4) * P->N, cudaMemcpyHostToDevice, P->stream);
+  cudaError_t e2 = cudaMemcpyAsync(P->d_nbr, P->nb.nbr.data(), sizeof(int) * P->N * 27, cudaMemcpyHostToDevice, P->stream);
+  cudaError_t e3 = P->nb.fine.empty() ? cudaSuccess
+                                      : cudaMemcpyAsync(P->d_fine, P->nb.fine.data(), sizeof(int) * P->nb.fine.size(),
+                                                        cudaMemcpyHostToDevice, P->stream);
+  cudaError_t e4 = P->hang.empty() ? cudaSuccess
+                                   : cudaMemcpyAsync(P->d_hang, P->hang.data(), sizeof(int) * P->hang.size(),
+                                                     cudaMemcpyHostToDevice, P->stream);
+  cudaError_t e5 = cudaMemsetAsync(P->d_K, 0, fbytes * P->p, P->stream);
+  cudaError_t e6 = cudaMemsetAsync(P->d_u[0], 0, fbytes, P->stream);
+  cudaError_t e7 = cudaMemsetAsync(P->d_u[1], 0, fbytes, P->stream);
+  cudaError_t e9 = cudaMemsetAsync(P->d_err, 0, sizeof(int) * 4, P->stream);
+  cudaError_t e8 = cudaStreamSynchronize(P->stream);
+  for (cudaError_t e : {e1, e2, e3, e4, e5, e6, e7, e9, e8})
+    if (e != cudaSuccess) {
+      release(P);
+      delete P;
+      return cuda_fail(e, "lts_plan_create: upload");
+    }
+  *out = P;
+  return LTS_OK;
+}
+
+void lts_plan_destroy(lts_plan* plan) {
+  if (!plan) return;
+  release(plan);
+  delete plan;
+}
+
+lts_status lts_plan_stats(const lts_plan* P, lts_stats* out) {
+  if (!P || !out) return fail(LTS_EINVAL, "lts_plan_stats: null argument");
+  std::memset(out, 0, sizeof(*out));
+  out->n_octants = P->N;
+  out->nf = P->nf;
+  out->p = P->p;
+  out->l_min = P->lmin;
+  out->l_max = P->lmax;
+  for (int l = 0; l < 32; ++l) out->octants_per_level[l] = P->count[l];
+  out->dt_finest = P->dt_f;
+  out->dt_coarsest = std::ldexp(P->dt_f, P->lmax - P->lmin);
+  out->time = P->t_macro + double(P->n_sub) * P->dt_f;
+  out->substep = P->n_sub;
+  out->model_speedup = P->w_gts / P->w_lts;
+  out->lts_work_per_macro = P->w_lts;
+  out->gts_work_per_macro = P->w_gts;
+  out->device_bytes = P->bytes;
+  out->kernel_launches = P->launches;
+  return LTS_OK;
+}
+
+lts_status lts_set_initial(lts_plan* P, double t0) {
+  if (!P) return fail(LTS_EINVAL, "lts_set_initial: null plan");
+  ltsoct::InitArgs a{};
+  a.tree = dev_tree(P);
+  a.u = P->d_u[0];
+  a.fstride = P->N * kNV;
+  a.nf = P->nf;
+  a.ic = P->prob.ic;
+  a.pde = P->prob.pde;
+  a.t0 = t0;
+  a.lo = P->spec.lo;
+  a.ext = P->spec.hi - P->spec.lo;
+  for (int d = 0; d < 3; ++d) a.adv[d] = P->prob.adv[d];
+  for (int i = 0; i < 32; ++i) a.icp.v[i] = P->prob.ic_params[i];
+  CK(ltsoct::launch_init(a, P->stream), "init kernel launch");
+  P->launches++;
+  CK(cudaMemsetAsync(P->d_K, 0, size_t(P->N) * kNV * sizeof(double) * P->nf * P->p, P->stream), "memset");
+  P->cur_mask = 0;
+  P->t_macro = t0;
+  P->n_sub = 0;
+  return LTS_OK;
+}
+
+lts_status lts_set_state(lts_plan* P, const double* u, double t0, int on_device) {
+  if (!P || !u) return fail(LTS_EINVAL, "lts_set_state: null argument");
+  const size_t bytes = size_t(P->N) * kNV * sizeof(double) * P->nf;
+  CK(cudaMemcpyAsync(P->d_u[0], u, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, P->stream),
+     "lts_set_state copy");
+  CK(cudaMemsetAsync(P->d_K, 0, bytes * P->p, P->stream), "memset");
+  P->cur_mask = 0;
+  P->t_macro = t0;
+  P->n_sub = 0;
+  return LTS_OK;
+}
+
+// device-side guard failures surface at the next synchronising call
+static lts_status check_device_error(lts_plan* P) {
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, P->stream), "error word read");
+  CK(cudaStreamSynchronize(P->stream), "cudaStreamSynchronize");
+  if (h) return fail(LTS_EINTERNAL, "device guard: a padding source lay outside its octant (code " + std::to_string(h) + ")");
+  return LTS_OK;
+}
+
+// the current state of level l lives in u[cur(l)]: gather level ranges
+static lts_status copy_state(lts_plan* P, const double* const* src_for_level, double* dst, int on_device) {
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const size_t fstride = size_t(P->N) * kNV;
+  for (int f = 0; f < P->nf; ++f)
+    for (int l = P->lmin; l <= P->lmax; ++l) {
+      if (!P->count[l]) continue;
+      const size_t o = f * fstride + size_t(P->off[l]) * kNV;
+      CK(cudaMemcpyAsync(dst + o, src_for_level[l] + o, size_t(P->count[l]) * kNV * sizeof(double), kind, P->stream),
+         "state copy");
+    }
+  CK(cudaStreamSynchronize(P->stream), "cudaStreamSynchronize");
+  return check_device_error(P);
+}
+
+lts_status lts_get_state(lts_plan* P, double* u, double* t, int on_device) {
+  if (!P || !u) return fail(LTS_EINVAL, "lts_get_state: null argument");
+  const double* src[33];
+  for (int l = 0; l < 33; ++l) src[l] = P->d_u[cur_of(P, l)];
+  lts_status st = copy_state(P, src, u, on_device);
+  if (st == LTS_OK && t) *t = P->t_macro + double(P->n_sub) * P->dt_f;
+  return st;
+}
+
+lts_status lts_get_stage(lts_plan* P, int j, double* k, int on_device) {
+  if (!P || !k || j < 0 || j >= P->p) return fail(LTS_EINVAL, "lts_get_stage: bad argument");
+  const double* src[33];
+  for (int l = 0; l < 33; ++l) src[l] = P->d_K + size_t(j) * P->nf * P->N * kNV;
+  return copy_state(P, src, k, on_device);
+}
+
+lts_status lts_run_substeps(lts_plan* P, int64_t n) {
+  if (!P || n < 0) return fail(LTS_EINVAL, "lts_run_substeps: bad argument");
+  for (int64_t i = 0; i < n; ++i) {
+    lts_status st = lts_substep(P);
+    if (st != LTS_OK) return st;
+  }
+  return LTS_OK;
+}
+
+lts_status lts_advance(lts_plan* P, double t_end) {
+  if (!P) return fail(LTS_EINVAL, "lts_advance: null plan");
+  if (P->n_sub != 0) return fail(LTS_ESTATE, "lts_advance: plan is inside a macro step");
+  const double dtc = std::ldexp(P->dt_f, P->lmax - P->lmin);
+  const double steps = (t_end - P->t_macro) / dtc;
+  const double n = std::round(steps);
+  if (n < 0 || std::fabs(steps - n) > 1e-9 * std::max(1.0, std::fabs(steps)))
+    return fail(LTS_EINVAL, "lts_advance: t_end - t is not a whole number of macro steps");
+  return lts_run_substeps(P, int64_t(n) << (P->lmax - P->lmin));
+}
+
+lts_status gts_steps(lts_plan* P, int64_t n) {
+  if (!P || n < 0) return fail(LTS_EINVAL, "gts_steps: bad argument");
+  for (int64_t i = 0; i < n; ++i) {
+    lts_status st = gts_step(P);
+    if (st != LTS_OK) return st;
+  }
+  return LTS_OK;
+}
+
+lts_status gts_advance(lts_plan* P, double t_end) {
+  if (!P) return fail(LTS_EINVAL, "gts_advance: null plan");
+  const double t = P->t_macro + double(P->n_sub) * P->dt_f;
+  const double steps = (t_end - t) / P->dt_f;
+  const double n = std::round(steps);
+  if (n < 0 || std::fabs(steps - n) > 1e-9 * std::max(1.0, std::fabs(steps)))
+    return fail(LTS_EINVAL, "gts_advance: t_end - t is not a whole number of steps");
+  return gts_steps(P, int64_t(n));
+}
+
+lts_status lts_export_o2o(const lts_plan* P, int32_t* out) {
+  if (!P || !out) return fail(LTS_EINVAL, "lts_export_o2o: null argument");
+  for (int64_t b = 0; b < P->N; ++b)
+    for (int d = 0; d < 27; ++d) {
+      int32_t* ent = out + (b * 27 + d) * 8;
+      const int e = P->nb.nbr[b * 27 + d];
+      for (int c = 0; c < 8; ++c) ent[c] = -1;
+      if (e == -1)
+        ent[0] = -2;
+      else if (e >= 0)
+        ent[0] = e;
+      else
+        for (int c = 0; c < 8; ++c) ent[c] = P->nb.fine[(-e - 2) * 8 + c];
+    }
+  return LTS_OK;
+}
+
+static lts_status export_map(lts_plan* P, const int32_t* octs, int64_t n, int32_t* src, int32_t* r, int nodes) {
+  if (!P || (n && (!octs || !src || !r)) || n < 0) return fail(LTS_EINVAL, "map export: bad argument");
+  for (int64_t i = 0; i < n; ++i)
+    if (octs[i] < 0 || octs[i] >= P->N) return fail(LTS_EINVAL, "map export: octant index out of range");
+  if (!n) return LTS_OK;
+  const int npts = nodes ? kNV : ltsoct::kNT;
+  int *d_list = nullptr, *d_src = nullptr, *d_r = nullptr;
+  CK(cudaMallocAsync(&d_list, sizeof(int) * n, P->stream), "cudaMallocAsync");
+  CK(cudaMallocAsync(&d_src, sizeof(int) * n * npts, P->stream), "cudaMallocAsync");
+  CK(cudaMallocAsync(&d_r, sizeof(int) * n * npts * 3, P->stream), "cudaMallocAsync");
+  CK(cudaMemcpyAsync(d_list, octs, sizeof(int) * n, cudaMemcpyHostToDevice, P->stream), "copy");
+  ltsoct::MapArgs a{};
+  a.tree = dev_tree(P);
+  a.octs = d_list;
+  a.count = int(n);
+  a.nodes = nodes;
+  a.src = d_src;
+  a.r = d_r;
+  CK(ltsoct::launch_maps(a, P->stream), "map kernel launch");
+  P->launches++;
+  CK(cudaMemcpyAsync(src, d_src, sizeof(int) * n * npts, cudaMemcpyDeviceToHost, P->stream), "copy");
+  CK(cudaMemcpyAsync(r, d_r, sizeof(int) * n * npts * 3, cudaMemcpyDeviceToHost, P->stream), "copy");
+  CK(cudaFreeAsync(d_list, P->stream), "cudaFreeAsync");
+  CK(cudaFreeAsync(d_src, P->stream), "cudaFreeAsync");
+  CK(cudaFreeAsync(d_r, P->stream), "cudaFreeAsync");
+  CK(cudaStreamSynchronize(P->stream), "cudaStreamSynchronize");
+  return LTS_OK;
+}
+
+lts_status lts_export_pad_map(lts_plan* P, const int32_t* octs, int64_t n, int32_t* src, int32_t* r) {
+  return export_map(P, octs, n, src, r, 0);
+}
+
+lts_status lts_export_node_map(lts_plan* P, const int32_t* octs, int64_t n, int32_t* src, int32_t* r) {
+  return export_map(P, octs, n, src, r, 1);
+}
+
+lts_status lts_set_profiling(lts_plan* P, int on) {
+  if (!P) return fail(LTS_EINVAL, "lts_set_profiling: null plan");
+  P->profiling = on != 0;
+  return LTS_OK;
+}
+
+lts_status lts_kernel_stats(lts_plan* P, int64_t* launches, double* ms, double* flops, double* bytes,
+                            int64_t* node_stages, int reset) {
+  if (!P) return fail(LTS_EINVAL, "lts_kernel_stats: null plan");
+  lts_status dst = check_device_error(P);
+  if (dst != LTS_OK) return dst;
+  for (size_t i = 0; i < P->events.size(); ++i) {
+    float t = 0.0f;
+    CK(cudaEventElapsedTime(&t, P->events[i].first, P->events[i].second), "cudaEventElapsedTime");
+    P->prof_ms += t;
+    P->prof_launches++;
+    P->prof_node_stages += P->event_nodes[i];
+    cudaEventDestroy(P->events[i].first);
+    cudaEventDestroy(P->events[i].second);
+  }
+  P->events.clear();
+  P->event_nodes.clear();
+  if (launches) *launches = P->prof_launches;
+  if (ms) *ms = P->prof_ms;
+  if (node_stages) *node_stages = P->prof_node_stages;
+  if (flops) *flops = double(P->prof_node_stages) * flops_per_node_stage(P->prob.pde);
+  if (bytes) *bytes = double(P->prof_node_stages) * bytes_per_node_stage(P->nf);
+  if (reset) {
+    P->prof_launches = 0;
+    P->prof_node_stages = 0;
+    P->prof_ms = 0.0;
+  }
+  return LTS_OK;
+}
+
+}  // extern "C"

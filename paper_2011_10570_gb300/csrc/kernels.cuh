@@ -1,0 +1,94 @@
+// Device-side argument blocks and launchers of libltsoct (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ltsoct_internal.h"
+
+namespace ltsoct {
+
+struct DevTree {
+  const int4* oct;   // (x, y, z, level), level order
+  const int* nbr;    // [N][27]
+  const int* fine;   // [F][8]
+  int n;
+};
+
+struct IcParams {
+  double v[32];
+};
+
+// One RK stage over the active octants [first, n) (Alg. 2 compute_stage, or
+// Alg. 1 when gts != 0).
+struct StageArgs {
+  DevTree tree;
+  double* u[2];          // double-buffered state [nf][N][343]; level l uses u[(cur_mask >> l) & 1]
+  double* K;             // RK stages [p][nf][N][343]
+  long long fstride;     // N * 343
+  int nf, p, scheme, stage;
+  int first;             // first active octant (level order)
+  int lstar, lmax;       // coarsest active level, finest level
+  unsigned cur_mask;
+  int gts;               // 1: every octant steps with dt_f, no correction, no fused update
+  int write_update;      // 1: the last stage also writes u_new into the other buffer
+  double dt_f, t_b;      // finest step; start time of the steps in this substep
+  double lo, ext;        // domain [lo, lo + ext]^3
+  int pde, bc, ic;
+  double adv[3];
+  double ko_sigma;
+  IcParams icp;
+  int* err;              // device error word: bit 0 source coordinate out of range, bit 1 balance violated
+};
+
+struct SyncArgs {
+  DevTree tree;
+  double* vb[2];         // level l's array is vb[(sel_mask >> l) & 1]
+  unsigned sel_mask;
+  long long fstride;
+  int nf;
+  const int* list;       // octants to process (hanging pass), or nullptr = [0, n)
+  int count;
+  int* err;
+};
+
+struct UpdateArgs {
+  double* u[2];
+  const double* K;
+  long long fstride;
+  int nf, p, scheme;
+  int n;
+  const int4* oct;
+  unsigned cur_mask;
+  double dt_f;
+};
+
+struct InitArgs {
+  DevTree tree;
+  double* u;             // [nf][N][343]
+  long long fstride;
+  int nf, ic, pde;
+  double t0, lo, ext;
+  double adv[3];
+  IcParams icp;
+};
+
+struct MapArgs {
+  DevTree tree;
+  const int* octs;
+  int count;
+  int nodes;             // 0: 2197 padded points, 1: 343 nodes
+  int* src;
+  int* r;
+};
+
+cudaError_t upload_tables(const Tables* rk4, const Tables* rk3, const double W[13][7], const double E[4][4]);
+cudaError_t launch_stage(const StageArgs& a, int count, cudaStream_t s);
+cudaError_t launch_sync_zip(const SyncArgs& a, cudaStream_t s);
+cudaError_t launch_sync_hanging(const SyncArgs& a, cudaStream_t s);
+cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
+cudaError_t launch_init(const InitArgs& a, cudaStream_t s);
+cudaError_t launch_maps(const MapArgs& a, cudaStream_t s);
+
+}  // namespace ltsoct

@@ -49,7 +49,7 @@ def shell_modes(seed, nmodes=4):
     return modes
 
 
-def wave_shell(l_min=4, l_max=9, band=0.05, seed=1, amp=1e-3, radius=2.0, width=0.1, t_end=5.0,
+def wave_shell(l_min=4, l_max=9, band=0.0, seed=1, amp=1e-3, radius=2.0, width=0.1, t_end=5.0,
                cfl=0.25, ko_sigma=0.1, rk=4, bc=BC_RADIATIVE, half=10.0):
     """Wave equation chi_t = phi, phi_t = lap chi on [-half,half]^3 around a Gaussian shell
     chi_0 = exp(-(r-R)^2/w) (1 + amp sum_i eps_i sin(kscale k_i.x + theta_i)), phi_0 = 0."""
