@@ -1240,9 +1240,10 @@ void orc_set_initial(orc_solver* s, double t0) {
       double x[3], d[2][6];
       pos6_to_x(s, P, x);
       orc_exact_derivs(&s->pr, x, t0, d);
-      double v0 = d[0][0];
+      double v0 = d[0][0], v1 = d[1][0];
       if (s->pr.ic == ORC_IC_WAVE_SHELL) {
-        /* reading R13: smooth seeded modulation of the shell amplitude */
+        /* reading R13: chi_0 = F(r) (1 + amp sum eps sin(kscale k.x + theta)), phi_0 = 0
+         * (the shell data at rest, not the time derivative of the closed form) */
         const double* p = s->pr.ic_params;
         double amp = p[2], ks = p[4], pert = 0.0;
         int nm = (int)p[3];
@@ -1250,10 +1251,12 @@ void orc_set_initial(orc_solver* s, double t0) {
           const double* md = p + 5 + 5 * m;
           pert += md[0] * sin(ks * (md[1] * x[0] + md[2] * x[1] + md[3] * x[2]) + md[4]);
         }
-        v0 = v0 * (1.0 + amp * pert);
+        double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]), z = r - p[0];
+        v0 = exp(-z * z / p[1]) * (1.0 + amp * pert);
+        v1 = 0.0;
       }
       fld(s->u, s, 0, b)[n] = v0;
-      if (s->nf == 2) fld(s->u, s, 1, b)[n] = d[1][0];
+      if (s->nf == 2) fld(s->u, s, 1, b)[n] = v1;
     }
   }
   memcpy(s->u_start, s->u, s->fsz * (size_t)s->nf * sizeof(double));

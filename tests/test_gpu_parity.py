@@ -151,7 +151,7 @@ def test_deep_narrow_tree(lt, orc):
     w = W.advection_gauss(l_min=1, l_max=10, radius=1e-4, width=0.05)
     gt, plan, ot, sol = both(lt, orc, w)
     _, lev = gt.export()
-    assert lev.min() == 1 and lev.max() == 10
+    assert lev.min() == 2 and lev.max() == 10 and len(set(lev)) == 9
     plan.set_initial(0.0)
     sol.set_initial(0.0)
     plan.run_substeps(3)
@@ -259,10 +259,10 @@ def test_full_wave_first_substeps_sampled(lt, orc, full_wave):
     sol.lts_substep_masked(need1.astype(np.uint8), S1.astype(np.uint8))
     u1 = sol.state()
     idx1 = np.where(S1)[0]
-    # errors relative to each field's global magnitude (sampled octants far from
-    # the shell hold values near zero)
+    # relative L-infinity over the state vector (both fields), as elsewhere; sampled
+    # octants far from the shell hold values near zero
     def err(a, b, full):
-        return max(np.abs(a[f] - b[f]).max() / np.abs(full[f]).max() for f in range(a.shape[0]))
+        return np.abs(a - b).max() / np.abs(full).max()
     assert err(u_gpu[:, idx1], u1[:, idx1], u_gpu) <= TOL
     # levels 4..8 stepped once in substep 0 and then rested
     assert err(u_gpu[:, idx0], u0[:, idx0], u_gpu) <= TOL
