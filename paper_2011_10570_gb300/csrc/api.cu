@@ -48,6 +48,7 @@ struct lts_plan {
   int* d_hang = nullptr;
   double* d_u[2] = {nullptr, nullptr};
   double* d_K = nullptr;
+  double* d_U[2] = {nullptr, nullptr};  // stage inputs of the current and the next stage
   int* d_err = nullptr;
   int64_t launches = 0;               // every kernel launched by the plan
   size_t bytes = 0;
@@ -141,16 +142,28 @@ lts_status sync_fields(lts_plan* P, double* vb0, double* vb1, unsigned sel) {
   return LTS_OK;
 }
 
+ltsoct::StageTerms terms_of(const double* row, int p) {
+  ltsoct::StageTerms t{};
+  for (int j = 0; j < p; ++j)
+    if (row[j] != 0.0) {
+      t.j[t.n] = j;
+      t.w[t.n] = row[j];
+      t.n++;
+    }
+  return t;
+}
+
 ltsoct::StageArgs stage_args(const lts_plan* P, int stage, int first, int lstar, int gts) {
   ltsoct::StageArgs a{};
   a.tree = dev_tree(P);
   a.u[0] = P->d_u[0];
   a.u[1] = P->d_u[1];
   a.K = P->d_K;
+  a.Uin = P->d_U[stage & 1];
+  a.Uout = P->d_U[(stage + 1) & 1];
   a.fstride = P->N * kNV;
   a.nf = P->nf;
   a.p = P->p;
-  a.scheme = P->scheme;
   a.stage = stage;
   a.first = first;
   a.lstar = lstar;
@@ -158,7 +171,6 @@ ltsoct::StageArgs stage_args(const lts_plan* P, int stage, int first, int lstar,
   a.cur_mask = P->cur_mask;
   a.gts = gts;
   a.write_update = gts ? 0 : 1;
-  a.dt_f = P->dt_f;
   a.t_b = P->t_macro + double(P->n_sub) * P->dt_f;
   a.lo = P->spec.lo;
   a.ext = P->spec.hi - P->spec.lo;
@@ -166,7 +178,20 @@ ltsoct::StageArgs stage_args(const lts_plan* P, int stage, int first, int lstar,
   a.bc = P->prob.bc;
   a.ic = P->prob.ic;
   for (int d = 0; d < 3; ++d) a.adv[d] = P->prob.adv[d];
-  a.ko_sigma = P->prob.ko_sigma;
+  for (int l = 0; l < 32; ++l) {
+    const double h = a.ext / (6.0 * std::ldexp(1.0, l));
+    a.lc[l].dt = gts ? P->dt_f : std::ldexp(P->dt_f, P->lmax - l);
+    a.lc[l].inv12h = 1.0 / (12.0 * h);
+    a.lc[l].inv12h2 = 1.0 / (12.0 * h * h);
+    a.lc[l].kos = P->prob.ko_sigma / (64.0 * h);
+  }
+  a.om[0] = terms_of(P->tab.a[stage], P->p);
+  for (int r = 1; r < 4; ++r) a.om[r] = terms_of(P->tab.omega[r][stage], P->p);
+  if (stage + 1 < P->p) a.next = terms_of(P->tab.a[stage + 1], P->p);
+  for (int j = 0; j < 4; ++j) {
+    a.w[j] = P->tab.w[j];
+    a.gamma[j] = P->tab.gamma[stage][j];
+  }
   for (int i = 0; i < 32; ++i) a.icp.v[i] = P->prob.ic_params[i];
   a.err = P->d_err;
   return a;
@@ -223,6 +248,12 @@ lts_status gts_step(lts_plan* P) {
     double* Ks = P->d_K + s * kstride;
     st = sync_fields(P, Ks, Ks, 0u);
     if (st != LTS_OK) return st;
+    if (s + 1 < P->p) {
+      // the next stage's inputs were formed from the unsynchronised stage: sync them too
+      double* Un = P->d_U[(s + 1) & 1];
+      st = sync_fields(P, Un, Un, 0u);
+      if (st != LTS_OK) return st;
+    }
   }
   ltsoct::UpdateArgs ua{};
   ua.u[0] = P->d_u[0];
@@ -409,7 +440,10 @@ lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_
   P->d_u[1] = static_cast<double*>(dev_alloc(P, fbytes));
   P->d_K = static_cast<double*>(dev_alloc(P, fbytes * P->p));
   P->d_err = static_cast<int*>(dev_alloc(P, sizeof(int) * 4));
-  if (!P->d_oct || !P->d_nbr || !P->d_fine || !P->d_hang || !P->d_u[0] || !P->d_u[1] || !P->d_K || !P->d_err) {
+  P->d_U[0] = static_cast<double*>(dev_alloc(P, fbytes));
+  P->d_U[1] = static_cast<double*>(dev_alloc(P, fbytes));
+  if (!P->d_oct || !P->d_nbr || !P->d_fine || !P->d_hang || !P->d_u[0] || !P->d_u[1] || !P->d_K || !P->d_err ||
+      !P->d_U[0] || !P->d_U[1]) {
     release(P);
     delete P;
     return fail(LTS_ENOMEM, "lts_plan_create: device allocation failed");

@@ -132,37 +132,30 @@ __device__ void load_neighbours(const DevTree& t, int b, NbrView& nv) {
   }
 }
 
-// stage input of a source node: u + dt * sum_j om[j] K_j (eq. rk_schemes with the
-// corrected weights of eqs. fc_1 / fc_2); zero weights are skipped
-__device__ __forceinline__ double stage_value(const double* __restrict__ u, const double* __restrict__ k0,
-                                              long long kstride, int p, const double* om, double dt) {
+// stage input of a source node from its step-start state and RK stages,
+// u + dt * sum_t w_t K_(j_t)  (eq. rk_schemes with the corrected weights of
+// eqs. fc_1 / fc_2)
+__device__ __forceinline__ double corrected_value(const double* __restrict__ u, const double* __restrict__ k0,
+                                                  long long kstride, const StageTerms& t, double dt) {
   double acc = 0.0;
-  for (int j = 0; j < p; ++j) {
-    const double w = om[j];
-    if (w != 0.0) acc = fma(w, __ldg(k0 + j * kstride), acc);
-  }
+  for (int q = 0; q < t.n; ++q) acc = fma(t.w[q], __ldg(k0 + t.j[q] * kstride), acc);
   return fma(dt, acc, __ldg(u));
 }
 
-__device__ double interp_tensor(const double* __restrict__ v, int rx, int ry, int rz) {
-  // x then y then z; even coordinates are exact nodes
+// tensor-product Lagrange interpolation, x then y then z; even coordinates are nodes
+__device__ double interp_tensor(const double* __restrict__ v, const double (*W)[7], int rx, int ry, int rz) {
   const int x0 = (rx & 1) ? 0 : rx >> 1, x1 = (rx & 1) ? 6 : rx >> 1;
   const int y0 = (ry & 1) ? 0 : ry >> 1, y1 = (ry & 1) ? 6 : ry >> 1;
   const int z0 = (rz & 1) ? 0 : rz >> 1, z1 = (rz & 1) ? 6 : rz >> 1;
   double sz = 0.0;
   for (int c = z0; c <= z1; ++c) {
-    const double wz = (rz & 1) ? c_W[rz][c] : 1.0;
     double sy = 0.0;
     for (int bb = y0; bb <= y1; ++bb) {
-      const double wy = (ry & 1) ? c_W[ry][bb] : 1.0;
       double sx = 0.0;
-      for (int a = x0; a <= x1; ++a) {
-        const double wx = (rx & 1) ? c_W[rx][a] : 1.0;
-        sx = fma(wx, v[a + 7 * bb + 49 * c], sx);
-      }
-      sy = fma(wy, sx, sy);
+      for (int a = x0; a <= x1; ++a) sx = fma(W[rx][a], v[a + 7 * bb + 49 * c], sx);
+      sy = fma(W[ry][bb], sx, sy);
     }
-    sz = fma(wz, sy, sz);
+    sz = fma(W[rz][c], sy, sz);
   }
   return sz;
 }
@@ -221,9 +214,10 @@ __device__ __forceinline__ double lattice_to_x(double lo, double ext, int P6) {
 // ---------------------------------------------------------------------------
 template <int NF>
 struct StageSmem {
-  double T[NF][kNT];   // padded tiles
-  double V[NF][kNV];   // stage inputs of one coarser source (interpolation)
-  double om[4][4];     // omega rows of this stage for the four relations
+  double T[NF][kNT];         // padded tiles
+  double V[NF][kNV];         // stage inputs of one coarser source (interpolation)
+  double W[13][7];           // Lagrange weights
+  StageTerms om[4];          // correction terms of this stage per relation
   int src[kNT];
   unsigned short code[kNT];  // rx | ry << 4 | rz << 8 | (level diff + 1) << 12 | exterior << 15
   NbrView nv;
@@ -232,24 +226,105 @@ struct StageSmem {
   int ncoarse;
 };
 
+constexpr unsigned kExterior = 1u << 15;
+constexpr int kPer = (kNT + kThreads - 1) / kThreads;  // padded points per thread
+
+// exact boundary data (reading R10): RK stage values of the closed-form solution
+template <int NF>
+__device__ __noinline__ void fill_exact(StageSmem<NF>& S, const StageArgs& A, int4 me, int eb, double dtb) {
+  for (int q = threadIdx.x; q < kNT; q += blockDim.x) {
+    if (!(S.code[q] & kExterior)) continue;
+    const int i = q % 13 - 3, j = (q / 13) % 13 - 3, k = q / 169 - 3;
+    const double x[3] = {lattice_to_x(A.lo, A.ext, 6 * me.x + i * eb), lattice_to_x(A.lo, A.ext, 6 * me.y + j * eb),
+                         lattice_to_x(A.lo, A.ext, 6 * me.z + k * eb)};
+    double d[2][5];
+    exact_derivs(A.ic, A.icp, A.adv, x, A.t_b, d);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      double v = d[f][0], dtp = 1.0;
+      for (int m = 0; m < A.p; ++m) {
+        dtp *= dtb;
+        v = fma(A.gamma[m] * dtp, d[f][m + 1], v);
+      }
+      S.T[f][q] = v;
+    }
+  }
+}
+
+// radiative boundary (reading R11): cubic extrapolation along the outward normal, x then y then z
+template <int NF>
+__device__ __noinline__ void fill_extrapolated(StageSmem<NF>& S, int4 me, int eb) {
+  const int anchor[3] = {me.x, me.y, me.z};
+  constexpr int kRoot = 1 << kDepth;
+  for (int a = 0; a < 3; ++a) {
+    const bool lo_b = anchor[a] == 0, hi_b = anchor[a] + eb == kRoot;
+    if (lo_b || hi_b) {
+      const int b1 = (a + 1) % 3, b2 = (a + 2) % 3;
+      const int str = a == 0 ? 1 : (a == 1 ? 13 : 169);
+      const int str1 = b1 == 0 ? 1 : (b1 == 1 ? 13 : 169);
+      const int str2 = b2 == 0 ? 1 : (b2 == 1 ? 13 : 169);
+      for (int t = threadIdx.x; t < 169 * 3; t += blockDim.x) {
+        const int v1 = t % 13 - 3, v2 = (t / 13) % 13 - 3, m = t / 169 + 1;
+        const bool ext1 = (anchor[b1] == 0 && v1 < 0) || (anchor[b1] + eb == kRoot && v1 > 6);
+        const bool ext2 = (anchor[b2] == 0 && v2 < 0) || (anchor[b2] + eb == kRoot && v2 > 6);
+        if ((b1 > a && ext1) || (b2 > a && ext2)) continue;
+        const int base = 3 * str + (v1 + 3) * str1 + (v2 + 3) * str2;  // index 0 along axis a
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          if (lo_b) {
+            double v = 0.0;
+            for (int qq = 0; qq < 4; ++qq) v = fma(c_E[m][qq], S.T[f][base + qq * str], v);
+            S.T[f][base - m * str] = v;
+          }
+          if (hi_b) {
+            double v = 0.0;
+            for (int qq = 0; qq < 4; ++qq) v = fma(c_E[m][qq], S.T[f][base + (6 - qq) * str], v);
+            S.T[f][base + (6 + m) * str] = v;
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// radiative right-hand side at a node on the domain boundary
+template <int NF>
+__device__ __noinline__ void radiative_rhs(const StageSmem<NF>& S, const StageArgs& A, int c0, const int P6[3],
+                                           double inv12h, double kv[NF]) {
+  const double x[3] = {lattice_to_x(A.lo, A.ext, P6[0]), lattice_to_x(A.lo, A.ext, P6[1]),
+                       lattice_to_x(A.lo, A.ext, P6[2])};
+  const double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  const int st[3] = {1, 13, 169};
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const double* T = S.T[f];
+    double xd = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double d1 = fma(8.0, T[c0 + st[a]] - T[c0 - st[a]], T[c0 - 2 * st[a]] - T[c0 + 2 * st[a]]) * inv12h;
+      xd = fma(x[a], d1, xd);
+    }
+    kv[f] = -(xd + (f == 0 ? 1.0 : 2.0) * T[c0]) / r;
+  }
+}
+
 template <int NF>
 __global__ void __launch_bounds__(kThreads) stage_kernel(StageArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StageSmem<NF>& S = *reinterpret_cast<StageSmem<NF>*>(smem_raw);
   const int b = A.first + blockIdx.x;
   const int tid = threadIdx.x;
-  const DevTables& tab = c_tab[A.scheme];
-  const int p = tab.p;
+  const int p = A.p;
   const int s = A.stage;
   const int4 me = A.tree.oct[b];
   const int lb = me.w;
   const int eb = 1 << (kDepth - lb);
+  const long long kstride = (long long)A.nf * A.fstride;
 
   load_neighbours(A.tree, b, S.nv);
-  if (tid < 16) {
-    const int r = tid >> 2, j = tid & 3;
-    S.om[r][j] = (r == 0 || A.gts) ? tab.a[s][j] : tab.omega[r][s][j];
-  }
+  if (tid < 4) S.om[tid] = A.om[tid];
+  for (int q = tid; q < 91; q += blockDim.x) S.W[q / 7][q % 7] = c_W[q / 7][q % 7];
   __syncthreads();
   if (tid < 27) {
     const int e = S.nv.nbr[tid];
@@ -268,7 +343,7 @@ __global__ void __launch_bounds__(kThreads) stage_kernel(StageArgs A) {
     S.ncoarse = n;
   }
 
-  // 1. resolve the source of every padded point
+  // 1. source of every padded point (coarsest leaf containing it, then smallest Morton key)
   for (int q = tid; q < kNT; q += blockDim.x) {
     const int i = q % 13 - 3, j = (q / 13) % 13 - 3, k = q / 169 - 3;
     int src;
@@ -279,17 +354,16 @@ __global__ void __launch_bounds__(kThreads) stage_kernel(StageArgs A) {
     } else {
       src = resolve_source(S.nv, i, j, k, b, false);
       if (src < 0) {
-        code = 1u << 15;
+        code = kExterior;
       } else {
         const int4 so = A.tree.oct[src];
         const int rx = half_node(6 * me.x + i * eb, so.x, so.w);
         const int ry = half_node(6 * me.y + j * eb, so.y, so.w);
         const int rz = half_node(6 * me.z + k * eb, so.z, so.w);
         if (unsigned(rx) > 12u || unsigned(ry) > 12u || unsigned(rz) > 12u || unsigned(so.w - lb + 1) > 2u) {
-          // never reached on a balanced tree: report, and treat the point as a zero ghost
-          atomicOr(A.err, 1);
+          atomicOr(A.err, 1);  // never on a balanced tree: report and use a zero ghost
           src = -1;
-          code = 1u << 15;
+          code = kExterior;
         } else {
           code = unsigned(rx) | unsigned(ry) << 4 | unsigned(rz) << 8 | unsigned(so.w - lb + 1) << 12;
         }
@@ -300,54 +374,71 @@ __global__ void __launch_bounds__(kThreads) stage_kernel(StageArgs A) {
   }
   __syncthreads();
 
-  const long long kstride = (long long)A.nf * A.fstride;
-  auto level_buffer = [&](int l, int rel) -> const double* {
-    const int cur = (A.cur_mask >> l) & 1;
-    return A.u[rel == 3 ? cur ^ 1 : cur];
-  };
-
-  // 2. copies: own interior, same-level and finer sources, even points of coarser sources
-  for (int q = tid; q < kNT; q += blockDim.x) {
-    const unsigned code = S.code[q];
-    if (code & (1u << 15)) {
+  // 2. direct copies: own interior and every source whose stage input is the plain
+  //    RK stage input (same level; every level under GTS), batched for memory parallelism
+  const double* direct = s == 0 ? A.u[(A.cur_mask >> lb) & 1] : A.Uin;
+  {
+    double v[kPer][NF];
 #pragma unroll
-      for (int f = 0; f < NF; ++f) S.T[f][q] = 0.0;
-      continue;
-    }
-    const int rx = code & 15, ry = (code >> 4) & 15, rz = (code >> 8) & 15;
-    if ((rx | ry | rz) & 1) continue;
-    const int src = S.src[q];
-    const int ls = lb + int((code >> 12) & 3) - 1;
-    int rel = 0;
-    double dt = A.dt_f;
-    if (!A.gts) {
-      rel = ls == lb ? 0 : (ls > lb ? 1 : (ls >= A.lstar ? 2 : 3));
-      dt = ldexp(A.dt_f, A.lmax - ls);
-    }
-    const long long off = (long long)src * kNV + (rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1);
-    const double* ub = level_buffer(ls, rel);
+    for (int it = 0; it < kPer; ++it) {
+      const int q = tid + it * kThreads;
 #pragma unroll
-    for (int f = 0; f < NF; ++f)
-      S.T[f][q] = stage_value(ub + f * A.fstride + off, A.K + f * A.fstride + off, kstride, p, S.om[rel], dt);
+      for (int f = 0; f < NF; ++f) v[it][f] = 0.0;
+      if (q < kNT) {
+        const unsigned code = S.code[q];
+        const int rx = code & 15, ry = (code >> 4) & 15, rz = (code >> 8) & 15;
+        const bool same = ((code >> 12) & 7) == 1 || A.gts;
+        if (!(code & kExterior) && same && !((rx | ry | rz) & 1)) {
+          const long long off = (long long)S.src[q] * kNV + (rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1);
+#pragma unroll
+          for (int f = 0; f < NF; ++f) v[it][f] = __ldg(direct + f * A.fstride + off);
+        }
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < kPer; ++it) {
+      const int q = tid + it * kThreads;
+      if (q < kNT) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) S.T[f][q] = v[it][f];
+      }
+    }
   }
 
-  // 3. interpolation from coarser sources (Fig. unzip: coarse -> fine)
+  // 3. corrected copies: finer sources (eq. fc_1) and nodes of coarser sources (eqs. fc_1, fc_2)
+  if (!A.gts) {
+    for (int q = tid; q < kNT; q += blockDim.x) {
+      const unsigned code = S.code[q];
+      const int rel_code = (code >> 12) & 7;
+      if ((code & kExterior) || rel_code == 1) continue;
+      const int rx = code & 15, ry = (code >> 4) & 15, rz = (code >> 8) & 15;
+      if ((rx | ry | rz) & 1) continue;
+      const int ls = lb + rel_code - 1;
+      const int rel = ls > lb ? 1 : (ls >= A.lstar ? 2 : 3);
+      const double* ub = A.u[((A.cur_mask >> ls) & 1) ^ (rel == 3 ? 1 : 0)];
+      const long long off = (long long)S.src[q] * kNV + (rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1);
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+        S.T[f][q] = corrected_value(ub + f * A.fstride + off, A.K + f * A.fstride + off, kstride, S.om[rel],
+                                    A.lc[ls].dt);
+    }
+  }
+
+  // 4. interpolation from coarser sources (Fig. unzip: coarse -> fine)
   const int ncoarse = S.ncoarse;
   for (int c = 0; c < ncoarse; ++c) {
     const int src = S.coarse[c];
     const int ls = lb - 1;
-    int rel = 0;
-    double dt = A.dt_f;
-    if (!A.gts) {
-      rel = ls >= A.lstar ? 2 : 3;
-      dt = ldexp(A.dt_f, A.lmax - ls);
-    }
-    const double* ub = level_buffer(ls, rel);
+    const int rel = ls >= A.lstar ? 2 : 3;
+    const double* ub = A.u[((A.cur_mask >> ls) & 1) ^ (rel == 3 ? 1 : 0)];
+    const double* cdirect = s == 0 ? A.u[(A.cur_mask >> ls) & 1] : A.Uin;
     __syncthreads();
     for (int t = tid; t < NF * kNV; t += blockDim.x) {
       const int f = t / kNV, n = t - f * kNV;
       const long long off = (long long)src * kNV + n;
-      S.V[f][n] = stage_value(ub + f * A.fstride + off, A.K + f * A.fstride + off, kstride, p, S.om[rel], dt);
+      S.V[f][n] = A.gts ? __ldg(cdirect + f * A.fstride + off)
+                        : corrected_value(ub + f * A.fstride + off, A.K + f * A.fstride + off, kstride,
+                                          S.om[rel], A.lc[ls].dt);
     }
     __syncthreads();
     for (int q = tid; q < kNT; q += blockDim.x) {
@@ -356,153 +447,80 @@ __global__ void __launch_bounds__(kThreads) stage_kernel(StageArgs A) {
       const int rx = code & 15, ry = (code >> 4) & 15, rz = (code >> 8) & 15;
       if (!((rx | ry | rz) & 1)) continue;
 #pragma unroll
-      for (int f = 0; f < NF; ++f) S.T[f][q] = interp_tensor(S.V[f], rx, ry, rz);
+      for (int f = 0; f < NF; ++f) S.T[f][q] = interp_tensor(S.V[f], S.W, rx, ry, rz);
     }
   }
   __syncthreads();
 
-  // 4. physical boundary
-  const double h = A.ext * static_cast<double>(eb) / (6.0 * static_cast<double>(1 << kDepth));
-  const double dtb = A.gts ? A.dt_f : ldexp(A.dt_f, A.lmax - lb);
-  const bool touches = me.x == 0 || me.y == 0 || me.z == 0 || me.x + eb == (1 << kDepth) ||
-                       me.y + eb == (1 << kDepth) || me.z + eb == (1 << kDepth);
+  // 5. physical boundary
+  const LevelConst lc = A.lc[lb];
+  constexpr int kRoot = 1 << kDepth;
+  const bool touches = me.x == 0 || me.y == 0 || me.z == 0 || me.x + eb == kRoot || me.y + eb == kRoot ||
+                       me.z + eb == kRoot;
   if (touches) {
-    if (A.bc == LTS_BC_EXACT) {
-      // RK stage value of the closed-form solution: u + sum_m gamma[s][m] dt^(m+1) d^(m+1)u
-      for (int q = tid; q < kNT; q += blockDim.x) {
-        if (!(S.code[q] & (1u << 15))) continue;
-        const int i = q % 13 - 3, j = (q / 13) % 13 - 3, k = q / 169 - 3;
-        const double x[3] = {lattice_to_x(A.lo, A.ext, 6 * me.x + i * eb), lattice_to_x(A.lo, A.ext, 6 * me.y + j * eb),
-                             lattice_to_x(A.lo, A.ext, 6 * me.z + k * eb)};
-        double d[2][5];
-        exact_derivs(A.ic, A.icp, A.adv, x, A.t_b, d);
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-          double v = d[f][0], dtp = 1.0;
-          for (int m = 0; m < p; ++m) {
-            dtp *= dtb;
-            v = fma(tab.gamma[s][m] * dtp, d[f][m + 1], v);
-          }
-          S.T[f][q] = v;
-        }
-      }
-    } else {
-      // cubic extrapolation along the outward normal, x then y then z
-      const int anchor[3] = {me.x, me.y, me.z};
-      for (int a = 0; a < 3; ++a) {
-        const bool lo_b = anchor[a] == 0, hi_b = anchor[a] + eb == (1 << kDepth);
-        if (lo_b || hi_b) {
-          const int b1 = (a + 1) % 3, b2 = (a + 2) % 3;
-          for (int t = tid; t < 169 * 3; t += blockDim.x) {
-            const int v1 = t % 13 - 3, v2 = (t / 13) % 13 - 3, m = t / 169 + 1;
-            const bool ext1 = (anchor[b1] == 0 && v1 < 0) || (anchor[b1] + eb == (1 << kDepth) && v1 > 6);
-            const bool ext2 = (anchor[b2] == 0 && v2 < 0) || (anchor[b2] + eb == (1 << kDepth) && v2 > 6);
-            if ((b1 > a && ext1) || (b2 > a && ext2)) continue;
-            int idx[3];
-            idx[b1] = v1;
-            idx[b2] = v2;
-            const int str = a == 0 ? 1 : (a == 1 ? 13 : 169);
-            idx[a] = 0;
-            const int base = (idx[0] + 3) + 13 * (idx[1] + 3) + 169 * (idx[2] + 3);
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-              if (lo_b) {
-                double v = 0.0;
-                for (int qq = 0; qq < 4; ++qq) v = fma(c_E[m][qq], S.T[f][base + qq * str], v);
-                S.T[f][base - m * str] = v;
-              }
-              if (hi_b) {
-                double v = 0.0;
-                for (int qq = 0; qq < 4; ++qq) v = fma(c_E[m][qq], S.T[f][base + (6 - qq) * str], v);
-                S.T[f][base + (6 + m) * str] = v;
-              }
-            }
-          }
-        }
-        __syncthreads();
-      }
-    }
+    if (A.bc == LTS_BC_EXACT)
+      fill_exact<NF>(S, A, me, eb, lc.dt);
+    else
+      fill_extrapolated<NF>(S, me, eb);
   }
   __syncthreads();
 
-  // 5. right-hand side on the 7^3 interior, stage write, fused RK update
+  // 6. right-hand side on the 7^3 interior; stage, next stage input, fused RK update
   if (tid < kNV) {
     const int i = tid % 7, j = (tid / 7) % 7, k = tid / 49;
     const int c0 = (i + 3) + 13 * (j + 3) + 169 * (k + 3);
-    const double kos = A.ko_sigma / (64.0 * h);
     double kv[NF];
     if (A.pde == LTS_PDE_ADVECTION) {
       const double* T = S.T[0];
       const double u0 = T[c0];
-      double d1s = 0.0, P1 = 0.0, P2 = 0.0, P3 = 0.0;
-      const int st[3] = {1, 13, 169};
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const double m1 = T[c0 - st[a]], p1 = T[c0 + st[a]];
-        const double m2 = T[c0 - 2 * st[a]], p2 = T[c0 + 2 * st[a]];
-        const double m3 = T[c0 - 3 * st[a]], p3 = T[c0 + 3 * st[a]];
-        const double d1 = fma(8.0, p1 - m1, m2 - p2);          // 12 h D1
-        d1s = fma(A.adv[a], d1, d1s);
-        P1 += m1 + p1;
-        P2 += m2 + p2;
-        P3 += m3 + p3;
-      }
-      const double ko = fma(-20.0 * 3.0, u0, fma(15.0, P1, fma(-6.0, P2, P3)));
-      kv[0] = fma(kos, ko, -d1s / (12.0 * h));
+      // symmetric pair sums at distance 1, 2, 3 (Kreiss-Oliger) and the D1 differences
+      const double P1 = (T[c0 - 1] + T[c0 + 1]) + (T[c0 - 13] + T[c0 + 13]) + (T[c0 - 169] + T[c0 + 169]);
+      const double P2 = (T[c0 - 2] + T[c0 + 2]) + (T[c0 - 26] + T[c0 + 26]) + (T[c0 - 338] + T[c0 + 338]);
+      const double P3 = (T[c0 - 3] + T[c0 + 3]) + (T[c0 - 39] + T[c0 + 39]) + (T[c0 - 507] + T[c0 + 507]);
+      double d1s = A.adv[0] * fma(8.0, T[c0 + 1] - T[c0 - 1], T[c0 - 2] - T[c0 + 2]);
+      d1s = fma(A.adv[1], fma(8.0, T[c0 + 13] - T[c0 - 13], T[c0 - 26] - T[c0 + 26]), d1s);
+      d1s = fma(A.adv[2], fma(8.0, T[c0 + 169] - T[c0 - 169], T[c0 - 338] - T[c0 + 338]), d1s);
+      const double ko = fma(-60.0, u0, fma(15.0, P1, fma(-6.0, P2, P3)));
+      kv[0] = fma(lc.kos, ko, -lc.inv12h * d1s);
     } else {
       const double* Tc = S.T[0];
       const double* Tp = S.T[NF - 1];
       const double c0v = Tc[c0], f0v = Tp[c0];
-      double C1 = 0.0, C2 = 0.0, C3 = 0.0, F1 = 0.0, F2 = 0.0, F3 = 0.0;
-      const int st[3] = {1, 13, 169};
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        C1 += Tc[c0 - st[a]] + Tc[c0 + st[a]];
-        C2 += Tc[c0 - 2 * st[a]] + Tc[c0 + 2 * st[a]];
-        C3 += Tc[c0 - 3 * st[a]] + Tc[c0 + 3 * st[a]];
-        F1 += Tp[c0 - st[a]] + Tp[c0 + st[a]];
-        F2 += Tp[c0 - 2 * st[a]] + Tp[c0 + 2 * st[a]];
-        F3 += Tp[c0 - 3 * st[a]] + Tp[c0 + 3 * st[a]];
-      }
-      const double lap = fma(-90.0, c0v, fma(16.0, C1, -C2)) / (12.0 * h * h);
+      const double C1 = (Tc[c0 - 1] + Tc[c0 + 1]) + (Tc[c0 - 13] + Tc[c0 + 13]) + (Tc[c0 - 169] + Tc[c0 + 169]);
+      const double C2 = (Tc[c0 - 2] + Tc[c0 + 2]) + (Tc[c0 - 26] + Tc[c0 + 26]) + (Tc[c0 - 338] + Tc[c0 + 338]);
+      const double C3 = (Tc[c0 - 3] + Tc[c0 + 3]) + (Tc[c0 - 39] + Tc[c0 + 39]) + (Tc[c0 - 507] + Tc[c0 + 507]);
+      const double F1 = (Tp[c0 - 1] + Tp[c0 + 1]) + (Tp[c0 - 13] + Tp[c0 + 13]) + (Tp[c0 - 169] + Tp[c0 + 169]);
+      const double F2 = (Tp[c0 - 2] + Tp[c0 + 2]) + (Tp[c0 - 26] + Tp[c0 + 26]) + (Tp[c0 - 338] + Tp[c0 + 338]);
+      const double F3 = (Tp[c0 - 3] + Tp[c0 + 3]) + (Tp[c0 - 39] + Tp[c0 + 39]) + (Tp[c0 - 507] + Tp[c0 + 507]);
+      const double lap = fma(-90.0, c0v, fma(16.0, C1, -C2)) * lc.inv12h2;
       const double koc = fma(-60.0, c0v, fma(15.0, C1, fma(-6.0, C2, C3)));
       const double kop = fma(-60.0, f0v, fma(15.0, F1, fma(-6.0, F2, F3)));
-      kv[0] = fma(kos, koc, f0v);
-      kv[NF - 1] = fma(kos, kop, lap);
+      kv[0] = fma(lc.kos, koc, f0v);
+      kv[NF - 1] = fma(lc.kos, kop, lap);
       if (A.bc == LTS_BC_RADIATIVE && touches) {
         const int P6[3] = {6 * me.x + i * eb, 6 * me.y + j * eb, 6 * me.z + k * eb};
         const bool on_bnd = P6[0] == 0 || P6[1] == 0 || P6[2] == 0 || P6[0] == kLatt6 || P6[1] == kLatt6 ||
                             P6[2] == kLatt6;
-        if (on_bnd) {
-          const double x[3] = {lattice_to_x(A.lo, A.ext, P6[0]), lattice_to_x(A.lo, A.ext, P6[1]),
-                               lattice_to_x(A.lo, A.ext, P6[2])};
-          const double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-#pragma unroll
-          for (int f = 0; f < NF; ++f) {
-            const double* T = S.T[f];
-            double xd = 0.0;
-            for (int a = 0; a < 3; ++a) {
-              const double d1 =
-                  fma(8.0, T[c0 + st[a]] - T[c0 - st[a]], T[c0 - 2 * st[a]] - T[c0 + 2 * st[a]]) / (12.0 * h);
-              xd = fma(x[a], d1, xd);
-            }
-            kv[f] = -(xd + (f == 0 ? 1.0 : 2.0) * T[c0]) / r;
-          }
-        }
+        if (on_bnd) radiative_rhs<NF>(S, A, c0, P6, lc.inv12h, kv);
       }
     }
     const long long node = (long long)b * kNV + tid;
+    const double* ucur = A.u[(A.cur_mask >> lb) & 1];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) A.K[(long long)s * kstride + f * A.fstride + node] = kv[f];
-    if (A.write_update && s == p - 1) {
-      const int cur = (A.cur_mask >> lb) & 1;
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        const long long o = f * A.fstride + node;
+    for (int f = 0; f < NF; ++f) {
+      const long long o = f * A.fstride + node;
+      A.K[(long long)s * kstride + o] = kv[f];
+      if (s < p - 1) {
+        // stage input of the next stage: u + dt sum_j a[s+1][j] k_j
         double acc = 0.0;
-        for (int q = 0; q < p - 1; ++q) acc = fma(tab.w[q], A.K[(long long)q * kstride + o], acc);
-        acc = fma(tab.w[p - 1], kv[f], acc);
-        A.u[cur ^ 1][o] = fma(dtb, acc, A.u[cur][o]);
+        for (int q = 0; q < A.next.n; ++q)
+          acc = fma(A.next.w[q], A.next.j[q] == s ? kv[f] : A.K[(long long)A.next.j[q] * kstride + o], acc);
+        A.Uout[o] = fma(lc.dt, acc, ucur[o]);
+      } else if (A.write_update) {
+        double acc = 0.0;
+        for (int q = 0; q < p - 1; ++q) acc = fma(A.w[q], A.K[(long long)q * kstride + o], acc);
+        acc = fma(A.w[p - 1], kv[f], acc);
+        A.u[((A.cur_mask >> lb) & 1) ^ 1][o] = fma(lc.dt, acc, ucur[o]);
       }
     }
   }
@@ -625,7 +643,7 @@ __global__ void __launch_bounds__(128) sync_hanging_kernel(SyncArgs A) {
     const double* vs = A.vb[(A.sel_mask >> so.w) & 1];
     double* vd = A.vb[(A.sel_mask >> me.w) & 1];
     for (int f = 0; f < A.nf; ++f)
-      vd[f * A.fstride + (long long)b * kNV + n] = interp_tensor(vs + f * A.fstride + (long long)src * kNV, rx, ry, rz);
+      vd[f * A.fstride + (long long)b * kNV + n] = interp_tensor(vs + f * A.fstride + (long long)src * kNV, c_W, rx, ry, rz);
   }
 }
 

@@ -22,24 +22,45 @@ struct IcParams {
 
 // One RK stage over the active octants [first, n) (Alg. 2 compute_stage, or
 // Alg. 1 when gts != 0).
+// constants of one refinement level, computed on the host
+struct LevelConst {
+  double dt;       // step of the level (dt_f for every level under GTS)
+  double inv12h;   // 1 / (12 h), h the node spacing
+  double inv12h2;  // 1 / (12 h^2)
+  double kos;      // Kreiss-Oliger factor sigma / (64 h)
+};
+
+// a weighted sum of RK stages: sum_t w[t] K_j[t]
+struct StageTerms {
+  int n;
+  int j[4];
+  double w[4];
+};
+
 struct StageArgs {
   DevTree tree;
   double* u[2];          // double-buffered state [nf][N][343]; level l uses u[(cur_mask >> l) & 1]
   double* K;             // RK stages [p][nf][N][343]
+  const double* Uin;     // stage inputs of this stage (stage >= 1), [nf][N][343]
+  double* Uout;          // stage inputs of the next stage, written by the epilogue
   long long fstride;     // N * 343
-  int nf, p, scheme, stage;
+  int nf, p, stage;
   int first;             // first active octant (level order)
   int lstar, lmax;       // coarsest active level, finest level
   unsigned cur_mask;
-  int gts;               // 1: every octant steps with dt_f, no correction, no fused update
+  int gts;               // 1: every octant steps with dt_f and the same-level tableau
   int write_update;      // 1: the last stage also writes u_new into the other buffer
-  double dt_f, t_b;      // finest step; start time of the steps in this substep
+  double t_b;            // start time of the steps in this substep
   double lo, ext;        // domain [lo, lo + ext]^3
   int pde, bc, ic;
   double adv[3];
-  double ko_sigma;
+  LevelConst lc[32];
+  StageTerms om[4];      // this stage's correction terms per relation (eqs. fc_1, fc_2)
+  StageTerms next;       // a[stage+1][.] terms of the next stage input
+  double w[4];           // RK weights
+  double gamma[4];       // gamma[stage][.] for exact boundary data
   IcParams icp;
-  int* err;              // device error word: bit 0 source coordinate out of range, bit 1 balance violated
+  int* err;              // device error word: bit 0 source coordinate out of range
 };
 
 struct SyncArgs {
