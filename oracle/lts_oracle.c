@@ -1259,6 +1259,9 @@ void orc_set_initial(orc_solver* s, double t0) {
       if (s->nf == 2) fld(s->u, s, 1, b)[n] = v1;
     }
   }
+  /* the state at a synchronised time is the unzip of its shared-node values
+   * (Sec. 3.3, Fig. dg_to_cg): hanging nodes take the coarse interpolant */
+  orc_sync(s, s->u);
   memcpy(s->u_start, s->u, s->fsz * (size_t)s->nf * sizeof(double));
   memset(s->K, 0, s->fsz * (size_t)s->nf * (size_t)s->p * sizeof(double));
   s->t_macro = t0;
@@ -1267,7 +1270,8 @@ void orc_set_initial(orc_solver* s, double t0) {
 
 void orc_set_state(orc_solver* s, const double* u, double t0) {
   memcpy(s->u, u, s->fsz * (size_t)s->nf * sizeof(double));
-  memcpy(s->u_start, u, s->fsz * (size_t)s->nf * sizeof(double));
+  orc_sync(s, s->u);
+  memcpy(s->u_start, s->u, s->fsz * (size_t)s->nf * sizeof(double));
   memset(s->K, 0, s->fsz * (size_t)s->nf * (size_t)s->p * sizeof(double));
   s->t_macro = t0;
   s->n_sub = 0;

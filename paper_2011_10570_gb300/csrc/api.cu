@@ -517,6 +517,9 @@ lts_status lts_set_initial(lts_plan* P, double t0) {
   CK(ltsoct::launch_init(a, P->stream), "init kernel launch");
   P->launches++;
   CK(cudaMemsetAsync(P->d_K, 0, size_t(P->N) * kNV * sizeof(double) * P->nf * P->p, P->stream), "memset");
+  // a synchronised state is the unzip of its shared-node values (hanging nodes interpolated)
+  lts_status st = sync_fields(P, P->d_u[0], P->d_u[0], 0u);
+  if (st != LTS_OK) return st;
   P->cur_mask = 0;
   P->t_macro = t0;
   P->n_sub = 0;
@@ -529,6 +532,8 @@ lts_status lts_set_state(lts_plan* P, const double* u, double t0, int on_device)
   CK(cudaMemcpyAsync(P->d_u[0], u, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, P->stream),
      "lts_set_state copy");
   CK(cudaMemsetAsync(P->d_K, 0, bytes * P->p, P->stream), "memset");
+  lts_status st = sync_fields(P, P->d_u[0], P->d_u[0], 0u);
+  if (st != LTS_OK) return st;
   P->cur_mask = 0;
   P->t_macro = t0;
   P->n_sub = 0;

@@ -216,6 +216,8 @@ template <int NF>
 struct StageSmem {
   double T[NF][kNT];         // padded tiles
   double V[NF][kNV];         // stage inputs of one coarser source (interpolation)
+  double X1[13 * 49];        // interpolated along x: [rx][z][y]
+  double X2[13 * 13 * 7];    // then along y: [rx][ry][z]
   double W[13][7];           // Lagrange weights
   StageTerms om[4];          // correction terms of this stage per relation
   int src[kNT];
@@ -223,6 +225,7 @@ struct StageSmem {
   NbrView nv;
   int nlev[27];
   int coarse[8];
+  int range[8][4];           // per coarser source: min/max of rx and ry over its interpolated points
   int ncoarse;
 };
 
@@ -341,7 +344,12 @@ __global__ void __launch_bounds__(kThreads) stage_kernel(StageArgs A) {
       if (!seen) S.coarse[n++] = e;
     }
     S.ncoarse = n;
+    for (int c = 0; c < 8; ++c) {
+      S.range[c][0] = S.range[c][2] = 12;
+      S.range[c][1] = S.range[c][3] = 0;
+    }
   }
+  __syncthreads();
 
   // 1. source of every padded point (coarsest leaf containing it, then smallest Morton key)
   for (int q = tid; q < kNT; q += blockDim.x) {
@@ -366,6 +374,16 @@ __global__ void __launch_bounds__(kThreads) stage_kernel(StageArgs A) {
           code = kExterior;
         } else {
           code = unsigned(rx) | unsigned(ry) << 4 | unsigned(rz) << 8 | unsigned(so.w - lb + 1) << 12;
+          if ((rx | ry | rz) & 1) {
+            // interpolated point: widen the sub-box of its coarser source
+            for (int c = 0; c < S.ncoarse; ++c)
+              if (S.coarse[c] == src) {
+                atomicMin(&S.range[c][0], rx);
+                atomicMax(&S.range[c][1], rx);
+                atomicMin(&S.range[c][2], ry);
+                atomicMax(&S.range[c][3], ry);
+              }
+          }
         }
       }
     }
@@ -424,7 +442,8 @@ __global__ void __launch_bounds__(kThreads) stage_kernel(StageArgs A) {
     }
   }
 
-  // 4. interpolation from coarser sources (Fig. unzip: coarse -> fine)
+  // 4. interpolation from coarser sources (Fig. unzip: coarse -> fine), sum-factorised
+  //    over the sub-box of half-node positions the points need: x, then y, then z
   const int ncoarse = S.ncoarse;
   for (int c = 0; c < ncoarse; ++c) {
     const int src = S.coarse[c];
@@ -432,6 +451,9 @@ __global__ void __launch_bounds__(kThreads) stage_kernel(StageArgs A) {
     const int rel = ls >= A.lstar ? 2 : 3;
     const double* ub = A.u[((A.cur_mask >> ls) & 1) ^ (rel == 3 ? 1 : 0)];
     const double* cdirect = s == 0 ? A.u[(A.cur_mask >> ls) & 1] : A.Uin;
+    const int rx0 = S.range[c][0], nrx = S.range[c][1] - rx0 + 1;
+    const int ry0 = S.range[c][2], nry = S.range[c][3] - ry0 + 1;
+    if (nrx <= 0 || nry <= 0) continue;  // only even points: all copied already
     __syncthreads();
     for (int t = tid; t < NF * kNV; t += blockDim.x) {
       const int f = t / kNV, n = t - f * kNV;
@@ -440,14 +462,53 @@ __global__ void __launch_bounds__(kThreads) stage_kernel(StageArgs A) {
                         : corrected_value(ub + f * A.fstride + off, A.K + f * A.fstride + off, kstride,
                                           S.om[rel], A.lc[ls].dt);
     }
-    __syncthreads();
-    for (int q = tid; q < kNT; q += blockDim.x) {
-      if (S.src[q] != src) continue;
-      const unsigned code = S.code[q];
-      const int rx = code & 15, ry = (code >> 4) & 15, rz = (code >> 8) & 15;
-      if (!((rx | ry | rz) & 1)) continue;
+    for (int f = 0; f < NF; ++f) {
+      __syncthreads();
+      for (int t = tid; t < nrx * 49; t += blockDim.x) {
+        const int rx = rx0 + t / 49, yz = t % 49;  // yz = y + 7 z
+        const double* v = S.V[f] + 7 * yz;
+        double acc;
+        if (rx & 1) {
+          acc = 0.0;
 #pragma unroll
-      for (int f = 0; f < NF; ++f) S.T[f][q] = interp_tensor(S.V[f], S.W, rx, ry, rz);
+          for (int a = 0; a < 7; ++a) acc = fma(S.W[rx][a], v[a], acc);
+        } else {
+          acc = v[rx >> 1];
+        }
+        S.X1[t] = acc;
+      }
+      __syncthreads();
+      for (int t = tid; t < nrx * nry * 7; t += blockDim.x) {
+        const int z = t % 7, ryi = (t / 7) % nry, rxi = t / (7 * nry);
+        const int ry = ry0 + ryi;
+        const double* x1 = S.X1 + rxi * 49 + 7 * z;  // [y] for fixed rx, z
+        double acc;
+        if (ry & 1) {
+          acc = 0.0;
+#pragma unroll
+          for (int bb = 0; bb < 7; ++bb) acc = fma(S.W[ry][bb], x1[bb], acc);
+        } else {
+          acc = x1[ry >> 1];
+        }
+        S.X2[t] = acc;
+      }
+      __syncthreads();
+      for (int q = tid; q < kNT; q += blockDim.x) {
+        if (S.src[q] != src) continue;
+        const unsigned code = S.code[q];
+        const int rx = code & 15, ry = (code >> 4) & 15, rz = (code >> 8) & 15;
+        if (!((rx | ry | rz) & 1)) continue;
+        const double* x2 = S.X2 + ((rx - rx0) * nry + (ry - ry0)) * 7;
+        double acc;
+        if (rz & 1) {
+          acc = 0.0;
+#pragma unroll
+          for (int cc = 0; cc < 7; ++cc) acc = fma(S.W[rz][cc], x2[cc], acc);
+        } else {
+          acc = x2[rz >> 1];
+        }
+        S.T[f][q] = acc;
+      }
     }
   }
   __syncthreads();

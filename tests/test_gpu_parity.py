@@ -32,6 +32,16 @@ def rel_linf(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
 
 
+def stage_err(plan, sol, gt, j):
+    """error of RK stage j as its contribution to the state: dt_l * |dK| against max|u|
+    (a stage is a time derivative; FD rounding is amplified by 1/h^2 in it)"""
+    st = plan.stats()
+    _, lev = gt.export()
+    dtl = st["dt_finest"] * 2.0 ** (st["l_max"] - lev)
+    dk = np.abs(plan.get_stage(j) - sol.stage(j)) * dtl[None, :, None]
+    return dk.max() / np.abs(sol.state()).max()
+
+
 def both(lt, orc, w):
     gt = lt.Octree(w["spec"])
     plan = lt.Plan(gt, w["prob"])
@@ -87,7 +97,7 @@ def test_lts_fields_match_oracle(lt, orc, name, mk):
         err = rel_linf(plan.get_state(), sol.state())
         assert err <= TOL, (name, chunk, err)
     for j in range(st["p"]):
-        assert rel_linf(plan.get_stage(j), sol.stage(j)) <= TOL
+        assert stage_err(plan, sol, gt, j) <= TOL
 
 
 @pytest.mark.parametrize("name,mk", SMALL[:4])
@@ -266,7 +276,10 @@ def test_full_wave_first_substeps_sampled(lt, orc, full_wave):
     assert err(u_gpu[:, idx1], u1[:, idx1], u_gpu) <= TOL
     # levels 4..8 stepped once in substep 0 and then rested
     assert err(u_gpu[:, idx0], u0[:, idx0], u_gpu) <= TOL
+    st = plan.stats()
+    dtl = st["dt_finest"] * 2.0 ** (st["l_max"] - lev)
     for j in range(4):
         kj = sol.stage(j)
-        assert err(k_gpu[j][:, idx1], kj[:, idx1], k_gpu[j]) <= TOL
-        assert err(k_gpu[j][:, idx0], kj[:, idx0], k_gpu[j]) <= TOL
+        for idx in (idx1, idx0):
+            dk = np.abs(k_gpu[j][:, idx] - kj[:, idx]) * dtl[None, idx, None]
+            assert dk.max() / np.abs(u_gpu).max() <= TOL
