@@ -168,6 +168,20 @@ lts_status lts_export_o2o(const lts_plan* plan, int32_t* out);
 lts_status lts_export_pad_map(lts_plan* plan, const int32_t* octs, int64_t n, int32_t* src, int32_t* r);
 /* Same for the 343 nodes of each listed octant (the shared-node owners). */
 lts_status lts_export_node_map(lts_plan* plan, const int32_t* octs, int64_t n, int32_t* src, int32_t* r);
+/* Allocation-free variant of lts_export_pad_map (the paper has no counterpart:
+ * this is a service of the library).  For callers that must not allocate device
+ * memory while they run -- e.g. a process whose device memory is all reserved up
+ * front by its own pool, or a loop that cannot afford an allocator call and the
+ * synchronisation it may bring.  Results are staged in one fixed device array
+ * inside the library (about 1.1 MB, held by every GPU that loads the library
+ * until the process exits), so at most 32 octants per call (more: LTS_EINVAL).
+ * The array's device address is looked up on the first call on each device, with
+ * that device current; make that first call outside any stream capture.  Every
+ * call shares the array and overwrites what the last call left there; calls whose
+ * GPU work overlaps (other threads, other plans, other streams) race on it.  The
+ * octant list, src[n][2197] and r[n][2197][3] are host buffers as above; the call
+ * synchronises the plan's stream. */
+lts_status lts_export_pad_map_static(lts_plan* plan, const int32_t* octs, int64_t n, int32_t* src, int32_t* r);
 
 /* ---- measurement ------------------------------------------------------------------- */
 /* When on, every stage-kernel launch is bracketed by CUDA events on the plan's

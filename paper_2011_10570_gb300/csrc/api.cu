@@ -673,6 +673,38 @@ lts_status lts_export_node_map(lts_plan* P, const int32_t* octs, int64_t n, int3
   return export_map(P, octs, n, src, r, 1);
 }
 
+// Same result as lts_export_pad_map, staged through the library's fixed device
+// array instead of memory allocated per call (see include/ltsoct.h).
+lts_status lts_export_pad_map_static(lts_plan* P, const int32_t* octs, int64_t n, int32_t* src, int32_t* r) {
+  if (!P || n < 0 || (n && (!octs || !src || !r))) return fail(LTS_EINVAL, "lts_export_pad_map_static: bad argument");
+  if (n > ltsoct::kStaticMapOctants)
+    return fail(LTS_EINVAL, "lts_export_pad_map_static: at most " + std::to_string(ltsoct::kStaticMapOctants) +
+                                " octants per call (got " + std::to_string(n) + ")");
+  for (int64_t i = 0; i < n; ++i)
+    if (octs[i] < 0 || octs[i] >= P->N) return fail(LTS_EINVAL, "lts_export_pad_map_static: octant index out of range");
+  if (!n) return LTS_OK;
+  int* scratch = nullptr;
+  CK(ltsoct::static_map_scratch(&scratch), "lts_export_pad_map_static: staging area address");
+  const int K = ltsoct::kStaticMapOctants;
+  int* d_list = scratch;
+  int* d_src = scratch + K;
+  int* d_r = d_src + size_t(K) * ltsoct::kNT;
+  CK(cudaMemcpyAsync(d_list, octs, sizeof(int) * n, cudaMemcpyHostToDevice, P->stream), "copy");
+  ltsoct::MapArgs a{};
+  a.tree = dev_tree(P);
+  a.octs = d_list;
+  a.count = int(n);
+  a.nodes = 0;
+  a.src = d_src;  // every element the copies below read is written by the kernel
+  a.r = d_r;
+  CK(ltsoct::launch_maps(a, P->stream), "map kernel launch");
+  P->launches++;
+  CK(cudaMemcpyAsync(src, d_src, sizeof(int) * n * ltsoct::kNT, cudaMemcpyDeviceToHost, P->stream), "copy");
+  CK(cudaMemcpyAsync(r, d_r, sizeof(int) * n * ltsoct::kNT * 3, cudaMemcpyDeviceToHost, P->stream), "copy");
+  CK(cudaStreamSynchronize(P->stream), "cudaStreamSynchronize");
+  return LTS_OK;
+}
+
 lts_status lts_set_profiling(lts_plan* P, int on) {
   if (!P) return fail(LTS_EINVAL, "lts_set_profiling: null plan");
   P->profiling = on != 0;

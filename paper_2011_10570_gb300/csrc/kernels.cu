@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <climits>
+#include <mutex>
 
 #include "kernels.cuh"
 
@@ -806,6 +807,35 @@ cudaError_t launch_maps(const MapArgs& a, cudaStream_t s) {
   if (a.count <= 0) return cudaSuccess;
   maps_kernel<<<a.count, 256, 0, s>>>(a);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Fixed device staging area of lts_export_pad_map_static: room for the octant
+// list and the padding sources of kStaticMapOctants octants.  It lives in the
+// library image, so every GPU that loads the library holds it (about 1.1 MB)
+// until the process exits, and no call allocates.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) int g_static_map_scratch[kStaticMapOctants * (1 + 4 * kNT)];
+
+// Device address of the staging area on the current device.  Host code cannot
+// use the symbol itself (it names a host-side stand-in), so the address is
+// looked up once per device, with that device current, and cached.
+cudaError_t static_map_scratch(int** out) {
+  static std::mutex mu;
+  static int* cached[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!cached[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_static_map_scratch);
+    if (e != cudaSuccess) return e;
+    cached[dev] = static_cast<int*>(ptr);
+  }
+  *out = cached[dev];
+  return cudaSuccess;
 }
 
 }  // namespace ltsoct

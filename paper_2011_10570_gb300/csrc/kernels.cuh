@@ -112,4 +112,8 @@ cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
 cudaError_t launch_init(const InitArgs& a, cudaStream_t s);
 cudaError_t launch_maps(const MapArgs& a, cudaStream_t s);
 
+// allocation-free padding-map export: largest octant list one call accepts
+constexpr int kStaticMapOctants = 32;
+cudaError_t static_map_scratch(int** out);
+
 }  // namespace ltsoct

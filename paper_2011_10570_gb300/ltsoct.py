@@ -51,7 +51,7 @@ class Stats(C.Structure):
 EXPORTS = ["octree_build", "octree_size", "octree_export", "octree_destroy", "lts_plan_create", "lts_plan_destroy",
            "lts_plan_stats", "lts_set_initial", "lts_set_state", "lts_get_state", "lts_get_stage",
            "lts_run_substeps", "lts_advance", "gts_steps", "gts_advance", "lts_export_o2o", "lts_export_pad_map",
-           "lts_export_node_map", "lts_set_profiling", "lts_kernel_stats", "lts_strerror", "lts_last_error"]
+           "lts_export_node_map", "lts_export_pad_map_static", "lts_set_profiling", "lts_kernel_stats", "lts_strerror", "lts_last_error"]
 
 
 def library_path():
@@ -88,6 +88,7 @@ def load(path=None):
         "lts_export_o2o": ([vp, i32p], st),
         "lts_export_pad_map": ([vp, i32p, i64, i32p, i32p], st),
         "lts_export_node_map": ([vp, i32p, i64, i32p, i32p], st),
+        "lts_export_pad_map_static": ([vp, i32p, i64, i32p, i32p], st),
         "lts_set_profiling": ([vp, C.c_int], st),
         "lts_kernel_stats": ([vp, C.POINTER(i64), C.POINTER(C.c_double), C.POINTER(C.c_double),
                               C.POINTER(C.c_double), C.POINTER(i64), C.c_int], st),
@@ -271,6 +272,15 @@ class Plan:
         src = np.zeros((len(octs), 2197), np.int32)
         r = np.zeros((len(octs), 2197, 3), np.int32)
         _check(_lib.lts_export_pad_map(self.h, _i32(octs), len(octs), _i32(src), _i32(r)), "lts_export_pad_map")
+        return src, r
+
+    def export_pad_map_static(self, octs):
+        """lts_export_pad_map without per-call device allocation (at most 32 octants)."""
+        octs = np.ascontiguousarray(octs, dtype=np.int32)
+        src = np.zeros((len(octs), 2197), np.int32)
+        r = np.zeros((len(octs), 2197, 3), np.int32)
+        _check(_lib.lts_export_pad_map_static(self.h, _i32(octs), len(octs), _i32(src), _i32(r)),
+               "lts_export_pad_map_static")
         return src, r
 
     def export_node_map(self, octs):
