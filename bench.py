@@ -98,9 +98,10 @@ def dist_setup(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     pg = None
     if world > 1:
+        # replicas only: the collectives are a timing barrier and a max over ranks
+        # of one float, on the host (gloo), for both arms
         import torch.distributed as dist
-        backend = "gloo" if args.impl == "reference" else "nccl"
-        dist.init_process_group(backend=backend)
+        dist.init_process_group(backend="gloo")
         pg = dist
     return world, rank, local, pg
 
@@ -149,7 +150,8 @@ def run_reference(args, w, world, rank, pg):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w["name"], "octants": n, "levels": "4..9", "fields": 2, "rk": 4,
+        "config": {"workload": w["name"], "octants": n, "levels": "%d..%d" % (w["spec"]["l_min"], w["spec"]["l_max"]),
+                   "fields": 2, "rk": 4,
                    "parallelism": "replicas", "l2": "state arrays (847 MB each) larger than L2"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -165,10 +167,13 @@ def main():
     ap.add_argument("--impl", default="lts", choices=["lts", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--gts", action="store_true", help="also time GTS over the same physical time")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--lmax", type=int, default=9,
+                    help="finest level of the wave workload (9: the benchmark configuration; 8: the profiling case)")
     args = ap.parse_args()
 
     from paper_2011_10570_gb300 import workloads
-    w = workloads.wave_shell()
+    w = workloads.wave_shell(l_max=args.lmax)
     world, rank, local, pg = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, w, world, rank, pg)
@@ -215,7 +220,7 @@ def main():
     ks = plan.kernel_stats(reset=True)
     plan.set_profiling(False)
     if pg:
-        t = torch.tensor([ms], device="cuda")
+        t = torch.tensor([ms], dtype=torch.float64)
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         ms = float(t.item())
     value = world * args.steps * work_nodes / (ms / 1e3)
@@ -226,7 +231,7 @@ def main():
     out_t = torch.empty((st["nf"], n, 343), dtype=torch.float64, pin_memory=True)
     host, out = host_t.numpy(), out_t.numpy()
     plan.get_state(host)
-    e2e_steps = max(1, args.steps)
+    e2e_steps = 0 if args.no_e2e else max(1, args.steps)
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
@@ -236,12 +241,12 @@ def main():
         plan.run_substeps(nsub)
         plan.get_state(out)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max(time.perf_counter() - t0, 1e-30)
     if pg:
-        t = torch.tensor([e2e_s], device="cuda")
+        t = torch.tensor([e2e_s], dtype=torch.float64)
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e_value = world * e2e_steps * work_nodes / e2e_s
+    e2e_value = world * e2e_steps * work_nodes / e2e_s if e2e_steps else None
     state_bytes = host.nbytes
 
     # GTS over the same physical time (2^L global steps per macro step)

@@ -49,6 +49,13 @@ struct lts_plan {
   double* d_u[2] = {nullptr, nullptr};
   double* d_K = nullptr;
   double* d_U[2] = {nullptr, nullptr};  // stage inputs of the current and the next stage
+  std::vector<int32_t> up_list;         // octants with finer neighbours (coarser sources), level order
+  int64_t up_off[34] = {};              // per level ranges in up_list
+  std::vector<int32_t> up_box, up_slot;
+  int* d_up_list = nullptr;
+  int* d_up_box = nullptr;
+  int* d_up_slot = nullptr;
+  double* d_up = nullptr;               // prolonged stage inputs [slot][nf][2197]
   int* d_err = nullptr;
   int64_t launches = 0;               // every kernel launched by the plan
   size_t bytes = 0;
@@ -194,7 +201,40 @@ ltsoct::StageArgs stage_args(const lts_plan* P, int stage, int first, int lstar,
   }
   for (int i = 0; i < 32; ++i) a.icp.v[i] = P->prob.ic_params[i];
   a.err = P->d_err;
+  a.up = P->d_up;
+  a.up_slot = P->d_up_slot;
   return a;
+}
+
+// prolongation of the coarser sources needed by the octants stepping in this stage:
+// octants of levels [max(l* - 1, l_min), l_max - 1] with finer neighbours
+lts_status launch_prolong_for(lts_plan* P, const ltsoct::StageArgs& sa, int lstar) {
+  const int lo = std::max(lstar - 1, P->lmin), hi = P->lmax - 1;
+  if (hi < lo) return LTS_OK;
+  const int64_t first = P->up_off[lo], count = P->up_off[hi + 1] - first;
+  if (count <= 0) return LTS_OK;
+  ltsoct::ProlongArgs a{};
+  a.tree = sa.tree;
+  a.list = P->d_up_list + first;
+  a.count = int(count);
+  a.box = P->d_up_box;
+  a.up_slot = P->d_up_slot;
+  a.up = P->d_up;
+  a.u[0] = sa.u[0];
+  a.u[1] = sa.u[1];
+  a.K = sa.K;
+  a.Uin = sa.Uin;
+  a.fstride = sa.fstride;
+  a.nf = sa.nf;
+  a.stage = sa.stage;
+  a.lstar = lstar;
+  a.cur_mask = sa.cur_mask;
+  a.gts = sa.gts;
+  for (int l = 0; l < 32; ++l) a.lc[l] = sa.lc[l];
+  for (int r = 0; r < 4; ++r) a.om[r] = sa.om[r];
+  CK(ltsoct::launch_prolong(a, P->stream), "prolongation kernel launch");
+  P->launches++;
+  return LTS_OK;
 }
 
 lts_status launch_stage_timed(lts_plan* P, const ltsoct::StageArgs& a, int count) {
@@ -225,7 +265,10 @@ lts_status lts_substep(lts_plan* P) {
   const int first = int(P->off[lstar]);
   const int count = int(P->N - first);
   for (int s = 0; s < P->p; ++s) {
-    lts_status st = launch_stage_timed(P, stage_args(P, s, first, lstar, 0), count);
+    const ltsoct::StageArgs sa = stage_args(P, s, first, lstar, 0);
+    lts_status st = launch_prolong_for(P, sa, lstar);
+    if (st != LTS_OK) return st;
+    st = launch_stage_timed(P, sa, count);
     if (st != LTS_OK) return st;
   }
   // the active levels completed a step: their state now lives in the other buffer
@@ -243,7 +286,10 @@ lts_status lts_substep(lts_plan* P) {
 lts_status gts_step(lts_plan* P) {
   const long long kstride = (long long)P->nf * P->N * kNV;
   for (int s = 0; s < P->p; ++s) {
-    lts_status st = launch_stage_timed(P, stage_args(P, s, 0, P->lmin, 1), int(P->N));
+    const ltsoct::StageArgs sa = stage_args(P, s, 0, P->lmin, 1);
+    lts_status st = launch_prolong_for(P, sa, P->lmin);
+    if (st != LTS_OK) return st;
+    st = launch_stage_timed(P, sa, int(P->N));
     if (st != LTS_OK) return st;
     double* Ks = P->d_K + s * kstride;
     st = sync_fields(P, Ks, Ks, 0u);
@@ -414,6 +460,31 @@ lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_
     while (P->hang_off[l + 1] < int64_t(P->hang.size()) && P->octs[P->hang[P->hang_off[l + 1]]].l == l)
       P->hang_off[l + 1]++;
   }
+  // coarser sources: octants with a split neighbour box; the box of half-node
+  // positions their finer neighbours read lies within 3 half-node units of the
+  // faces, edges and corners those neighbours touch
+  P->up_slot.assign(P->N, -1);
+  for (int64_t b = 0; b < P->N; ++b) {
+    int lo[3] = {13, 13, 13}, hi[3] = {-1, -1, -1};
+    for (int d = 0; d < 27; ++d) {
+      if (d == 13 || P->nb.nbr[b * 27 + d] > -2) continue;
+      const int dd[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
+      for (int a = 0; a < 3; ++a) {
+        const int l0 = dd[a] > 0 ? 9 : 0, h0 = dd[a] < 0 ? 3 : 12;
+        lo[a] = std::min(lo[a], l0);
+        hi[a] = std::max(hi[a], h0);
+      }
+    }
+    if (hi[0] < 0) continue;
+    P->up_slot[b] = int32_t(P->up_list.size());
+    P->up_list.push_back(int32_t(b));
+    P->up_box.push_back(lo[0] | hi[0] << 4 | lo[1] << 8 | hi[1] << 12 | lo[2] << 16 | hi[2] << 20);
+  }
+  for (int l = 0; l <= 32; ++l) {
+    P->up_off[l + 1] = P->up_off[l];
+    while (P->up_off[l + 1] < int64_t(P->up_list.size()) && P->octs[P->up_list[P->up_off[l + 1]]].l == l)
+      P->up_off[l + 1]++;
+  }
   // reading of the CFL condition (Sec. 3.4): dt_f = cfl * node spacing of the finest level
   const double h_f = (P->spec.hi - P->spec.lo) / (6.0 * double(int64_t(1) << P->lmax));
   P->dt_f = prob->cfl * h_f;
@@ -442,8 +513,13 @@ lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_
   P->d_err = static_cast<int*>(dev_alloc(P, sizeof(int) * 4));
   P->d_U[0] = static_cast<double*>(dev_alloc(P, fbytes));
   P->d_U[1] = static_cast<double*>(dev_alloc(P, fbytes));
+  const size_t nup = std::max<size_t>(P->up_list.size(), 1);
+  P->d_up_list = static_cast<int*>(dev_alloc(P, sizeof(int) * nup));
+  P->d_up_box = static_cast<int*>(dev_alloc(P, sizeof(int) * nup));
+  P->d_up_slot = static_cast<int*>(dev_alloc(P, sizeof(int) * P->N));
+  P->d_up = static_cast<double*>(dev_alloc(P, sizeof(double) * nup * P->nf * ltsoct::kNT));
   if (!P->d_oct || !P->d_nbr || !P->d_fine || !P->d_hang || !P->d_u[0] || !P->d_u[1] || !P->d_K || !P->d_err ||
-      !P->d_U[0] || !P->d_U[1]) {
+      !P->d_U[0] || !P->d_U[1] || !P->d_up_list || !P->d_up_box || !P->d_up_slot || !P->d_up) {
     release(P);
     delete P;
     return fail(LTS_ENOMEM, "lts_plan_create: device allocation failed");
@@ -458,12 +534,19 @@ lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_
   cudaError_t e4 = P->hang.empty() ? cudaSuccess
                                    : cudaMemcpyAsync(P->d_hang, P->hang.data(), sizeof(int) * P->hang.size(),
                                                      cudaMemcpyHostToDevice, P->stream);
+  cudaError_t e10 = P->up_list.empty() ? cudaSuccess
+                                        : cudaMemcpyAsync(P->d_up_list, P->up_list.data(), sizeof(int) * P->up_list.size(),
+                                                          cudaMemcpyHostToDevice, P->stream);
+  cudaError_t e11 = P->up_box.empty() ? cudaSuccess
+                                       : cudaMemcpyAsync(P->d_up_box, P->up_box.data(), sizeof(int) * P->up_box.size(),
+                                                         cudaMemcpyHostToDevice, P->stream);
+  cudaError_t e12 = cudaMemcpyAsync(P->d_up_slot, P->up_slot.data(), sizeof(int) * P->N, cudaMemcpyHostToDevice, P->stream);
   cudaError_t e5 = cudaMemsetAsync(P->d_K, 0, fbytes * P->p, P->stream);
   cudaError_t e6 = cudaMemsetAsync(P->d_u[0], 0, fbytes, P->stream);
   cudaError_t e7 = cudaMemsetAsync(P->d_u[1], 0, fbytes, P->stream);
   cudaError_t e9 = cudaMemsetAsync(P->d_err, 0, sizeof(int) * 4, P->stream);
   cudaError_t e8 = cudaStreamSynchronize(P->stream);
-  for (cudaError_t e : {e1, e2, e3, e4, e5, e6, e7, e9, e8})
+  for (cudaError_t e : {e1, e2, e3, e4, e5, e6, e7, e9, e10, e11, e12, e8})
     if (e != cudaSuccess) {
       release(P);
       delete P;

@@ -216,18 +216,10 @@ __device__ __forceinline__ double lattice_to_x(double lo, double ext, int P6) {
 template <int NF>
 struct StageSmem {
   double T[NF][kNT];         // padded tiles
-  double V[NF][kNV];         // stage inputs of one coarser source (interpolation)
-  double X1[13 * 49];        // interpolated along x: [rx][z][y]
-  double X2[13 * 13 * 7];    // then along y: [rx][ry][z]
-  double W[13][7];           // Lagrange weights
   StageTerms om[4];          // correction terms of this stage per relation
   int src[kNT];
   unsigned short code[kNT];  // rx | ry << 4 | rz << 8 | (level diff + 1) << 12 | exterior << 15
   NbrView nv;
-  int nlev[27];
-  int coarse[8];
-  int range[8][4];           // per coarser source: min/max of rx and ry over its interpolated points
-  int ncoarse;
 };
 
 constexpr unsigned kExterior = 1u << 15;
@@ -314,7 +306,7 @@ __device__ __noinline__ void radiative_rhs(const StageSmem<NF>& S, const StageAr
 }
 
 template <int NF>
-__global__ void __launch_bounds__(kThreads) stage_kernel(StageArgs A) {
+__global__ void __launch_bounds__(kThreads, 4) stage_kernel(StageArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StageSmem<NF>& S = *reinterpret_cast<StageSmem<NF>*>(smem_raw);
   const int b = A.first + blockIdx.x;
@@ -328,28 +320,6 @@ __global__ void __launch_bounds__(kThreads) stage_kernel(StageArgs A) {
 
   load_neighbours(A.tree, b, S.nv);
   if (tid < 4) S.om[tid] = A.om[tid];
-  for (int q = tid; q < 91; q += blockDim.x) S.W[q / 7][q % 7] = c_W[q / 7][q % 7];
-  __syncthreads();
-  if (tid < 27) {
-    const int e = S.nv.nbr[tid];
-    S.nlev[tid] = e >= 0 ? A.tree.oct[e].w : -1;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    int n = 0;
-    for (int d = 0; d < 27; ++d) {
-      const int e = S.nv.nbr[d];
-      if (d == 13 || e < 0 || S.nlev[d] != lb - 1) continue;
-      bool seen = false;
-      for (int q = 0; q < n; ++q) seen |= S.coarse[q] == e;
-      if (!seen) S.coarse[n++] = e;
-    }
-    S.ncoarse = n;
-    for (int c = 0; c < 8; ++c) {
-      S.range[c][0] = S.range[c][2] = 12;
-      S.range[c][1] = S.range[c][3] = 0;
-    }
-  }
   __syncthreads();
 
   // 1. source of every padded point (coarsest leaf containing it, then smallest Morton key)
@@ -375,16 +345,6 @@ __global__ void __launch_bounds__(kThreads) stage_kernel(StageArgs A) {
           code = kExterior;
         } else {
           code = unsigned(rx) | unsigned(ry) << 4 | unsigned(rz) << 8 | unsigned(so.w - lb + 1) << 12;
-          if ((rx | ry | rz) & 1) {
-            // interpolated point: widen the sub-box of its coarser source
-            for (int c = 0; c < S.ncoarse; ++c)
-              if (S.coarse[c] == src) {
-                atomicMin(&S.range[c][0], rx);
-                atomicMax(&S.range[c][1], rx);
-                atomicMin(&S.range[c][2], ry);
-                atomicMax(&S.range[c][3], ry);
-              }
-          }
         }
       }
     }
@@ -393,8 +353,9 @@ __global__ void __launch_bounds__(kThreads) stage_kernel(StageArgs A) {
   }
   __syncthreads();
 
-  // 2. direct copies: own interior and every source whose stage input is the plain
-  //    RK stage input (same level; every level under GTS), batched for memory parallelism
+  // 2. gathers, batched for memory parallelism: own interior and same-level sources
+  //    read the stage inputs; coarser sources read their prolonged stage inputs
+  //    (Fig. unzip, prepared by prolong_kernel); under GTS every source is read directly
   const double* direct = s == 0 ? A.u[(A.cur_mask >> lb) & 1] : A.Uin;
   {
     double v[kPer][NF];
@@ -405,12 +366,19 @@ __global__ void __launch_bounds__(kThreads) stage_kernel(StageArgs A) {
       for (int f = 0; f < NF; ++f) v[it][f] = 0.0;
       if (q < kNT) {
         const unsigned code = S.code[q];
-        const int rx = code & 15, ry = (code >> 4) & 15, rz = (code >> 8) & 15;
-        const bool same = ((code >> 12) & 7) == 1 || A.gts;
-        if (!(code & kExterior) && same && !((rx | ry | rz) & 1)) {
-          const long long off = (long long)S.src[q] * kNV + (rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1);
+        if (!(code & kExterior)) {
+          const int rx = code & 15, ry = (code >> 4) & 15, rz = (code >> 8) & 15;
+          const int rel_code = (code >> 12) & 3;  // 0 coarser, 1 same, 2 finer
+          const int src = S.src[q];
+          if (rel_code == 0) {
+            const double* up = A.up + (long long)__ldg(A.up_slot + src) * NF * kNT + rx + 13 * ry + 169 * rz;
 #pragma unroll
-          for (int f = 0; f < NF; ++f) v[it][f] = __ldg(direct + f * A.fstride + off);
+            for (int f = 0; f < NF; ++f) v[it][f] = __ldg(up + f * kNT);
+          } else if (rel_code == 1 || A.gts) {
+            const long long off = (long long)src * kNV + (rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) v[it][f] = __ldg(direct + f * A.fstride + off);
+          }
         }
       }
     }
@@ -424,92 +392,19 @@ __global__ void __launch_bounds__(kThreads) stage_kernel(StageArgs A) {
     }
   }
 
-  // 3. corrected copies: finer sources (eq. fc_1) and nodes of coarser sources (eqs. fc_1, fc_2)
+  // 3. finer sources (injection) with the coarse<-fine correction of eq. fc_1
   if (!A.gts) {
     for (int q = tid; q < kNT; q += blockDim.x) {
       const unsigned code = S.code[q];
-      const int rel_code = (code >> 12) & 7;
-      if ((code & kExterior) || rel_code == 1) continue;
+      if ((code & kExterior) || ((code >> 12) & 3) != 2) continue;
       const int rx = code & 15, ry = (code >> 4) & 15, rz = (code >> 8) & 15;
-      if ((rx | ry | rz) & 1) continue;
-      const int ls = lb + rel_code - 1;
-      const int rel = ls > lb ? 1 : (ls >= A.lstar ? 2 : 3);
-      const double* ub = A.u[((A.cur_mask >> ls) & 1) ^ (rel == 3 ? 1 : 0)];
+      const int ls = lb + 1;
+      const double* ub = A.u[(A.cur_mask >> ls) & 1];
       const long long off = (long long)S.src[q] * kNV + (rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1);
 #pragma unroll
       for (int f = 0; f < NF; ++f)
-        S.T[f][q] = corrected_value(ub + f * A.fstride + off, A.K + f * A.fstride + off, kstride, S.om[rel],
+        S.T[f][q] = corrected_value(ub + f * A.fstride + off, A.K + f * A.fstride + off, kstride, S.om[1],
                                     A.lc[ls].dt);
-    }
-  }
-
-  // 4. interpolation from coarser sources (Fig. unzip: coarse -> fine), sum-factorised
-  //    over the sub-box of half-node positions the points need: x, then y, then z
-  const int ncoarse = S.ncoarse;
-  for (int c = 0; c < ncoarse; ++c) {
-    const int src = S.coarse[c];
-    const int ls = lb - 1;
-    const int rel = ls >= A.lstar ? 2 : 3;
-    const double* ub = A.u[((A.cur_mask >> ls) & 1) ^ (rel == 3 ? 1 : 0)];
-    const double* cdirect = s == 0 ? A.u[(A.cur_mask >> ls) & 1] : A.Uin;
-    const int rx0 = S.range[c][0], nrx = S.range[c][1] - rx0 + 1;
-    const int ry0 = S.range[c][2], nry = S.range[c][3] - ry0 + 1;
-    if (nrx <= 0 || nry <= 0) continue;  // only even points: all copied already
-    __syncthreads();
-    for (int t = tid; t < NF * kNV; t += blockDim.x) {
-      const int f = t / kNV, n = t - f * kNV;
-      const long long off = (long long)src * kNV + n;
-      S.V[f][n] = A.gts ? __ldg(cdirect + f * A.fstride + off)
-                        : corrected_value(ub + f * A.fstride + off, A.K + f * A.fstride + off, kstride,
-                                          S.om[rel], A.lc[ls].dt);
-    }
-    for (int f = 0; f < NF; ++f) {
-      __syncthreads();
-      for (int t = tid; t < nrx * 49; t += blockDim.x) {
-        const int rx = rx0 + t / 49, yz = t % 49;  // yz = y + 7 z
-        const double* v = S.V[f] + 7 * yz;
-        double acc;
-        if (rx & 1) {
-          acc = 0.0;
-#pragma unroll
-          for (int a = 0; a < 7; ++a) acc = fma(S.W[rx][a], v[a], acc);
-        } else {
-          acc = v[rx >> 1];
-        }
-        S.X1[t] = acc;
-      }
-      __syncthreads();
-      for (int t = tid; t < nrx * nry * 7; t += blockDim.x) {
-        const int z = t % 7, ryi = (t / 7) % nry, rxi = t / (7 * nry);
-        const int ry = ry0 + ryi;
-        const double* x1 = S.X1 + rxi * 49 + 7 * z;  // [y] for fixed rx, z
-        double acc;
-        if (ry & 1) {
-          acc = 0.0;
-#pragma unroll
-          for (int bb = 0; bb < 7; ++bb) acc = fma(S.W[ry][bb], x1[bb], acc);
-        } else {
-          acc = x1[ry >> 1];
-        }
-        S.X2[t] = acc;
-      }
-      __syncthreads();
-      for (int q = tid; q < kNT; q += blockDim.x) {
-        if (S.src[q] != src) continue;
-        const unsigned code = S.code[q];
-        const int rx = code & 15, ry = (code >> 4) & 15, rz = (code >> 8) & 15;
-        if (!((rx | ry | rz) & 1)) continue;
-        const double* x2 = S.X2 + ((rx - rx0) * nry + (ry - ry0)) * 7;
-        double acc;
-        if (rz & 1) {
-          acc = 0.0;
-#pragma unroll
-          for (int cc = 0; cc < 7; ++cc) acc = fma(S.W[rz][cc], x2[cc], acc);
-        } else {
-          acc = x2[rz >> 1];
-        }
-        S.T[f][q] = acc;
-      }
     }
   }
   __syncthreads();
@@ -607,6 +502,105 @@ cudaError_t launch_stage(const StageArgs& a, int count, cudaStream_t s) {
     stage_kernel<1><<<count, kThreads, stage_smem<1>(), s>>>(a);
   else
     stage_kernel<2><<<count, kThreads, stage_smem<2>(), s>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Prolongation of coarser sources (Fig. unzip, coarse -> fine).  One CTA per
+// octant with finer neighbours forms its stage inputs as those neighbours see
+// them (eqs. fc_1 / fc_2) and interpolates them, sum-factorised x, then y, then z,
+// to every half-node position of the box its finer neighbours read.  Each finer
+// neighbour then gathers these values as plain copies.
+// ---------------------------------------------------------------------------
+template <int NF>
+struct ProlongSmem {
+  double V[NF][kNV];
+  double X1[NF][13 * 49];      // [rx][z][y]
+  double X2[NF][13 * 13 * 7];  // [rx][ry][z]
+  double W[13][7];
+};
+
+template <int NF>
+__global__ void __launch_bounds__(256) prolong_kernel(ProlongArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ProlongSmem<NF>& S = *reinterpret_cast<ProlongSmem<NF>*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int b = A.list[blockIdx.x];
+  const int slot = A.up_slot[b];
+  const int lb = A.tree.oct[b].w;
+  const int rel = A.gts ? 0 : (lb >= A.lstar ? 2 : 3);
+  const int bx = A.box[slot];
+  const int rx0 = bx & 15, ry0 = (bx >> 8) & 15, rz0 = (bx >> 16) & 15;
+  const int nrx = ((bx >> 4) & 15) - rx0 + 1, nry = ((bx >> 12) & 15) - ry0 + 1, nrz = ((bx >> 20) & 15) - rz0 + 1;
+  const long long kstride = (long long)A.nf * A.fstride;
+  for (int q = tid; q < 91; q += blockDim.x) S.W[q / 7][q % 7] = c_W[q / 7][q % 7];
+  const int cur = (A.cur_mask >> lb) & 1;
+  const double* direct = A.stage == 0 ? A.u[cur] : A.Uin;
+  const double* ub = A.u[cur ^ (rel == 3 ? 1 : 0)];
+  for (int t = tid; t < NF * kNV; t += blockDim.x) {
+    const int f = t / kNV, n = t - f * kNV;
+    const long long off = (long long)b * kNV + n;
+    S.V[f][n] = rel == 0 ? __ldg(direct + f * A.fstride + off)
+                         : corrected_value(ub + f * A.fstride + off, A.K + f * A.fstride + off, kstride, A.om[rel],
+                                           A.lc[lb].dt);
+  }
+  __syncthreads();
+  for (int t = tid; t < NF * nrx * 49; t += blockDim.x) {
+    const int f = t / (nrx * 49), rem = t - f * nrx * 49;
+    const int rxi = rem / 49, yz = rem - rxi * 49;  // yz = y + 7 z
+    const int rx = rx0 + rxi;
+    const double* v = S.V[f] + 7 * yz;
+    double acc;
+    if (rx & 1) {
+      acc = 0.0;
+#pragma unroll
+      for (int a = 0; a < 7; ++a) acc = fma(S.W[rx][a], v[a], acc);
+    } else {
+      acc = v[rx >> 1];
+    }
+    S.X1[f][rem] = acc;
+  }
+  __syncthreads();
+  for (int t = tid; t < NF * nrx * nry * 7; t += blockDim.x) {
+    const int f = t / (nrx * nry * 7), rem = t - f * nrx * nry * 7;
+    const int z = rem % 7, ryi = (rem / 7) % nry, rxi = rem / (7 * nry);
+    const int ry = ry0 + ryi;
+    const double* x1 = S.X1[f] + rxi * 49 + 7 * z;  // [y]
+    double acc;
+    if (ry & 1) {
+      acc = 0.0;
+#pragma unroll
+      for (int bb = 0; bb < 7; ++bb) acc = fma(S.W[ry][bb], x1[bb], acc);
+    } else {
+      acc = x1[ry >> 1];
+    }
+    S.X2[f][rem] = acc;
+  }
+  __syncthreads();
+  double* out = A.up + (long long)slot * NF * kNT;
+  for (int t = tid; t < NF * nrx * nry * nrz; t += blockDim.x) {
+    const int f = t / (nrx * nry * nrz), rem = t - f * nrx * nry * nrz;
+    const int rxi = rem % nrx, ryi = (rem / nrx) % nry, rzi = rem / (nrx * nry);
+    const int rz = rz0 + rzi;
+    const double* x2 = S.X2[f] + (rxi * nry + ryi) * 7;  // [z]
+    double acc;
+    if (rz & 1) {
+      acc = 0.0;
+#pragma unroll
+      for (int cc = 0; cc < 7; ++cc) acc = fma(S.W[rz][cc], x2[cc], acc);
+    } else {
+      acc = x2[rz >> 1];
+    }
+    out[f * kNT + (rx0 + rxi) + 13 * (ry0 + ryi) + 169 * rz] = acc;
+  }
+}
+
+cudaError_t launch_prolong(const ProlongArgs& a, cudaStream_t s) {
+  if (a.count <= 0) return cudaSuccess;
+  if (a.nf == 1)
+    prolong_kernel<1><<<a.count, 256, sizeof(ProlongSmem<1>), s>>>(a);
+  else
+    prolong_kernel<2><<<a.count, 256, sizeof(ProlongSmem<2>), s>>>(a);
   return cudaGetLastError();
 }
 

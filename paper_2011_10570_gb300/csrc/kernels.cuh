@@ -61,6 +61,30 @@ struct StageArgs {
   double gamma[4];       // gamma[stage][.] for exact boundary data
   IcParams icp;
   int* err;              // device error word: bit 0 source coordinate out of range
+  const double* up;      // prolonged stage inputs of coarser sources, [slot][nf][2197]
+  const int* up_slot;    // slot of an octant in `up` (-1: not a coarser source)
+};
+
+// Prolongation of the stage inputs of coarser sources (Fig. unzip, coarse -> fine)
+// for one stage: every listed octant has finer neighbours; its time-corrected
+// stage inputs (eqs. fc_1 / fc_2) are interpolated to the half-node positions of
+// the box its finer neighbours read.
+struct ProlongArgs {
+  DevTree tree;
+  const int* list;       // octants to process (level order)
+  int count;
+  const int* box;        // per slot: packed half-node box rx0 | rx1 << 4 | ry0 << 8 | ry1 << 12 | rz0 << 16 | rz1 << 20
+  const int* up_slot;
+  double* up;
+  const double* u[2];
+  const double* K;
+  const double* Uin;
+  long long fstride;
+  int nf, stage, lstar;
+  unsigned cur_mask;
+  int gts;
+  LevelConst lc[32];
+  StageTerms om[4];
 };
 
 struct SyncArgs {
@@ -106,6 +130,7 @@ struct MapArgs {
 
 cudaError_t upload_tables(const Tables* rk4, const Tables* rk3, const double W[13][7], const double E[4][4]);
 cudaError_t launch_stage(const StageArgs& a, int count, cudaStream_t s);
+cudaError_t launch_prolong(const ProlongArgs& a, cudaStream_t s);
 cudaError_t launch_sync_zip(const SyncArgs& a, cudaStream_t s);
 cudaError_t launch_sync_hanging(const SyncArgs& a, cudaStream_t s);
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);

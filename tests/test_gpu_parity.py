@@ -85,7 +85,7 @@ def test_lts_fields_match_oracle(lt, orc, name, mk):
     gt, plan, ot, sol = both(lt, orc, w)
     plan.set_initial(0.0)
     sol.set_initial(0.0)
-    assert rel_linf(plan.get_state(), sol.state()) <= 1e-15
+    assert rel_linf(plan.get_state(), sol.state()) <= 1e-14   # synced initial data (rounding of the interpolation)
     st = plan.stats()
     nsub = 2 ** (st["l_max"] - st["l_min"])
     # one substep (all levels), the rest of the macro step (finest-only and partial
