@@ -29,6 +29,9 @@ sys.path.insert(0, ROOT)
 METRIC = "LTS octant-node updates/s"
 UNIT = "node-updates/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x flops/FMA x max clock
+# DRAM bytes (read + write) per node-stage of stage_kernel<2>, from the ncu capture of
+# profiles/stage_kernel_wave_l4-8.md; set to None whenever the kernel changes after it
+STAGE_DRAM_BYTES_PER_NODE_STAGE = 85.0
 
 
 def measured_peaks():
@@ -281,8 +284,11 @@ def main():
         avg_ms = ks["ms"] / ks["launches"]
         flops_per_launch = ks["flops"] / ks["launches"]
         achieved = flops_per_launch / (avg_ms / 1e3) / 1e12
+        traffic = (STAGE_DRAM_BYTES_PER_NODE_STAGE * ks["node_stages"] / ks["launches"]
+                   if STAGE_DRAM_BYTES_PER_NODE_STAGE else None)
         line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                            "traffic_source": "ncu dram bytes per node-stage (levels 4..8 capture) x node-stages per launch",
                             "kernel": "stage_kernel<2>", "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 x 2.07 GHz",
                             "hbm_gbs_algorithmic": ks["bytes"] / (ks["ms"] / 1e3) / 1e9,
                             "hbm_peak_gbs": measured_peaks().get("hbm_gbs"),

@@ -19,12 +19,18 @@ const char* last_error_cstr();
 
 using ltsoct::kNV;
 
-// Algorithmic work of one node-stage (FMA = 2 flops), counted from the formulas of
-// the stage kernel: RHS stencils + own stage input + the share of the RK update.
-static double flops_per_node_stage(int pde) { return pde == LTS_PDE_ADVECTION ? 49.0 : 65.0; }
-// Algorithmic HBM bytes of one node-stage per field: own u (8), stage inputs
-// (0.75 K reads), the stage write (8), and the update's share (K reads + u write).
-static double bytes_per_node_stage(int nf) { return 30.0 * nf; }
+// Algorithmic work of one node-stage (FMA = 2 flops, add/mul = 1), counted from
+// the stage kernel's formulas.  Wave: six symmetric pair sums per field (30), the
+// Laplacian (5), two dissipation combinations (12), two outputs (4), the next
+// stage input (3 over four stages) and the RK update's share (5) = 59.
+// Advection: pair sums (15), D1 differences and a.grad (17), dissipation (6),
+// output (3), next stage input (1.5), update share (2.5) = 45.
+static double flops_per_node_stage(int pde) { return pde == LTS_PDE_ADVECTION ? 45.0 : 59.0; }
+// Algorithmic HBM bytes of one node-stage per field: own stage input (8), own
+// step-start state (8), the stage (8), the next stage input (6 over four
+// stages), the update's share of stage reads and state write (6 + 2) = 38.
+// Ghost reads of neighbours are expected to hit L2 and are not counted.
+static double bytes_per_node_stage(int nf) { return 38.0 * nf; }
 
 struct lts_plan {
   lts_problem prob;
