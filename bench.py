@@ -109,23 +109,28 @@ def dist_setup(args):
     return world, rank, local, pg
 
 
-def oracle_sample(w, threads=None):
-    """Times the oracle on one LTS substep of the workload in which every level is
-    active (substep 0), after a warm call that builds its padding maps.  Returns
-    (node-updates/s, seconds, octants, threads)."""
-    import oracle
-    if threads:
-        oracle.set_threads(threads)
-    tree = oracle.Tree.build(w["spec"])
-    sol = oracle.Solver(tree, w["spec"], w["prob"])
-    sol.set_initial(0.0)
-    sol.lts_substeps(1)              # warm: padding maps are built on first use
-    sol.set_initial(0.0)
-    t0 = time.perf_counter()
-    sol.lts_substeps(1)
-    dt = time.perf_counter() - t0
-    n = len(tree)
-    return n * 343 / dt, dt, n
+class OracleSample:
+    """The CPU oracle on a bounded sample of the workload: one LTS substep in which
+    every level is active (substep 0), each octant advanced one full RK step on its
+    own level.  The tree and the oracle's padding maps are built once (first call
+    untimed); every timed call restarts from the initial data."""
+
+    def __init__(self, w, threads=None):
+        import oracle
+        if threads:
+            oracle.set_threads(threads)
+        self.tree = oracle.Tree.build(w["spec"])
+        self.sol = oracle.Solver(self.tree, w["spec"], w["prob"])
+        self.n = len(self.tree)
+        self.sol.set_initial(0.0)
+        self.sol.lts_substeps(1)          # builds the padding maps
+
+    def run(self):
+        self.sol.set_initial(0.0)
+        t0 = time.perf_counter()
+        self.sol.lts_substeps(1)
+        dt = time.perf_counter() - t0
+        return self.n * 343 / dt, dt
 
 
 def host_threads():
@@ -139,11 +144,13 @@ def run_reference(args, w, world, rank, pg):
     if rank != 0:
         return
     threads = host_threads()
+    sample = OracleSample(w, threads)
+    n = sample.n
     vals, times = [], []
     for _ in range(args.warmup):
-        oracle_sample(w, threads)
+        sample.run()
     for _ in range(args.steps):
-        v, dt, n = oracle_sample(w, threads)
+        v, dt = sample.run()
         vals.append(v)
         times.append(dt)
     value = len(vals) / sum(1.0 / v for v in vals)
@@ -296,7 +303,11 @@ def main():
     if gts:
         line["gts"] = gts
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, dt, nn = oracle_sample(w, host_threads())
+        del plan
+        torch.cuda.empty_cache()
+        samp = OracleSample(w, host_threads())
+        v, dt = samp.run()
+        nn = samp.n
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": host_threads(), "kind": "oracle",
                                 "sample": "one LTS substep with every level active (%d octants, one RK4 step each), "
                                           "%.1f s" % (nn, dt)}
