@@ -92,6 +92,9 @@ typedef struct {
   int bc;
   int ic;
   double ic_params[32];
+  int precision;       /* 0: FP64 throughout.  1: mixed -- RK stages, stage inputs, the padded
+                          block and the right-hand side in FP32; the state, the RK update and
+                          the time corrections (eqs. fc_1, fc_2) in FP64 */
   void* stream;        /* cudaStream_t; NULL = default stream */
   void* (*dev_alloc)(size_t bytes, void* ctx);  /* optional device allocator */
   void (*dev_free)(void* ptr, void* ctx);
@@ -139,7 +142,8 @@ lts_status lts_set_initial(lts_plan* plan, double t0);
 lts_status lts_set_state(lts_plan* plan, const double* u, double t0, int on_device);
 /* Copies the current DG state; synchronises the stream.  t (optional) gets the time. */
 lts_status lts_get_state(lts_plan* plan, double* u, double* t, int on_device);
-/* RK stage j (0-based) of every octant's most recent step, [nf][N][343]. */
+/* RK stage j (0-based) of every octant's most recent step, [nf][N][343], widened to FP64
+ * in the mixed-precision mode. */
 lts_status lts_get_stage(lts_plan* plan, int j, double* k, int on_device);
 
 /* ---- time stepping ------------------------------------------------------------ */

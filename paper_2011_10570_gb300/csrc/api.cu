@@ -29,8 +29,9 @@ static double flops_per_node_stage(int pde) { return pde == LTS_PDE_ADVECTION ? 
 // Algorithmic HBM bytes of one node-stage per field: own stage input (8), own
 // step-start state (8), the stage (8), the next stage input (6 over four
 // stages), the update's share of stage reads and state write (6 + 2) = 38.
-// Ghost reads of neighbours are expected to hit L2 and are not counted.
-static double bytes_per_node_stage(int nf) { return 38.0 * nf; }
+// Ghost reads of neighbours are expected to hit L2 and are not counted.  Mixed
+// precision (FP32 stage type): 4 + 8 + 4 + 3 + (3 + 2) = 24 bytes per field.
+static double bytes_per_node_stage(int nf, int mixed) { return (mixed ? 24.0 : 38.0) * nf; }
 
 struct lts_plan {
   lts_problem prob;
@@ -53,15 +54,17 @@ struct lts_plan {
   int* d_fine = nullptr;
   int* d_hang = nullptr;
   double* d_u[2] = {nullptr, nullptr};
-  double* d_K = nullptr;
-  double* d_U[2] = {nullptr, nullptr};  // stage inputs of the current and the next stage
+  void* d_K = nullptr;                  // RK stages, stage type
+  void* d_U[2] = {nullptr, nullptr};    // stage inputs of the current and the next stage, stage type
+  int mixed = 0;                        // 1: FP32 stage type
+  size_t es = 8;                        // bytes per stage-type element
   std::vector<int32_t> up_list;         // octants with finer neighbours (coarser sources), level order
   int64_t up_off[34] = {};              // per level ranges in up_list
   std::vector<int32_t> up_box, up_slot;
   int* d_up_list = nullptr;
   int* d_up_box = nullptr;
   int* d_up_slot = nullptr;
-  double* d_up = nullptr;               // prolonged stage inputs [slot][nf][2197]
+  void* d_up = nullptr;                 // prolonged stage inputs [slot][nf][2197], stage type
   int* d_err = nullptr;
   int64_t launches = 0;               // every kernel launched by the plan
   size_t bytes = 0;
@@ -131,11 +134,12 @@ ltsoct::DevTree dev_tree(const lts_plan* P) {
 int cur_of(const lts_plan* P, int l) { return (P->cur_mask >> l) & 1; }
 
 // in-place shared-node sync of the arrays vb (level l uses vb[(sel >> l) & 1])
-lts_status sync_fields(lts_plan* P, double* vb0, double* vb1, unsigned sel) {
+lts_status sync_fields(lts_plan* P, void* vb0, void* vb1, unsigned sel, int elem) {
   ltsoct::SyncArgs a{};
   a.tree = dev_tree(P);
   a.vb[0] = vb0;
   a.vb[1] = vb1;
+  a.elem = elem;
   a.sel_mask = sel;
   a.fstride = P->N * kNV;
   a.nf = P->nf;
@@ -174,6 +178,7 @@ ltsoct::StageArgs stage_args(const lts_plan* P, int stage, int first, int lstar,
   a.K = P->d_K;
   a.Uin = P->d_U[stage & 1];
   a.Uout = P->d_U[(stage + 1) & 1];
+  a.mixed = P->mixed;
   a.fstride = P->N * kNV;
   a.nf = P->nf;
   a.p = P->p;
@@ -236,6 +241,7 @@ lts_status launch_prolong_for(lts_plan* P, const ltsoct::StageArgs& sa, int lsta
   a.lstar = lstar;
   a.cur_mask = sa.cur_mask;
   a.gts = sa.gts;
+  a.mixed = sa.mixed;
   for (int l = 0; l < 32; ++l) a.lc[l] = sa.lc[l];
   for (int r = 0; r < 4; ++r) a.om[r] = sa.om[r];
   CK(ltsoct::launch_prolong(a, P->stream), "prolongation kernel launch");
@@ -281,7 +287,7 @@ lts_status lts_substep(lts_plan* P) {
   for (int l = lstar; l <= P->lmax; ++l) P->cur_mask ^= 1u << l;
   P->n_sub++;
   if (P->n_sub == (int64_t(1) << (P->lmax - P->lmin))) {
-    lts_status st = sync_fields(P, P->d_u[0], P->d_u[1], P->cur_mask);
+    lts_status st = sync_fields(P, P->d_u[0], P->d_u[1], P->cur_mask, 8);
     if (st != LTS_OK) return st;
     P->t_macro += double(P->n_sub) * P->dt_f;
     P->n_sub = 0;
@@ -290,20 +296,20 @@ lts_status lts_substep(lts_plan* P) {
 }
 
 lts_status gts_step(lts_plan* P) {
-  const long long kstride = (long long)P->nf * P->N * kNV;
+  const size_t kstride_bytes = P->es * size_t(P->nf) * P->N * kNV;
   for (int s = 0; s < P->p; ++s) {
     const ltsoct::StageArgs sa = stage_args(P, s, 0, P->lmin, 1);
     lts_status st = launch_prolong_for(P, sa, P->lmin);
     if (st != LTS_OK) return st;
     st = launch_stage_timed(P, sa, int(P->N));
     if (st != LTS_OK) return st;
-    double* Ks = P->d_K + s * kstride;
-    st = sync_fields(P, Ks, Ks, 0u);
+    void* Ks = static_cast<char*>(P->d_K) + s * kstride_bytes;
+    st = sync_fields(P, Ks, Ks, 0u, int(P->es));
     if (st != LTS_OK) return st;
     if (s + 1 < P->p) {
       // the next stage's inputs were formed from the unsynchronised stage: sync them too
-      double* Un = P->d_U[(s + 1) & 1];
-      st = sync_fields(P, Un, Un, 0u);
+      void* Un = P->d_U[(s + 1) & 1];
+      st = sync_fields(P, Un, Un, 0u, int(P->es));
       if (st != LTS_OK) return st;
     }
   }
@@ -311,6 +317,7 @@ lts_status gts_step(lts_plan* P) {
   ua.u[0] = P->d_u[0];
   ua.u[1] = P->d_u[1];
   ua.K = P->d_K;
+  ua.mixed = P->mixed;
   ua.fstride = P->N * kNV;
   ua.nf = P->nf;
   ua.p = P->p;
@@ -322,7 +329,7 @@ lts_status gts_step(lts_plan* P) {
   CK(ltsoct::launch_update(ua, P->stream), "update kernel launch");
   P->launches++;
   for (int l = P->lmin; l <= P->lmax; ++l) P->cur_mask ^= 1u << l;
-  lts_status st = sync_fields(P, P->d_u[0], P->d_u[1], P->cur_mask);
+  lts_status st = sync_fields(P, P->d_u[0], P->d_u[1], P->cur_mask, 8);
   if (st != LTS_OK) return st;
   P->n_sub++;
   if (P->n_sub == (int64_t(1) << (P->lmax - P->lmin))) {
@@ -348,6 +355,7 @@ bool supported(const lts_problem& p, std::string* why) {
   } else {
     return *why = "bc must be 0 or 1", false;
   }
+  if (p.precision != 0 && p.precision != 1) return *why = "precision must be 0 (FP64) or 1 (mixed)", false;
   if (p.ic == LTS_IC_WAVE_SHELL && (p.ic_params[3] < 0 || p.ic_params[3] > 4))
     return *why = "shell initial data takes at most 4 modes", false;
   return true;
@@ -432,6 +440,8 @@ lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_
   P->tab = prob->rk == 4 ? rk4 : rk3;
   P->p = P->tab.p;
   P->nf = prob->pde == LTS_PDE_WAVE ? 2 : 1;
+  P->mixed = prob->precision == 1;
+  P->es = P->mixed ? sizeof(float) : sizeof(double);
   P->octs = tree->leaves;
   P->N = int64_t(P->octs.size());
   if (P->N * 27 > INT32_MAX || P->N * kNV * 4 > (int64_t(1) << 46)) {
@@ -515,15 +525,16 @@ lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_
   P->d_hang = static_cast<int*>(dev_alloc(P, sizeof(int) * std::max<size_t>(P->hang.size(), 1)));
   P->d_u[0] = static_cast<double*>(dev_alloc(P, fbytes));
   P->d_u[1] = static_cast<double*>(dev_alloc(P, fbytes));
-  P->d_K = static_cast<double*>(dev_alloc(P, fbytes * P->p));
+  const size_t sbytes = size_t(P->N) * kNV * P->es * P->nf;  // one stage-type field set
+  P->d_K = dev_alloc(P, sbytes * P->p);
   P->d_err = static_cast<int*>(dev_alloc(P, sizeof(int) * 4));
-  P->d_U[0] = static_cast<double*>(dev_alloc(P, fbytes));
-  P->d_U[1] = static_cast<double*>(dev_alloc(P, fbytes));
+  P->d_U[0] = dev_alloc(P, sbytes);
+  P->d_U[1] = dev_alloc(P, sbytes);
   const size_t nup = std::max<size_t>(P->up_list.size(), 1);
   P->d_up_list = static_cast<int*>(dev_alloc(P, sizeof(int) * nup));
   P->d_up_box = static_cast<int*>(dev_alloc(P, sizeof(int) * nup));
   P->d_up_slot = static_cast<int*>(dev_alloc(P, sizeof(int) * P->N));
-  P->d_up = static_cast<double*>(dev_alloc(P, sizeof(double) * nup * P->nf * ltsoct::kNT));
+  P->d_up = dev_alloc(P, P->es * nup * P->nf * ltsoct::kNT);
   if (!P->d_oct || !P->d_nbr || !P->d_fine || !P->d_hang || !P->d_u[0] || !P->d_u[1] || !P->d_K || !P->d_err ||
       !P->d_U[0] || !P->d_U[1] || !P->d_up_list || !P->d_up_box || !P->d_up_slot || !P->d_up) {
     release(P);
@@ -547,7 +558,7 @@ lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_
                                        : cudaMemcpyAsync(P->d_up_box, P->up_box.data(), sizeof(int) * P->up_box.size(),
                                                          cudaMemcpyHostToDevice, P->stream);
   cudaError_t e12 = cudaMemcpyAsync(P->d_up_slot, P->up_slot.data(), sizeof(int) * P->N, cudaMemcpyHostToDevice, P->stream);
-  cudaError_t e5 = cudaMemsetAsync(P->d_K, 0, fbytes * P->p, P->stream);
+  cudaError_t e5 = cudaMemsetAsync(P->d_K, 0, sbytes * P->p, P->stream);
   cudaError_t e6 = cudaMemsetAsync(P->d_u[0], 0, fbytes, P->stream);
   cudaError_t e7 = cudaMemsetAsync(P->d_u[1], 0, fbytes, P->stream);
   cudaError_t e9 = cudaMemsetAsync(P->d_err, 0, sizeof(int) * 4, P->stream);
@@ -605,9 +616,9 @@ lts_status lts_set_initial(lts_plan* P, double t0) {
   for (int i = 0; i < 32; ++i) a.icp.v[i] = P->prob.ic_params[i];
   CK(ltsoct::launch_init(a, P->stream), "init kernel launch");
   P->launches++;
-  CK(cudaMemsetAsync(P->d_K, 0, size_t(P->N) * kNV * sizeof(double) * P->nf * P->p, P->stream), "memset");
+  CK(cudaMemsetAsync(P->d_K, 0, size_t(P->N) * kNV * P->es * P->nf * P->p, P->stream), "memset");
   // a synchronised state is the unzip of its shared-node values (hanging nodes interpolated)
-  lts_status st = sync_fields(P, P->d_u[0], P->d_u[0], 0u);
+  lts_status st = sync_fields(P, P->d_u[0], P->d_u[0], 0u, 8);
   if (st != LTS_OK) return st;
   P->cur_mask = 0;
   P->t_macro = t0;
@@ -620,8 +631,8 @@ lts_status lts_set_state(lts_plan* P, const double* u, double t0, int on_device)
   const size_t bytes = size_t(P->N) * kNV * sizeof(double) * P->nf;
   CK(cudaMemcpyAsync(P->d_u[0], u, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, P->stream),
      "lts_set_state copy");
-  CK(cudaMemsetAsync(P->d_K, 0, bytes * P->p, P->stream), "memset");
-  lts_status st = sync_fields(P, P->d_u[0], P->d_u[0], 0u);
+  CK(cudaMemsetAsync(P->d_K, 0, size_t(P->N) * kNV * P->es * P->nf * P->p, P->stream), "memset");
+  lts_status st = sync_fields(P, P->d_u[0], P->d_u[0], 0u, 8);
   if (st != LTS_OK) return st;
   P->cur_mask = 0;
   P->t_macro = t0;
@@ -664,9 +675,22 @@ lts_status lts_get_state(lts_plan* P, double* u, double* t, int on_device) {
 
 lts_status lts_get_stage(lts_plan* P, int j, double* k, int on_device) {
   if (!P || !k || j < 0 || j >= P->p) return fail(LTS_EINVAL, "lts_get_stage: bad argument");
-  const double* src[33];
-  for (int l = 0; l < 33; ++l) src[l] = P->d_K + size_t(j) * P->nf * P->N * kNV;
-  return copy_state(P, src, k, on_device);
+  const size_t n = size_t(P->nf) * P->N * kNV;
+  const char* base = static_cast<const char*>(P->d_K) + size_t(j) * n * P->es;
+  if (!P->mixed) {
+    const double* src[33];
+    for (int l = 0; l < 33; ++l) src[l] = reinterpret_cast<const double*>(base);
+    return copy_state(P, src, k, on_device);
+  }
+  double* tmp = nullptr;
+  CK(cudaMallocAsync(&tmp, n * sizeof(double), P->stream), "cudaMallocAsync");
+  CK(ltsoct::launch_widen(reinterpret_cast<const float*>(base), tmp, (long long)n, P->stream), "widen");
+  P->launches++;
+  CK(cudaMemcpyAsync(k, tmp, n * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     P->stream), "stage copy");
+  CK(cudaFreeAsync(tmp, P->stream), "cudaFreeAsync");
+  CK(cudaStreamSynchronize(P->stream), "cudaStreamSynchronize");
+  return check_device_error(P);
 }
 
 lts_status lts_run_substeps(lts_plan* P, int64_t n) {
@@ -820,7 +844,7 @@ lts_status lts_kernel_stats(lts_plan* P, int64_t* launches, double* ms, double* 
   if (ms) *ms = P->prof_ms;
   if (node_stages) *node_stages = P->prof_node_stages;
   if (flops) *flops = double(P->prof_node_stages) * flops_per_node_stage(P->prob.pde);
-  if (bytes) *bytes = double(P->prof_node_stages) * bytes_per_node_stage(P->nf);
+  if (bytes) *bytes = double(P->prof_node_stages) * bytes_per_node_stage(P->nf, P->mixed);
   if (reset) {
     P->prof_launches = 0;
     P->prof_node_stages = 0;

@@ -1,20 +1,25 @@
 // CUDA kernels of libltsoct for GB300 (sm_103a).
 //
-// The LTS substep (Alg. 2, Fig. blk_loop) runs one launch of stage_kernel per
-// RK stage over the active octants, which are a contiguous suffix of the level
-// order.  One CTA owns one octant: it resolves the source of each of the 2197
-// points of its padded block (Sec. 3.3: coarsest leaf containing the point, ties
-// to the smallest Morton key = smallest level-order index), forms the time-
-// corrected stage inputs of the sources (eqs. fc_1, fc_2), interpolates from
-// coarser sources in shared memory (Fig. unzip), fills the physical boundary,
-// evaluates the 4th-order FD right-hand side with Kreiss-Oliger dissipation on
-// the 7^3 interior and writes the stage (and, at the last stage, the RK update
-// of eq. rk_schemes into the other half of the double-buffered state).
+// The LTS substep (Alg. 2, Fig. blk_loop) runs, per RK stage, one launch of
+// prolong_kernel and one of stage_kernel over the active octants (a contiguous
+// suffix of the level order).
+//   prolong_kernel: one CTA per octant with finer neighbours forms its stage
+//     inputs as those neighbours see them (eqs. fc_1, fc_2) and interpolates
+//     them to the half-node positions they read (Fig. unzip, coarse -> fine).
+//   stage_kernel: one CTA per active octant resolves the source of each of the
+//     2197 points of its padded block (Sec. 3.3: coarsest leaf containing the
+//     point, ties to the smallest Morton key = smallest level-order index),
+//     gathers the sources' stage inputs into shared memory, fills the physical
+//     boundary, evaluates the 4th-order FD right-hand side with Kreiss-Oliger
+//     dissipation on the 7^3 interior and writes the stage, the next stage's
+//     inputs and, at the last stage, the RK update of eq. rk_schemes into the
+//     other half of the double-buffered state.
 //
-// FP64 on GB300 issues about 2 DFMA per clock per SM, so these kernels are
-// bound by the FP64 pipe; integer work (source resolution) and memory traffic
-// hide behind it.  The FD formulas are arranged to share the symmetric sums
-// between the Laplacian and the dissipation.
+// Precision.  The state u, the RK update and the time corrections are FP64.
+// The stage type R (stages, stage inputs, prolonged inputs, the padded tile
+// and the right-hand side) is double, or float in the mixed-precision mode.
+// FP64 on GB300 issues about 2 DFMA per clock per SM, so the FP64 kernels are
+// bound by the FP64 pipe; integer work and memory traffic hide behind it.
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -133,30 +138,33 @@ __device__ void load_neighbours(const DevTree& t, int b, NbrView& nv) {
   }
 }
 
+
 // stage input of a source node from its step-start state and RK stages,
-// u + dt * sum_t w_t K_(j_t)  (eq. rk_schemes with the corrected weights of
-// eqs. fc_1 / fc_2)
-__device__ __forceinline__ double corrected_value(const double* __restrict__ u, const double* __restrict__ k0,
+// u + dt * sum_t w_t K_(j_t), in FP64 (eq. rk_schemes with the corrected weights
+// of eqs. fc_1 / fc_2)
+template <typename R>
+__device__ __forceinline__ double corrected_value(const double* __restrict__ u, const R* __restrict__ k0,
                                                   long long kstride, const StageTerms& t, double dt) {
   double acc = 0.0;
-  for (int q = 0; q < t.n; ++q) acc = fma(t.w[q], __ldg(k0 + t.j[q] * kstride), acc);
+  for (int q = 0; q < t.n; ++q) acc = fma(t.w[q], static_cast<double>(__ldg(k0 + t.j[q] * kstride)), acc);
   return fma(dt, acc, __ldg(u));
 }
 
 // tensor-product Lagrange interpolation, x then y then z; even coordinates are nodes
-__device__ double interp_tensor(const double* __restrict__ v, const double (*W)[7], int rx, int ry, int rz) {
+template <typename T>
+__device__ T interp_tensor(const T* __restrict__ v, const double (*W)[7], int rx, int ry, int rz) {
   const int x0 = (rx & 1) ? 0 : rx >> 1, x1 = (rx & 1) ? 6 : rx >> 1;
   const int y0 = (ry & 1) ? 0 : ry >> 1, y1 = (ry & 1) ? 6 : ry >> 1;
   const int z0 = (rz & 1) ? 0 : rz >> 1, z1 = (rz & 1) ? 6 : rz >> 1;
-  double sz = 0.0;
+  T sz = 0;
   for (int c = z0; c <= z1; ++c) {
-    double sy = 0.0;
+    T sy = 0;
     for (int bb = y0; bb <= y1; ++bb) {
-      double sx = 0.0;
-      for (int a = x0; a <= x1; ++a) sx = fma(W[rx][a], v[a + 7 * bb + 49 * c], sx);
-      sy = fma(W[ry][bb], sx, sy);
+      T sx = 0;
+      for (int a = x0; a <= x1; ++a) sx = fma(T(W[rx][a]), v[a + 7 * bb + 49 * c], sx);
+      sy = fma(T(W[ry][bb]), sx, sy);
     }
-    sz = fma(W[rz][c], sy, sz);
+    sz = fma(T(W[rz][c]), sy, sz);
   }
   return sz;
 }
@@ -213,9 +221,9 @@ __device__ __forceinline__ double lattice_to_x(double lo, double ext, int P6) {
 // ---------------------------------------------------------------------------
 // The stage kernel
 // ---------------------------------------------------------------------------
-template <int NF>
+template <int NF, typename R>
 struct StageSmem {
-  double T[NF][kNT];         // padded tiles
+  R T[NF][kNT];              // padded tiles
   StageTerms om[4];          // correction terms of this stage per relation
   int src[kNT];
   unsigned short code[kNT];  // rx | ry << 4 | rz << 8 | (level diff + 1) << 12 | exterior << 15
@@ -226,8 +234,8 @@ constexpr unsigned kExterior = 1u << 15;
 constexpr int kPer = (kNT + kThreads - 1) / kThreads;  // padded points per thread
 
 // exact boundary data (reading R10): RK stage values of the closed-form solution
-template <int NF>
-__device__ __noinline__ void fill_exact(StageSmem<NF>& S, const StageArgs& A, int4 me, int eb, double dtb) {
+template <int NF, typename R>
+__device__ __noinline__ void fill_exact(StageSmem<NF, R>& S, const StageArgs& A, int4 me, int eb, double dtb) {
   for (int q = threadIdx.x; q < kNT; q += blockDim.x) {
     if (!(S.code[q] & kExterior)) continue;
     const int i = q % 13 - 3, j = (q / 13) % 13 - 3, k = q / 169 - 3;
@@ -242,14 +250,14 @@ __device__ __noinline__ void fill_exact(StageSmem<NF>& S, const StageArgs& A, in
         dtp *= dtb;
         v = fma(A.gamma[m] * dtp, d[f][m + 1], v);
       }
-      S.T[f][q] = v;
+      S.T[f][q] = static_cast<R>(v);
     }
   }
 }
 
 // radiative boundary (reading R11): cubic extrapolation along the outward normal, x then y then z
-template <int NF>
-__device__ __noinline__ void fill_extrapolated(StageSmem<NF>& S, int4 me, int eb) {
+template <int NF, typename R>
+__device__ __noinline__ void fill_extrapolated(StageSmem<NF, R>& S, int4 me, int eb) {
   const int anchor[3] = {me.x, me.y, me.z};
   constexpr int kRoot = 1 << kDepth;
   for (int a = 0; a < 3; ++a) {
@@ -268,13 +276,13 @@ __device__ __noinline__ void fill_extrapolated(StageSmem<NF>& S, int4 me, int eb
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
           if (lo_b) {
-            double v = 0.0;
-            for (int qq = 0; qq < 4; ++qq) v = fma(c_E[m][qq], S.T[f][base + qq * str], v);
+            R v = 0;
+            for (int qq = 0; qq < 4; ++qq) v = fma(R(c_E[m][qq]), S.T[f][base + qq * str], v);
             S.T[f][base - m * str] = v;
           }
           if (hi_b) {
-            double v = 0.0;
-            for (int qq = 0; qq < 4; ++qq) v = fma(c_E[m][qq], S.T[f][base + (6 - qq) * str], v);
+            R v = 0;
+            for (int qq = 0; qq < 4; ++qq) v = fma(R(c_E[m][qq]), S.T[f][base + (6 - qq) * str], v);
             S.T[f][base + (6 + m) * str] = v;
           }
         }
@@ -285,30 +293,30 @@ __device__ __noinline__ void fill_extrapolated(StageSmem<NF>& S, int4 me, int eb
 }
 
 // radiative right-hand side at a node on the domain boundary
-template <int NF>
-__device__ __noinline__ void radiative_rhs(const StageSmem<NF>& S, const StageArgs& A, int c0, const int P6[3],
-                                           double inv12h, double kv[NF]) {
-  const double x[3] = {lattice_to_x(A.lo, A.ext, P6[0]), lattice_to_x(A.lo, A.ext, P6[1]),
-                       lattice_to_x(A.lo, A.ext, P6[2])};
-  const double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+template <int NF, typename R>
+__device__ __noinline__ void radiative_rhs(const StageSmem<NF, R>& S, const StageArgs& A, int c0, const int P6[3],
+                                           R inv12h, R kv[NF]) {
+  const R x[3] = {R(lattice_to_x(A.lo, A.ext, P6[0])), R(lattice_to_x(A.lo, A.ext, P6[1])),
+                  R(lattice_to_x(A.lo, A.ext, P6[2]))};
+  const R r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
   const int st[3] = {1, 13, 169};
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
-    const double* T = S.T[f];
-    double xd = 0.0;
+    const R* T = S.T[f];
+    R xd = 0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const double d1 = fma(8.0, T[c0 + st[a]] - T[c0 - st[a]], T[c0 - 2 * st[a]] - T[c0 + 2 * st[a]]) * inv12h;
+      const R d1 = fma(R(8), T[c0 + st[a]] - T[c0 - st[a]], T[c0 - 2 * st[a]] - T[c0 + 2 * st[a]]) * inv12h;
       xd = fma(x[a], d1, xd);
     }
-    kv[f] = -(xd + (f == 0 ? 1.0 : 2.0) * T[c0]) / r;
+    kv[f] = -(xd + (f == 0 ? R(1) : R(2)) * T[c0]) / r;
   }
 }
 
-template <int NF>
+template <int NF, typename R>
 __global__ void __launch_bounds__(kThreads, 4) stage_kernel(StageArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  StageSmem<NF>& S = *reinterpret_cast<StageSmem<NF>*>(smem_raw);
+  StageSmem<NF, R>& S = *reinterpret_cast<StageSmem<NF, R>*>(smem_raw);
   const int b = A.first + blockIdx.x;
   const int tid = threadIdx.x;
   const int p = A.p;
@@ -317,6 +325,7 @@ __global__ void __launch_bounds__(kThreads, 4) stage_kernel(StageArgs A) {
   const int lb = me.w;
   const int eb = 1 << (kDepth - lb);
   const long long kstride = (long long)A.nf * A.fstride;
+  R* __restrict__ K = static_cast<R*>(A.K);
 
   load_neighbours(A.tree, b, S.nv);
   if (tid < 4) S.om[tid] = A.om[tid];
@@ -355,15 +364,18 @@ __global__ void __launch_bounds__(kThreads, 4) stage_kernel(StageArgs A) {
 
   // 2. gathers, batched for memory parallelism: own interior and same-level sources
   //    read the stage inputs; coarser sources read their prolonged stage inputs
-  //    (Fig. unzip, prepared by prolong_kernel); under GTS every source is read directly
-  const double* direct = s == 0 ? A.u[(A.cur_mask >> lb) & 1] : A.Uin;
+  //    (prepared by prolong_kernel); under GTS every source is read directly.  At
+  //    stage 0 the stage input is the state u itself.
+  const R* Uin = static_cast<const R*>(A.Uin);
+  const double* u0 = A.u[(A.cur_mask >> lb) & 1];
+  const R* up_all = static_cast<const R*>(A.up);
   {
-    double v[kPer][NF];
+    R v[kPer][NF];
 #pragma unroll
     for (int it = 0; it < kPer; ++it) {
       const int q = tid + it * kThreads;
 #pragma unroll
-      for (int f = 0; f < NF; ++f) v[it][f] = 0.0;
+      for (int f = 0; f < NF; ++f) v[it][f] = 0;
       if (q < kNT) {
         const unsigned code = S.code[q];
         if (!(code & kExterior)) {
@@ -371,13 +383,18 @@ __global__ void __launch_bounds__(kThreads, 4) stage_kernel(StageArgs A) {
           const int rel_code = (code >> 12) & 3;  // 0 coarser, 1 same, 2 finer
           const int src = S.src[q];
           if (rel_code == 0) {
-            const double* up = A.up + (long long)__ldg(A.up_slot + src) * NF * kNT + rx + 13 * ry + 169 * rz;
+            const R* up = up_all + (long long)__ldg(A.up_slot + src) * NF * kNT + rx + 13 * ry + 169 * rz;
 #pragma unroll
             for (int f = 0; f < NF; ++f) v[it][f] = __ldg(up + f * kNT);
           } else if (rel_code == 1 || A.gts) {
             const long long off = (long long)src * kNV + (rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1);
+            if (s == 0) {
 #pragma unroll
-            for (int f = 0; f < NF; ++f) v[it][f] = __ldg(direct + f * A.fstride + off);
+              for (int f = 0; f < NF; ++f) v[it][f] = static_cast<R>(__ldg(u0 + f * A.fstride + off));
+            } else {
+#pragma unroll
+              for (int f = 0; f < NF; ++f) v[it][f] = __ldg(Uin + f * A.fstride + off);
+            }
           }
         }
       }
@@ -392,7 +409,7 @@ __global__ void __launch_bounds__(kThreads, 4) stage_kernel(StageArgs A) {
     }
   }
 
-  // 3. finer sources (injection) with the coarse<-fine correction of eq. fc_1
+  // 3. finer sources (injection) with the coarse<-fine correction of eq. fc_1 (FP64)
   if (!A.gts) {
     for (int q = tid; q < kNT; q += blockDim.x) {
       const unsigned code = S.code[q];
@@ -403,127 +420,128 @@ __global__ void __launch_bounds__(kThreads, 4) stage_kernel(StageArgs A) {
       const long long off = (long long)S.src[q] * kNV + (rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1);
 #pragma unroll
       for (int f = 0; f < NF; ++f)
-        S.T[f][q] = corrected_value(ub + f * A.fstride + off, A.K + f * A.fstride + off, kstride, S.om[1],
-                                    A.lc[ls].dt);
+        S.T[f][q] = static_cast<R>(corrected_value<R>(ub + f * A.fstride + off, K + f * A.fstride + off, kstride,
+                                                      S.om[1], A.lc[ls].dt));
     }
   }
   __syncthreads();
 
-  // 5. physical boundary
+  // 4. physical boundary
   const LevelConst lc = A.lc[lb];
   constexpr int kRoot = 1 << kDepth;
   const bool touches = me.x == 0 || me.y == 0 || me.z == 0 || me.x + eb == kRoot || me.y + eb == kRoot ||
                        me.z + eb == kRoot;
   if (touches) {
     if (A.bc == LTS_BC_EXACT)
-      fill_exact<NF>(S, A, me, eb, lc.dt);
+      fill_exact<NF, R>(S, A, me, eb, lc.dt);
     else
-      fill_extrapolated<NF>(S, me, eb);
+      fill_extrapolated<NF, R>(S, me, eb);
   }
   __syncthreads();
 
-  // 6. right-hand side on the 7^3 interior; stage, next stage input, fused RK update
+  // 5. right-hand side on the 7^3 interior (stage type R); stage, next stage input
+  //    and RK update (FP64)
   if (tid < kNV) {
     const int i = tid % 7, j = (tid / 7) % 7, k = tid / 49;
     const int c0 = (i + 3) + 13 * (j + 3) + 169 * (k + 3);
-    double kv[NF];
+    const R kos = R(lc.kos), inv12h = R(lc.inv12h), inv12h2 = R(lc.inv12h2);
+    R kv[NF];
     if (A.pde == LTS_PDE_ADVECTION) {
-      const double* T = S.T[0];
-      const double u0 = T[c0];
+      const R* T = S.T[0];
+      const R uc = T[c0];
       // symmetric pair sums at distance 1, 2, 3 (Kreiss-Oliger) and the D1 differences
-      const double P1 = (T[c0 - 1] + T[c0 + 1]) + (T[c0 - 13] + T[c0 + 13]) + (T[c0 - 169] + T[c0 + 169]);
-      const double P2 = (T[c0 - 2] + T[c0 + 2]) + (T[c0 - 26] + T[c0 + 26]) + (T[c0 - 338] + T[c0 + 338]);
-      const double P3 = (T[c0 - 3] + T[c0 + 3]) + (T[c0 - 39] + T[c0 + 39]) + (T[c0 - 507] + T[c0 + 507]);
-      double d1s = A.adv[0] * fma(8.0, T[c0 + 1] - T[c0 - 1], T[c0 - 2] - T[c0 + 2]);
-      d1s = fma(A.adv[1], fma(8.0, T[c0 + 13] - T[c0 - 13], T[c0 - 26] - T[c0 + 26]), d1s);
-      d1s = fma(A.adv[2], fma(8.0, T[c0 + 169] - T[c0 - 169], T[c0 - 338] - T[c0 + 338]), d1s);
-      const double ko = fma(-60.0, u0, fma(15.0, P1, fma(-6.0, P2, P3)));
-      kv[0] = fma(lc.kos, ko, -lc.inv12h * d1s);
+      const R P1 = (T[c0 - 1] + T[c0 + 1]) + (T[c0 - 13] + T[c0 + 13]) + (T[c0 - 169] + T[c0 + 169]);
+      const R P2 = (T[c0 - 2] + T[c0 + 2]) + (T[c0 - 26] + T[c0 + 26]) + (T[c0 - 338] + T[c0 + 338]);
+      const R P3 = (T[c0 - 3] + T[c0 + 3]) + (T[c0 - 39] + T[c0 + 39]) + (T[c0 - 507] + T[c0 + 507]);
+      R d1s = R(A.adv[0]) * fma(R(8), T[c0 + 1] - T[c0 - 1], T[c0 - 2] - T[c0 + 2]);
+      d1s = fma(R(A.adv[1]), fma(R(8), T[c0 + 13] - T[c0 - 13], T[c0 - 26] - T[c0 + 26]), d1s);
+      d1s = fma(R(A.adv[2]), fma(R(8), T[c0 + 169] - T[c0 - 169], T[c0 - 338] - T[c0 + 338]), d1s);
+      const R ko = fma(R(-60), uc, fma(R(15), P1, fma(R(-6), P2, P3)));
+      kv[0] = fma(kos, ko, -inv12h * d1s);
     } else {
-      const double* Tc = S.T[0];
-      const double* Tp = S.T[NF - 1];
-      const double c0v = Tc[c0], f0v = Tp[c0];
-      const double C1 = (Tc[c0 - 1] + Tc[c0 + 1]) + (Tc[c0 - 13] + Tc[c0 + 13]) + (Tc[c0 - 169] + Tc[c0 + 169]);
-      const double C2 = (Tc[c0 - 2] + Tc[c0 + 2]) + (Tc[c0 - 26] + Tc[c0 + 26]) + (Tc[c0 - 338] + Tc[c0 + 338]);
-      const double C3 = (Tc[c0 - 3] + Tc[c0 + 3]) + (Tc[c0 - 39] + Tc[c0 + 39]) + (Tc[c0 - 507] + Tc[c0 + 507]);
-      const double F1 = (Tp[c0 - 1] + Tp[c0 + 1]) + (Tp[c0 - 13] + Tp[c0 + 13]) + (Tp[c0 - 169] + Tp[c0 + 169]);
-      const double F2 = (Tp[c0 - 2] + Tp[c0 + 2]) + (Tp[c0 - 26] + Tp[c0 + 26]) + (Tp[c0 - 338] + Tp[c0 + 338]);
-      const double F3 = (Tp[c0 - 3] + Tp[c0 + 3]) + (Tp[c0 - 39] + Tp[c0 + 39]) + (Tp[c0 - 507] + Tp[c0 + 507]);
-      const double lap = fma(-90.0, c0v, fma(16.0, C1, -C2)) * lc.inv12h2;
-      const double koc = fma(-60.0, c0v, fma(15.0, C1, fma(-6.0, C2, C3)));
-      const double kop = fma(-60.0, f0v, fma(15.0, F1, fma(-6.0, F2, F3)));
-      kv[0] = fma(lc.kos, koc, f0v);
-      kv[NF - 1] = fma(lc.kos, kop, lap);
+      const R* Tc = S.T[0];
+      const R* Tp = S.T[NF - 1];
+      const R c0v = Tc[c0], f0v = Tp[c0];
+      const R C1 = (Tc[c0 - 1] + Tc[c0 + 1]) + (Tc[c0 - 13] + Tc[c0 + 13]) + (Tc[c0 - 169] + Tc[c0 + 169]);
+      const R C2 = (Tc[c0 - 2] + Tc[c0 + 2]) + (Tc[c0 - 26] + Tc[c0 + 26]) + (Tc[c0 - 338] + Tc[c0 + 338]);
+      const R C3 = (Tc[c0 - 3] + Tc[c0 + 3]) + (Tc[c0 - 39] + Tc[c0 + 39]) + (Tc[c0 - 507] + Tc[c0 + 507]);
+      const R F1 = (Tp[c0 - 1] + Tp[c0 + 1]) + (Tp[c0 - 13] + Tp[c0 + 13]) + (Tp[c0 - 169] + Tp[c0 + 169]);
+      const R F2 = (Tp[c0 - 2] + Tp[c0 + 2]) + (Tp[c0 - 26] + Tp[c0 + 26]) + (Tp[c0 - 338] + Tp[c0 + 338]);
+      const R F3 = (Tp[c0 - 3] + Tp[c0 + 3]) + (Tp[c0 - 39] + Tp[c0 + 39]) + (Tp[c0 - 507] + Tp[c0 + 507]);
+      const R lap = fma(R(-90), c0v, fma(R(16), C1, -C2)) * inv12h2;
+      const R koc = fma(R(-60), c0v, fma(R(15), C1, fma(R(-6), C2, C3)));
+      const R kop = fma(R(-60), f0v, fma(R(15), F1, fma(R(-6), F2, F3)));
+      kv[0] = fma(kos, koc, f0v);
+      kv[NF - 1] = fma(kos, kop, lap);
       if (A.bc == LTS_BC_RADIATIVE && touches) {
         const int P6[3] = {6 * me.x + i * eb, 6 * me.y + j * eb, 6 * me.z + k * eb};
         const bool on_bnd = P6[0] == 0 || P6[1] == 0 || P6[2] == 0 || P6[0] == kLatt6 || P6[1] == kLatt6 ||
                             P6[2] == kLatt6;
-        if (on_bnd) radiative_rhs<NF>(S, A, c0, P6, lc.inv12h, kv);
+        if (on_bnd) radiative_rhs<NF, R>(S, A, c0, P6, inv12h, kv);
       }
     }
     const long long node = (long long)b * kNV + tid;
-    const double* ucur = A.u[(A.cur_mask >> lb) & 1];
+    R* Uout = static_cast<R*>(A.Uout);
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       const long long o = f * A.fstride + node;
-      A.K[(long long)s * kstride + o] = kv[f];
+      K[(long long)s * kstride + o] = kv[f];
+      const double kd = static_cast<double>(kv[f]);
       if (s < p - 1) {
         // stage input of the next stage: u + dt sum_j a[s+1][j] k_j
         double acc = 0.0;
         for (int q = 0; q < A.next.n; ++q)
-          acc = fma(A.next.w[q], A.next.j[q] == s ? kv[f] : A.K[(long long)A.next.j[q] * kstride + o], acc);
-        A.Uout[o] = fma(lc.dt, acc, ucur[o]);
+          acc = fma(A.next.w[q], A.next.j[q] == s ? kd : static_cast<double>(K[(long long)A.next.j[q] * kstride + o]),
+                    acc);
+        Uout[o] = static_cast<R>(fma(lc.dt, acc, u0[o]));
       } else if (A.write_update) {
         double acc = 0.0;
-        for (int q = 0; q < p - 1; ++q) acc = fma(A.w[q], A.K[(long long)q * kstride + o], acc);
-        acc = fma(A.w[p - 1], kv[f], acc);
-        A.u[((A.cur_mask >> lb) & 1) ^ 1][o] = fma(lc.dt, acc, ucur[o]);
+        for (int q = 0; q < p - 1; ++q) acc = fma(A.w[q], static_cast<double>(K[(long long)q * kstride + o]), acc);
+        acc = fma(A.w[p - 1], kd, acc);
+        A.u[((A.cur_mask >> lb) & 1) ^ 1][o] = fma(lc.dt, acc, u0[o]);
       }
     }
   }
 }
 
-template <int NF>
-static size_t stage_smem() {
-  return sizeof(StageSmem<NF>);
+template <int NF, typename R>
+static cudaError_t launch_stage_t(const StageArgs& a, int count, cudaStream_t s) {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(stage_kernel<NF, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(StageSmem<NF, R>));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  stage_kernel<NF, R><<<count, kThreads, sizeof(StageSmem<NF, R>), s>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_stage(const StageArgs& a, int count, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(stage_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage_smem<1>());
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(stage_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage_smem<2>());
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
-  if (a.nf == 1)
-    stage_kernel<1><<<count, kThreads, stage_smem<1>(), s>>>(a);
-  else
-    stage_kernel<2><<<count, kThreads, stage_smem<2>(), s>>>(a);
-  return cudaGetLastError();
+  if (a.nf == 1) return a.mixed ? launch_stage_t<1, float>(a, count, s) : launch_stage_t<1, double>(a, count, s);
+  return a.mixed ? launch_stage_t<2, float>(a, count, s) : launch_stage_t<2, double>(a, count, s);
 }
 
 // ---------------------------------------------------------------------------
 // Prolongation of coarser sources (Fig. unzip, coarse -> fine).  One CTA per
 // octant with finer neighbours forms its stage inputs as those neighbours see
-// them (eqs. fc_1 / fc_2) and interpolates them, sum-factorised x, then y, then z,
-// to every half-node position of the box its finer neighbours read.  Each finer
-// neighbour then gathers these values as plain copies.
+// them (eqs. fc_1 / fc_2, FP64) and interpolates them, sum-factorised x, then y,
+// then z (stage type), to every half-node position of the box its finer
+// neighbours read.  Each finer neighbour then gathers these values as copies.
 // ---------------------------------------------------------------------------
-template <int NF>
+template <int NF, typename R>
 struct ProlongSmem {
-  double V[NF][kNV];
-  double X1[NF][13 * 49];      // [rx][z][y]
-  double X2[NF][13 * 13 * 7];  // [rx][ry][z]
-  double W[13][7];
+  R V[NF][kNV];
+  R X1[NF][13 * 49];      // [rx][z][y]
+  R X2[NF][13 * 13 * 7];  // [rx][ry][z]
+  R W[13][7];
 };
 
-template <int NF>
+template <int NF, typename R>
 __global__ void __launch_bounds__(256) prolong_kernel(ProlongArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  ProlongSmem<NF>& S = *reinterpret_cast<ProlongSmem<NF>*>(smem_raw);
+  ProlongSmem<NF, R>& S = *reinterpret_cast<ProlongSmem<NF, R>*>(smem_raw);
   const int tid = threadIdx.x;
   const int b = A.list[blockIdx.x];
   const int slot = A.up_slot[b];
@@ -533,26 +551,33 @@ __global__ void __launch_bounds__(256) prolong_kernel(ProlongArgs A) {
   const int rx0 = bx & 15, ry0 = (bx >> 8) & 15, rz0 = (bx >> 16) & 15;
   const int nrx = ((bx >> 4) & 15) - rx0 + 1, nry = ((bx >> 12) & 15) - ry0 + 1, nrz = ((bx >> 20) & 15) - rz0 + 1;
   const long long kstride = (long long)A.nf * A.fstride;
-  for (int q = tid; q < 91; q += blockDim.x) S.W[q / 7][q % 7] = c_W[q / 7][q % 7];
+  const R* K = static_cast<const R*>(A.K);
+  for (int q = tid; q < 91; q += blockDim.x) S.W[q / 7][q % 7] = R(c_W[q / 7][q % 7]);
   const int cur = (A.cur_mask >> lb) & 1;
-  const double* direct = A.stage == 0 ? A.u[cur] : A.Uin;
+  const R* Uin = static_cast<const R*>(A.Uin);
   const double* ub = A.u[cur ^ (rel == 3 ? 1 : 0)];
   for (int t = tid; t < NF * kNV; t += blockDim.x) {
     const int f = t / kNV, n = t - f * kNV;
     const long long off = (long long)b * kNV + n;
-    S.V[f][n] = rel == 0 ? __ldg(direct + f * A.fstride + off)
-                         : corrected_value(ub + f * A.fstride + off, A.K + f * A.fstride + off, kstride, A.om[rel],
-                                           A.lc[lb].dt);
+    R v;
+    if (rel != 0)
+      v = static_cast<R>(corrected_value<R>(ub + f * A.fstride + off, K + f * A.fstride + off, kstride, A.om[rel],
+                                            A.lc[lb].dt));
+    else if (A.stage == 0)
+      v = static_cast<R>(__ldg(A.u[cur] + f * A.fstride + off));
+    else
+      v = __ldg(Uin + f * A.fstride + off);
+    S.V[f][n] = v;
   }
   __syncthreads();
   for (int t = tid; t < NF * nrx * 49; t += blockDim.x) {
     const int f = t / (nrx * 49), rem = t - f * nrx * 49;
     const int rxi = rem / 49, yz = rem - rxi * 49;  // yz = y + 7 z
     const int rx = rx0 + rxi;
-    const double* v = S.V[f] + 7 * yz;
-    double acc;
+    const R* v = S.V[f] + 7 * yz;
+    R acc;
     if (rx & 1) {
-      acc = 0.0;
+      acc = 0;
 #pragma unroll
       for (int a = 0; a < 7; ++a) acc = fma(S.W[rx][a], v[a], acc);
     } else {
@@ -565,10 +590,10 @@ __global__ void __launch_bounds__(256) prolong_kernel(ProlongArgs A) {
     const int f = t / (nrx * nry * 7), rem = t - f * nrx * nry * 7;
     const int z = rem % 7, ryi = (rem / 7) % nry, rxi = rem / (7 * nry);
     const int ry = ry0 + ryi;
-    const double* x1 = S.X1[f] + rxi * 49 + 7 * z;  // [y]
-    double acc;
+    const R* x1 = S.X1[f] + rxi * 49 + 7 * z;  // [y]
+    R acc;
     if (ry & 1) {
-      acc = 0.0;
+      acc = 0;
 #pragma unroll
       for (int bb = 0; bb < 7; ++bb) acc = fma(S.W[ry][bb], x1[bb], acc);
     } else {
@@ -577,15 +602,15 @@ __global__ void __launch_bounds__(256) prolong_kernel(ProlongArgs A) {
     S.X2[f][rem] = acc;
   }
   __syncthreads();
-  double* out = A.up + (long long)slot * NF * kNT;
+  R* out = static_cast<R*>(A.up) + (long long)slot * NF * kNT;
   for (int t = tid; t < NF * nrx * nry * nrz; t += blockDim.x) {
     const int f = t / (nrx * nry * nrz), rem = t - f * nrx * nry * nrz;
     const int rxi = rem % nrx, ryi = (rem / nrx) % nry, rzi = rem / (nrx * nry);
     const int rz = rz0 + rzi;
-    const double* x2 = S.X2[f] + (rxi * nry + ryi) * 7;  // [z]
-    double acc;
+    const R* x2 = S.X2[f] + (rxi * nry + ryi) * 7;  // [z]
+    R acc;
     if (rz & 1) {
-      acc = 0.0;
+      acc = 0;
 #pragma unroll
       for (int cc = 0; cc < 7; ++cc) acc = fma(S.W[rz][cc], x2[cc], acc);
     } else {
@@ -595,30 +620,35 @@ __global__ void __launch_bounds__(256) prolong_kernel(ProlongArgs A) {
   }
 }
 
-cudaError_t launch_prolong(const ProlongArgs& a, cudaStream_t s) {
-  if (a.count <= 0) return cudaSuccess;
-  if (a.nf == 1)
-    prolong_kernel<1><<<a.count, 256, sizeof(ProlongSmem<1>), s>>>(a);
-  else
-    prolong_kernel<2><<<a.count, 256, sizeof(ProlongSmem<2>), s>>>(a);
+template <int NF, typename R>
+static cudaError_t launch_prolong_t(const ProlongArgs& a, cudaStream_t s) {
+  prolong_kernel<NF, R><<<a.count, 256, sizeof(ProlongSmem<NF, R>), s>>>(a);
   return cudaGetLastError();
 }
 
+cudaError_t launch_prolong(const ProlongArgs& a, cudaStream_t s) {
+  if (a.count <= 0) return cudaSuccess;
+  if (a.nf == 1) return a.mixed ? launch_prolong_t<1, float>(a, s) : launch_prolong_t<1, double>(a, s);
+  return a.mixed ? launch_prolong_t<2, float>(a, s) : launch_prolong_t<2, double>(a, s);
+}
+
 // ---------------------------------------------------------------------------
-// GTS step update (Alg. 1 compute_step) from the synchronised stages
+// GTS step update (Alg. 1 compute_step) from the synchronised stages, FP64
 // ---------------------------------------------------------------------------
+template <typename R>
 __global__ void update_kernel(UpdateArgs A) {
   const long long total = (long long)A.nf * A.fstride;
   const DevTables& tab = c_tab[A.scheme];
   const long long kstride = (long long)A.nf * A.fstride;
+  const R* K = static_cast<const R*>(A.K);
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const long long inf = e % A.fstride;
     const int b = int(inf / kNV);
     const int cur = (A.cur_mask >> A.oct[b].w) & 1;
     double acc = 0.0;
-    for (int q = 0; q < A.p - 1; ++q) acc = fma(tab.w[q], A.K[q * kstride + e], acc);
-    acc = fma(tab.w[A.p - 1], A.K[(A.p - 1) * kstride + e], acc);
+    for (int q = 0; q < A.p - 1; ++q) acc = fma(tab.w[q], static_cast<double>(K[q * kstride + e]), acc);
+    acc = fma(tab.w[A.p - 1], static_cast<double>(K[(A.p - 1) * kstride + e]), acc);
     A.u[cur ^ 1][e] = fma(A.dt_f, acc, A.u[cur][e]);
   }
 }
@@ -628,7 +658,10 @@ cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s) {
   const int threads = 256;
   long long blocks = (total + threads - 1) / threads;
   if (blocks > 152 * 32) blocks = 152 * 32;
-  update_kernel<<<(int)blocks, threads, 0, s>>>(a);
+  if (a.mixed)
+    update_kernel<float><<<(int)blocks, threads, 0, s>>>(a);
+  else
+    update_kernel<double><<<(int)blocks, threads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -644,6 +677,7 @@ __device__ __forceinline__ bool is_boundary_node(int i, int j, int k) {
 }
 
 // zip: every non-hanging node takes its owner's value (owners keep theirs)
+template <typename T>
 __global__ void __launch_bounds__(128) sync_zip_kernel(SyncArgs A) {
   __shared__ SyncSmem S;
   const int b = A.list ? A.list[blockIdx.x] : blockIdx.x;
@@ -665,8 +699,8 @@ __global__ void __launch_bounds__(128) sync_zip_kernel(SyncArgs A) {
       continue;
     }
     if ((rx | ry | rz) & 1) continue;
-    const double* vs = A.vb[(A.sel_mask >> so.w) & 1];
-    double* vd = A.vb[(A.sel_mask >> me.w) & 1];
+    const T* vs = static_cast<const T*>(A.vb[(A.sel_mask >> so.w) & 1]);
+    T* vd = static_cast<T*>(A.vb[(A.sel_mask >> me.w) & 1]);
     for (int f = 0; f < A.nf; ++f)
       vd[f * A.fstride + (long long)b * kNV + n] =
           vs[f * A.fstride + (long long)src * kNV + (rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1)];
@@ -675,6 +709,7 @@ __global__ void __launch_bounds__(128) sync_zip_kernel(SyncArgs A) {
 
 // unzip of hanging nodes of the listed octants (all of one level, whose coarser
 // sources are final)
+template <typename T>
 __global__ void __launch_bounds__(128) sync_hanging_kernel(SyncArgs A) {
   __shared__ SyncSmem S;
   const int b = A.list[blockIdx.x];
@@ -696,22 +731,29 @@ __global__ void __launch_bounds__(128) sync_hanging_kernel(SyncArgs A) {
       continue;
     }
     if (!((rx | ry | rz) & 1)) continue;
-    const double* vs = A.vb[(A.sel_mask >> so.w) & 1];
-    double* vd = A.vb[(A.sel_mask >> me.w) & 1];
+    const T* vs = static_cast<const T*>(A.vb[(A.sel_mask >> so.w) & 1]);
+    T* vd = static_cast<T*>(A.vb[(A.sel_mask >> me.w) & 1]);
     for (int f = 0; f < A.nf; ++f)
-      vd[f * A.fstride + (long long)b * kNV + n] = interp_tensor(vs + f * A.fstride + (long long)src * kNV, c_W, rx, ry, rz);
+      vd[f * A.fstride + (long long)b * kNV + n] =
+          interp_tensor<T>(vs + f * A.fstride + (long long)src * kNV, c_W, rx, ry, rz);
   }
 }
 
 cudaError_t launch_sync_zip(const SyncArgs& a, cudaStream_t s) {
   if (a.count <= 0) return cudaSuccess;
-  sync_zip_kernel<<<a.count, 128, 0, s>>>(a);
+  if (a.elem == 4)
+    sync_zip_kernel<float><<<a.count, 128, 0, s>>>(a);
+  else
+    sync_zip_kernel<double><<<a.count, 128, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sync_hanging(const SyncArgs& a, cudaStream_t s) {
   if (a.count <= 0) return cudaSuccess;
-  sync_hanging_kernel<<<a.count, 128, 0, s>>>(a);
+  if (a.elem == 4)
+    sync_hanging_kernel<float><<<a.count, 128, 0, s>>>(a);
+  else
+    sync_hanging_kernel<double><<<a.count, 128, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -795,6 +837,19 @@ __global__ void maps_kernel(MapArgs A) {
     A.src[o] = src;
     for (int a = 0; a < 3; ++a) A.r[o * 3 + a] = r[a];
   }
+}
+
+__global__ void widen_kernel(const float* __restrict__ in, double* __restrict__ out, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    out[e] = static_cast<double>(in[e]);
+}
+
+cudaError_t launch_widen(const float* in, double* out, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  widen_kernel<<<(int)blocks, 256, 0, s>>>(in, out, n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_maps(const MapArgs& a, cudaStream_t s) {

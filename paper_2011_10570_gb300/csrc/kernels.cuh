@@ -40,9 +40,9 @@ struct StageTerms {
 struct StageArgs {
   DevTree tree;
   double* u[2];          // double-buffered state [nf][N][343]; level l uses u[(cur_mask >> l) & 1]
-  double* K;             // RK stages [p][nf][N][343]
-  const double* Uin;     // stage inputs of this stage (stage >= 1), [nf][N][343]
-  double* Uout;          // stage inputs of the next stage, written by the epilogue
+  void* K;               // RK stages [p][nf][N][343] (stage type: double, or float when mixed)
+  const void* Uin;       // stage inputs of this stage (stage >= 1), [nf][N][343], stage type
+  void* Uout;            // stage inputs of the next stage, written by the epilogue, stage type
   long long fstride;     // N * 343
   int nf, p, stage;
   int first;             // first active octant (level order)
@@ -61,7 +61,8 @@ struct StageArgs {
   double gamma[4];       // gamma[stage][.] for exact boundary data
   IcParams icp;
   int* err;              // device error word: bit 0 source coordinate out of range
-  const double* up;      // prolonged stage inputs of coarser sources, [slot][nf][2197]
+  const void* up;        // prolonged stage inputs of coarser sources, [slot][nf][2197], stage type
+  int mixed;             // 1: FP32 stages, tile and right-hand side; FP64 state and corrections
   const int* up_slot;    // slot of an octant in `up` (-1: not a coarser source)
 };
 
@@ -75,12 +76,13 @@ struct ProlongArgs {
   int count;
   const int* box;        // per slot: packed half-node box rx0 | rx1 << 4 | ry0 << 8 | ry1 << 12 | rz0 << 16 | rz1 << 20
   const int* up_slot;
-  double* up;
+  void* up;
   const double* u[2];
-  const double* K;
-  const double* Uin;
+  const void* K;
+  const void* Uin;
   long long fstride;
   int nf, stage, lstar;
+  int mixed;
   unsigned cur_mask;
   int gts;
   LevelConst lc[32];
@@ -89,7 +91,8 @@ struct ProlongArgs {
 
 struct SyncArgs {
   DevTree tree;
-  double* vb[2];         // level l's array is vb[(sel_mask >> l) & 1]
+  void* vb[2];           // level l's array is vb[(sel_mask >> l) & 1]
+  int elem;              // element size of the arrays: 8 (double) or 4 (float)
   unsigned sel_mask;
   long long fstride;
   int nf;
@@ -100,7 +103,8 @@ struct SyncArgs {
 
 struct UpdateArgs {
   double* u[2];
-  const double* K;
+  const void* K;         // stage type
+  int mixed;
   long long fstride;
   int nf, p, scheme;
   int n;
@@ -136,6 +140,7 @@ cudaError_t launch_sync_hanging(const SyncArgs& a, cudaStream_t s);
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
 cudaError_t launch_init(const InitArgs& a, cudaStream_t s);
 cudaError_t launch_maps(const MapArgs& a, cudaStream_t s);
+cudaError_t launch_widen(const float* in, double* out, long long n, cudaStream_t s);
 
 // allocation-free padding-map export: largest octant list one call accepts
 constexpr int kStaticMapOctants = 32;
