@@ -169,6 +169,79 @@ def run_reference(args, w, world, rank, pg):
     print(json.dumps(line), flush=True)
 
 
+def schedule_work(st, n_sub0, rounds):
+    """node-updates of `rounds` substeps of one plan starting at substep n_sub0 (Fig. blk_loop)"""
+    lmin, lmax = st["l_min"], st["l_max"]
+    counts = st["octants_per_level"]
+    nsub = 2 ** (lmax - lmin)
+    total, n = 0, n_sub0
+    for _ in range(rounds):
+        lstar = next(l for l in range(lmin, lmax + 1) if n % (2 ** (lmax - l)) == 0)
+        total += 343 * sum(counts[lstar:lmax + 1])
+        n = (n + 1) % nsub
+    return total
+
+
+def run_batch(args):
+    """Batched instances (NEXT-2): one persistent launch per stage covers all instances;
+    rounds replayed from a captured CUDA graph; grid shapes autotuned."""
+    import numpy as np
+    import torch
+
+    from paper_2011_10570_gb300 import build, ltsoct, workloads
+    build.build()
+    torch.cuda.set_device(0)
+    ws = workloads.batch_instances(seed=3, n=args.batch)
+    stream = torch.cuda.current_stream()
+    plans = [ltsoct.Plan(ltsoct.Octree(w["spec"]), w["prob"], stream=stream) for w in ws]
+    sts = [p.stats() for p in plans]
+    for p in plans:
+        p.set_initial(0.0)
+    batch = ltsoct.Batch(plans)
+    tune = batch.autotune(rounds=4)
+    rounds = args.rounds
+    for p in plans:
+        p.set_initial(0.0)
+    batch.run([args.warmup] * len(plans))
+    torch.cuda.synchronize()
+    n0 = [p.stats()["substep"] for p in plans]
+    work = sum(schedule_work(st, n, rounds) for st, n in zip(sts, n0))
+    l0 = batch.stats()["launches"]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        ev0.record(stream)
+        batch.run([rounds] * len(plans), graph=True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = batch.stats()["launches"] - l0
+    # the same work one instance at a time (per-plan launches, no batching)
+    for p in plans:
+        p.set_initial(0.0)
+        p.run_substeps(args.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for p in plans:
+        p.run_substeps(rounds)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_alone = e0.elapsed_time(e1)
+    n_oct = [st["n_octants"] for st in sts]
+    line = {
+        "metric": "batched LTS octant-node updates/s", "value": work / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+        "steps": rounds, "warmup": args.warmup, "ms_per_step": ms / rounds, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "batch of %d instances (seed 3)" % len(plans), "octants_min": min(n_oct),
+                   "octants_median": int(np.median(n_oct)), "octants_max": max(n_oct),
+                   "levels": "3..6-11", "step": "one round: one substep of every instance"},
+        "gpu_launches": launches, "graph": True, "autotuned_grid": tune["grid"],
+        "one_at_a_time": {"value": work / (ms_alone / 1e3), "ms_per_step": ms_alone / rounds},
+        "batch_speedup": ms_alone / ms, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -178,12 +251,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--gts", action="store_true", help="also time GTS over the same physical time")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--batch", type=int, default=0, help="batched mode: number of instances (64 for the C4 workload)")
+    ap.add_argument("--rounds", type=int, default=64, help="batched mode: timed rounds")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="mixed: FP32 stages and right-hand side, FP64 state and time corrections")
     ap.add_argument("--lmax", type=int, default=9,
                     help="finest level of the wave workload (9: the benchmark configuration; 8: the profiling case)")
     args = ap.parse_args()
 
+    if args.batch:
+        return run_batch(args)
     from paper_2011_10570_gb300 import workloads
     w = workloads.wave_shell(l_max=args.lmax)
     if args.precision == "mixed":

@@ -196,6 +196,26 @@ lts_status lts_set_profiling(lts_plan* plan, int on);
 lts_status lts_kernel_stats(lts_plan* plan, int64_t* launches, double* ms, double* flops, double* bytes,
                             int64_t* node_stages, int reset);
 
+/* ---- batches: many independent solves advanced together (NEXT-2) ------------------ */
+/* A batch advances several plans together in rounds: in each round every plan with
+ * substeps left performs one LTS substep of its own schedule (Alg. 2, Fig. blk_loop);
+ * each RK stage of a round is one persistent launch (a fixed grid looping over the
+ * active octants of all plans) of the prolongation and of the stage kernels, and the
+ * schedule is advanced on the device, so a round is a fixed launch sequence that can be
+ * captured once in a CUDA graph and replayed.  Results equal those of running each
+ * plan alone.  The plans must share one stream and one precision; the batch keeps
+ * pointers to them (they must outlive it).  Up to 1024 plans. */
+typedef struct lts_batch lts_batch;
+lts_status lts_batch_create(lts_plan* const* plans, int n, lts_batch** out);
+void lts_batch_destroy(lts_batch* batch);
+/* Advance plan i by substeps[i] substeps (host array of n counts), in max(substeps)
+ * rounds.  use_graph: replay one captured round.  Asynchronous on the plans' stream. */
+lts_status lts_batch_run(lts_batch* batch, const int64_t* substeps, int use_graph);
+/* Grid sizes of the persistent launches (CTAs); set by an autotuner or by hand. */
+lts_status lts_batch_set_grid(lts_batch* batch, int grid_stage, int grid_prolong, int grid_sync);
+lts_status lts_batch_stats(const lts_batch* batch, int64_t* launches, int* grid_stage, int* grid_prolong,
+                           int* grid_sync);
+
 const char* lts_strerror(lts_status s);
 const char* lts_last_error(void);
 

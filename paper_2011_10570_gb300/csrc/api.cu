@@ -854,3 +854,236 @@ lts_status lts_kernel_stats(lts_plan* P, int64_t* launches, double* ms, double* 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches: many plans advanced together, one persistent launch per stage
+// ---------------------------------------------------------------------------
+struct lts_batch {
+  std::vector<lts_plan*> plans;
+  cudaStream_t stream = nullptr;     // the plans' stream
+  cudaStream_t cap = nullptr;        // stream the rounds run on (capturable)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  ltsoct::BatchInst* d_inst = nullptr;
+  int* d_pre = nullptr;
+  ltsoct::BatchArgs args{};
+  int pmax = 0, lmax_all = 0, mixed = 0;
+  int grid_stage = 152 * 4, grid_prolong = 152 * 6, grid_sync = 152 * 8;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches = 0;
+};
+
+namespace {
+
+lts_status batch_round(lts_batch* B, bool graph) {
+  if (graph) {
+    if (!B->exec) {
+      CK(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+      cudaError_t e = ltsoct::launch_batch_round(B->args, B->pmax, B->lmax_all, B->grid_stage, B->grid_prolong,
+                                                 B->grid_sync, B->mixed, B->cap);
+      cudaGraph_t g = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(B->cap, &g);
+      if (e != cudaSuccess) return cuda_fail(e, "batch round capture");
+      if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+      B->graph = g;
+      CK(cudaGraphInstantiate(&B->exec, g, 0), "cudaGraphInstantiate");
+    }
+    CK(cudaGraphLaunch(B->exec, B->cap), "cudaGraphLaunch");
+  } else {
+    CK(ltsoct::launch_batch_round(B->args, B->pmax, B->lmax_all, B->grid_stage, B->grid_prolong, B->grid_sync,
+                                  B->mixed, B->cap),
+       "batch round launch");
+  }
+  B->launches += 3 + 2 * B->pmax + B->lmax_all;
+  return LTS_OK;
+}
+
+// the host's copy of a plan's schedule, advanced by n substeps (the same arithmetic
+// the device applies in batch_round_end)
+void advance_host_schedule(lts_plan* P, int64_t n) {
+  for (int64_t i = 0; i < n; ++i) {
+    const int lstar = active_level(P, P->n_sub);
+    for (int l = lstar; l <= P->lmax; ++l) P->cur_mask ^= 1u << l;
+    P->n_sub++;
+    if (P->n_sub == (int64_t(1) << (P->lmax - P->lmin))) {
+      P->t_macro += double(P->n_sub) * P->dt_f;
+      P->n_sub = 0;
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+lts_status lts_batch_create(lts_plan* const* plans, int n, lts_batch** out) {
+  if (!plans || !out || n < 1 || n > ltsoct::kMaxBatch) return fail(LTS_EINVAL, "lts_batch_create: 1..1024 plans");
+  *out = nullptr;
+  lts_batch* B = new (std::nothrow) lts_batch();
+  if (!B) return fail(LTS_ENOMEM, "lts_batch_create: out of host memory");
+  B->stream = plans[0]->stream;
+  B->mixed = plans[0]->mixed;
+  for (int i = 0; i < n; ++i) {
+    lts_plan* P = plans[i];
+    if (!P || P->stream != B->stream || P->mixed != B->mixed) {
+      delete B;
+      return fail(LTS_EINVAL, "lts_batch_create: plans must be valid and share one stream and one precision");
+    }
+    B->plans.push_back(P);
+    B->pmax = std::max(B->pmax, P->p);
+    B->lmax_all = std::max(B->lmax_all, P->lmax);
+  }
+  std::vector<ltsoct::BatchInst> h(n);
+  for (int i = 0; i < n; ++i) {
+    lts_plan* P = plans[i];
+    ltsoct::BatchInst& I = h[i];
+    std::memset(&I, 0, sizeof(I));
+    for (int s = 0; s < 4; ++s) {
+      const int ss = std::min(s, P->p - 1);
+      I.st[s] = stage_args(P, ss, 0, P->lmin, 0);
+      ltsoct::ProlongArgs& a = I.pr[s];
+      a.tree = I.st[s].tree;
+      a.box = P->d_up_box;
+      a.up_slot = P->d_up_slot;
+      a.up = P->d_up;
+      a.u[0] = P->d_u[0];
+      a.u[1] = P->d_u[1];
+      a.K = P->d_K;
+      a.Uin = I.st[s].Uin;
+      a.fstride = P->N * kNV;
+      a.nf = P->nf;
+      a.stage = ss;
+      a.gts = 0;
+      a.mixed = P->mixed;
+      for (int l = 0; l < 32; ++l) a.lc[l] = I.st[s].lc[l];
+      for (int r = 0; r < 4; ++r) a.om[r] = I.st[s].om[r];
+    }
+    for (ltsoct::SyncArgs* y : {&I.zip, &I.hang}) {
+      y->tree = I.st[0].tree;
+      y->vb[0] = P->d_u[0];
+      y->vb[1] = P->d_u[1];
+      y->elem = 8;
+      y->fstride = P->N * kNV;
+      y->nf = P->nf;
+      y->list = nullptr;
+      y->err = P->d_err;
+    }
+    I.up_list = P->d_up_list;
+    I.hang_list = P->d_hang;
+    for (int l = 0; l < 34; ++l) {
+      I.off[l] = int(P->off[l]);
+      I.up_off[l] = int(P->up_off[l]);
+      I.hang_off[l] = int(P->hang_off[l]);
+    }
+    I.n = int(P->N);
+    I.nf = P->nf;
+    I.p = P->p;
+    I.lmin = P->lmin;
+    I.lmax = P->lmax;
+    I.nsub_macro = int64_t(1) << (P->lmax - P->lmin);
+    I.n_sub = P->n_sub;
+    I.remaining = 0;
+    I.t_macro = P->t_macro;
+    I.dt_f = P->dt_f;
+    I.cur_mask = P->cur_mask;
+  }
+  const size_t pre_ints = size_t(ltsoct::kMaxBatch + 1) * (4 + 4 + 1 + ltsoct::kMaxLevel + 2);
+  cudaError_t e = ltsoct::prepare_batch_kernels();
+  if (e == cudaSuccess) e = cudaMalloc(&B->d_inst, sizeof(ltsoct::BatchInst) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&B->d_pre, sizeof(int) * pre_ints);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_out, cudaEventDisableTiming);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(B->d_inst, h.data(), sizeof(ltsoct::BatchInst) * n, cudaMemcpyHostToDevice, B->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(B->d_pre, 0, sizeof(int) * pre_ints, B->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
+  if (e != cudaSuccess) {
+    lts_batch_destroy(B);
+    return cuda_fail(e, "lts_batch_create");
+  }
+  B->args.inst = B->d_inst;
+  B->args.n = n;
+  B->args.stage_pre = B->d_pre;
+  B->args.prol_pre = B->d_pre + 4 * (ltsoct::kMaxBatch + 1);
+  B->args.zip_pre = B->d_pre + 8 * (ltsoct::kMaxBatch + 1);
+  B->args.hang_pre = B->d_pre + 9 * (ltsoct::kMaxBatch + 1);
+  *out = B;
+  return LTS_OK;
+}
+
+void lts_batch_destroy(lts_batch* B) {
+  if (!B) return;
+  if (B->cap) cudaStreamSynchronize(B->cap);
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  if (B->graph) cudaGraphDestroy(B->graph);
+  if (B->ev_in) cudaEventDestroy(B->ev_in);
+  if (B->ev_out) cudaEventDestroy(B->ev_out);
+  if (B->cap) cudaStreamDestroy(B->cap);
+  if (B->d_inst) cudaFree(B->d_inst);
+  if (B->d_pre) cudaFree(B->d_pre);
+  delete B;
+}
+
+lts_status lts_batch_set_grid(lts_batch* B, int grid_stage, int grid_prolong, int grid_sync) {
+  if (!B || grid_stage < 1 || grid_prolong < 1 || grid_sync < 1) return fail(LTS_EINVAL, "lts_batch_set_grid: bad argument");
+  B->grid_stage = grid_stage;
+  B->grid_prolong = grid_prolong;
+  B->grid_sync = grid_sync;
+  if (B->exec) {
+    cudaGraphExecDestroy(B->exec);
+    B->exec = nullptr;
+  }
+  if (B->graph) {
+    cudaGraphDestroy(B->graph);
+    B->graph = nullptr;
+  }
+  return LTS_OK;
+}
+
+lts_status lts_batch_run(lts_batch* B, const int64_t* substeps, int use_graph) {
+  if (!B || !substeps) return fail(LTS_EINVAL, "lts_batch_run: null argument");
+  const int n = int(B->plans.size());
+  int64_t rounds = 0;
+  for (int i = 0; i < n; ++i) {
+    if (substeps[i] < 0) return fail(LTS_EINVAL, "lts_batch_run: negative substep count");
+    rounds = std::max(rounds, substeps[i]);
+  }
+  // the plans' work so far precedes the rounds
+  CK(cudaEventRecord(B->ev_in, B->stream), "cudaEventRecord");
+  CK(cudaStreamWaitEvent(B->cap, B->ev_in, 0), "cudaStreamWaitEvent");
+  for (int i = 0; i < n; ++i) {
+    ltsoct::BatchInst* I = B->d_inst + i;
+    lts_plan* P = B->plans[i];
+    // the host schedule of the plan is authoritative at the start of a run
+    const long long nsub = P->n_sub, rem = substeps[i];
+    const double tm = P->t_macro;
+    const unsigned cm = P->cur_mask;
+    CK(cudaMemcpyAsync(&I->n_sub, &nsub, sizeof(nsub), cudaMemcpyHostToDevice, B->cap), "copy");
+    CK(cudaMemcpyAsync(&I->remaining, &rem, sizeof(rem), cudaMemcpyHostToDevice, B->cap), "copy");
+    CK(cudaMemcpyAsync(&I->t_macro, &tm, sizeof(tm), cudaMemcpyHostToDevice, B->cap), "copy");
+    CK(cudaMemcpyAsync(&I->cur_mask, &cm, sizeof(cm), cudaMemcpyHostToDevice, B->cap), "copy");
+    CK(cudaStreamSynchronize(B->cap), "cudaStreamSynchronize");  // host sources go out of scope
+  }
+  for (int64_t r = 0; r < rounds; ++r) {
+    lts_status st = batch_round(B, use_graph != 0);
+    if (st != LTS_OK) return st;
+  }
+  CK(cudaEventRecord(B->ev_out, B->cap), "cudaEventRecord");
+  CK(cudaStreamWaitEvent(B->stream, B->ev_out, 0), "cudaStreamWaitEvent");
+  for (int i = 0; i < n; ++i) {
+    advance_host_schedule(B->plans[i], substeps[i]);
+  }
+  return LTS_OK;
+}
+
+lts_status lts_batch_stats(const lts_batch* B, int64_t* launches, int* grid_stage, int* grid_prolong, int* grid_sync) {
+  if (!B) return fail(LTS_EINVAL, "lts_batch_stats: null batch");
+  if (launches) *launches = B->launches;
+  if (grid_stage) *grid_stage = B->grid_stage;
+  if (grid_prolong) *grid_prolong = B->grid_prolong;
+  if (grid_sync) *grid_sync = B->grid_sync;
+  return LTS_OK;
+}
+
+}  // extern "C"

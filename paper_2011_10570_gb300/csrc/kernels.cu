@@ -313,11 +313,10 @@ __device__ __noinline__ void radiative_rhs(const StageSmem<NF, R>& S, const Stag
   }
 }
 
+// One RK stage of octant b (Alg. 2 compute_stage, or Alg. 1 when A.gts): called by
+// every thread of a CTA of kThreads threads, with S in shared memory.
 template <int NF, typename R>
-__global__ void __launch_bounds__(kThreads, 4) stage_kernel(StageArgs A) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  StageSmem<NF, R>& S = *reinterpret_cast<StageSmem<NF, R>*>(smem_raw);
-  const int b = A.first + blockIdx.x;
+__device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int b) {
   const int tid = threadIdx.x;
   const int p = A.p;
   const int s = A.stage;
@@ -505,6 +504,13 @@ __global__ void __launch_bounds__(kThreads, 4) stage_kernel(StageArgs A) {
 }
 
 template <int NF, typename R>
+__global__ void __launch_bounds__(kThreads, 4) stage_kernel(const __grid_constant__ StageArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  StageSmem<NF, R>& S = *reinterpret_cast<StageSmem<NF, R>*>(smem_raw);
+  stage_octant<NF, R>(S, A, A.first + blockIdx.x);
+}
+
+template <int NF, typename R>
 static cudaError_t launch_stage_t(const StageArgs& a, int count, cudaStream_t s) {
   static bool configured = false;
   if (!configured) {
@@ -538,12 +544,10 @@ struct ProlongSmem {
   R W[13][7];
 };
 
+// Prolongation of octant b for one stage; called by every thread of a CTA.
 template <int NF, typename R>
-__global__ void __launch_bounds__(256) prolong_kernel(ProlongArgs A) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  ProlongSmem<NF, R>& S = *reinterpret_cast<ProlongSmem<NF, R>*>(smem_raw);
+__device__ void prolong_octant(ProlongSmem<NF, R>& S, const ProlongArgs& A, const int b) {
   const int tid = threadIdx.x;
-  const int b = A.list[blockIdx.x];
   const int slot = A.up_slot[b];
   const int lb = A.tree.oct[b].w;
   const int rel = A.gts ? 0 : (lb >= A.lstar ? 2 : 3);
@@ -621,6 +625,13 @@ __global__ void __launch_bounds__(256) prolong_kernel(ProlongArgs A) {
 }
 
 template <int NF, typename R>
+__global__ void __launch_bounds__(256) prolong_kernel(const __grid_constant__ ProlongArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ProlongSmem<NF, R>& S = *reinterpret_cast<ProlongSmem<NF, R>*>(smem_raw);
+  prolong_octant<NF, R>(S, A, A.list[blockIdx.x]);
+}
+
+template <int NF, typename R>
 static cudaError_t launch_prolong_t(const ProlongArgs& a, cudaStream_t s) {
   prolong_kernel<NF, R><<<a.count, 256, sizeof(ProlongSmem<NF, R>), s>>>(a);
   return cudaGetLastError();
@@ -678,9 +689,7 @@ __device__ __forceinline__ bool is_boundary_node(int i, int j, int k) {
 
 // zip: every non-hanging node takes its owner's value (owners keep theirs)
 template <typename T>
-__global__ void __launch_bounds__(128) sync_zip_kernel(SyncArgs A) {
-  __shared__ SyncSmem S;
-  const int b = A.list ? A.list[blockIdx.x] : blockIdx.x;
+__device__ void sync_zip_octant(SyncSmem& S, const SyncArgs& A, const int b) {
   load_neighbours(A.tree, b, S.nv);
   __syncthreads();
   const int4 me = A.tree.oct[b];
@@ -710,9 +719,7 @@ __global__ void __launch_bounds__(128) sync_zip_kernel(SyncArgs A) {
 // unzip of hanging nodes of the listed octants (all of one level, whose coarser
 // sources are final)
 template <typename T>
-__global__ void __launch_bounds__(128) sync_hanging_kernel(SyncArgs A) {
-  __shared__ SyncSmem S;
-  const int b = A.list[blockIdx.x];
+__device__ void sync_hanging_octant(SyncSmem& S, const SyncArgs& A, const int b) {
   load_neighbours(A.tree, b, S.nv);
   __syncthreads();
   const int4 me = A.tree.oct[b];
@@ -739,6 +746,18 @@ __global__ void __launch_bounds__(128) sync_hanging_kernel(SyncArgs A) {
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(128) sync_zip_kernel(const __grid_constant__ SyncArgs A) {
+  __shared__ SyncSmem S;
+  sync_zip_octant<T>(S, A, A.list ? A.list[blockIdx.x] : blockIdx.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) sync_hanging_kernel(const __grid_constant__ SyncArgs A) {
+  __shared__ SyncSmem S;
+  sync_hanging_octant<T>(S, A, A.list[blockIdx.x]);
+}
+
 cudaError_t launch_sync_zip(const SyncArgs& a, cudaStream_t s) {
   if (a.count <= 0) return cudaSuccess;
   if (a.elem == 4)
@@ -755,6 +774,186 @@ cudaError_t launch_sync_hanging(const SyncArgs& a, cudaStream_t s) {
   else
     sync_hanging_kernel<double><<<a.count, 128, 0, s>>>(a);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Batches (many instances advanced together).  A round advances every instance
+// with substeps left by one substep of its own schedule (Fig. blk_loop): one
+// persistent launch per stage covers the active octants of all instances.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int batch_find(const int* pre, int n, int item) {
+  // largest i with pre[i] <= item (pre is non-decreasing, pre[0] = 0)
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(pre + mid) <= item)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void batch_round_begin(BatchArgs B) {
+  const int i = threadIdx.x;
+  if (i < B.n) {
+    BatchInst& I = B.inst[i];
+    I.reconcile = 0;
+    I.active = I.remaining > 0;
+    int lstar = I.lmax;
+    for (int l = I.lmin; l <= I.lmax; ++l)
+      if (I.n_sub % (1ll << (I.lmax - l)) == 0) {
+        lstar = l;
+        break;
+      }
+    I.lstar = lstar;
+    const double t_b = I.t_macro + double(I.n_sub) * I.dt_f;
+    const int lo = max(lstar - 1, I.lmin), hi = I.lmax - 1;
+    for (int s = 0; s < 4; ++s) {
+      StageArgs& A = I.st[s];
+      A.first = I.off[lstar];
+      A.lstar = lstar;
+      A.cur_mask = I.cur_mask;
+      A.t_b = t_b;
+      ProlongArgs& P = I.pr[s];
+      P.list = I.up_list + I.up_off[lo];
+      P.count = hi >= lo ? I.up_off[hi + 1] - I.up_off[lo] : 0;
+      P.lstar = lstar;
+      P.cur_mask = I.cur_mask;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 4; ++s) {
+      int* sp = B.stage_pre + s * (kMaxBatch + 1);
+      int* pp = B.prol_pre + s * (kMaxBatch + 1);
+      sp[0] = pp[0] = 0;
+      for (int k = 0; k < B.n; ++k) {
+        const BatchInst& I = B.inst[k];
+        const bool on = I.active && s < I.p;
+        sp[k + 1] = sp[k] + (on ? I.n - I.off[I.lstar] : 0);
+        pp[k + 1] = pp[k] + (on ? I.pr[s].count : 0);
+      }
+    }
+  }
+}
+
+__global__ void batch_round_end(BatchArgs B) {
+  const int i = threadIdx.x;
+  if (i < B.n) {
+    BatchInst& I = B.inst[i];
+    if (I.active) {
+      for (int l = I.lstar; l <= I.lmax; ++l) I.cur_mask ^= 1u << l;
+      I.n_sub++;
+      I.remaining--;
+      if (I.n_sub == I.nsub_macro) {
+        I.reconcile = 1;
+        I.t_macro += double(I.n_sub) * I.dt_f;
+        I.n_sub = 0;
+      }
+    }
+    I.zip.sel_mask = I.cur_mask;
+    I.hang.sel_mask = I.cur_mask;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    B.zip_pre[0] = 0;
+    for (int k = 0; k < B.n; ++k) B.zip_pre[k + 1] = B.zip_pre[k] + (B.inst[k].reconcile ? B.inst[k].n : 0);
+    for (int l = 0; l <= kMaxLevel + 1; ++l) {
+      int* hp = B.hang_pre + l * (kMaxBatch + 1);
+      hp[0] = 0;
+      for (int k = 0; k < B.n; ++k) {
+        const BatchInst& I = B.inst[k];
+        const int c = (I.reconcile && l <= 32) ? I.hang_off[l + 1] - I.hang_off[l] : 0;
+        hp[k + 1] = hp[k] + c;
+      }
+    }
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads, 4) batch_stage_kernel(const __grid_constant__ BatchArgs B, int stage) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int* pre = B.stage_pre + stage * (kMaxBatch + 1);
+  const int total = pre[B.n];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int i = batch_find(pre, B.n + 1, item);
+    const StageArgs& A = B.inst[i].st[stage];
+    const int b = A.first + (item - pre[i]);
+    if (A.nf == 1)
+      stage_octant<1, R>(*reinterpret_cast<StageSmem<1, R>*>(smem_raw), A, b);
+    else
+      stage_octant<2, R>(*reinterpret_cast<StageSmem<2, R>*>(smem_raw), A, b);
+    __syncthreads();
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) batch_prolong_kernel(const __grid_constant__ BatchArgs B, int stage) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int* pre = B.prol_pre + stage * (kMaxBatch + 1);
+  const int total = pre[B.n];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int i = batch_find(pre, B.n + 1, item);
+    const ProlongArgs& A = B.inst[i].pr[stage];
+    const int b = A.list[item - pre[i]];
+    if (A.nf == 1)
+      prolong_octant<1, R>(*reinterpret_cast<ProlongSmem<1, R>*>(smem_raw), A, b);
+    else
+      prolong_octant<2, R>(*reinterpret_cast<ProlongSmem<2, R>*>(smem_raw), A, b);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(128) batch_zip_kernel(const __grid_constant__ BatchArgs B) {
+  __shared__ SyncSmem S;
+  const int total = B.zip_pre[B.n];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int i = batch_find(B.zip_pre, B.n + 1, item);
+    sync_zip_octant<double>(S, B.inst[i].zip, item - B.zip_pre[i]);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(128) batch_hanging_kernel(const __grid_constant__ BatchArgs B, int level) {
+  __shared__ SyncSmem S;
+  const int* pre = B.hang_pre + level * (kMaxBatch + 1);
+  const int total = pre[B.n];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int i = batch_find(pre, B.n + 1, item);
+    const BatchInst& I = B.inst[i];
+    sync_hanging_octant<double>(S, I.hang, I.hang_list[I.hang_off[level] + (item - pre[i])]);
+    __syncthreads();
+  }
+}
+
+cudaError_t prepare_batch_kernels() {
+  cudaError_t e = cudaFuncSetAttribute(batch_stage_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(StageSmem<2, double>));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(batch_stage_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sizeof(StageSmem<2, float>));
+}
+
+template <typename R>
+static cudaError_t batch_round_t(const BatchArgs& a, int pmax, int lmax_all, int gs, int gp, int gy, cudaStream_t s) {
+  const size_t smem_stage = sizeof(StageSmem<2, R>);
+  const size_t smem_prol = sizeof(ProlongSmem<2, R>);
+  batch_round_begin<<<1, kMaxBatch, 0, s>>>(a);
+  for (int st = 0; st < pmax; ++st) {
+    batch_prolong_kernel<R><<<gp, 256, smem_prol, s>>>(a, st);
+    batch_stage_kernel<R><<<gs, kThreads, smem_stage, s>>>(a, st);
+  }
+  batch_round_end<<<1, kMaxBatch, 0, s>>>(a);
+  batch_zip_kernel<<<gy, 128, 0, s>>>(a);
+  for (int l = 1; l <= lmax_all; ++l) batch_hanging_kernel<<<gy, 128, 0, s>>>(a, l);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_round(const BatchArgs& a, int pmax, int lmax_all, int grid_stage, int grid_prolong,
+                               int grid_sync, int mixed, cudaStream_t s) {
+  return mixed ? batch_round_t<float>(a, pmax, lmax_all, grid_stage, grid_prolong, grid_sync, s)
+               : batch_round_t<double>(a, pmax, lmax_all, grid_stage, grid_prolong, grid_sync, s);
 }
 
 // ---------------------------------------------------------------------------

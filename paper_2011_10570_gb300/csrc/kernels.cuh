@@ -132,6 +132,45 @@ struct MapArgs {
   int* r;
 };
 
+// ---- batches: many instances advanced together ------------------------------
+// Device-resident descriptor of one instance of a batch.  The static parts are
+// written by the host at batch creation; the schedule fields are advanced on the
+// device by batch_round_begin / batch_round_end, so that a round is a fixed
+// sequence of launches (capturable in a CUDA graph).
+struct BatchInst {
+  StageArgs st[4];       // per stage
+  ProlongArgs pr[4];     // per stage
+  SyncArgs zip, hang;    // reconcile of the state at the end of a macro step
+  const int* up_list;
+  const int* hang_list;
+  int off[34];           // level offsets (level order)
+  int up_off[34];        // per-level ranges of up_list
+  int hang_off[34];      // per-level ranges of hang_list
+  int n, nf, p, lmin, lmax;
+  long long nsub_macro;  // substeps per macro step, 2^(lmax - lmin)
+  // schedule state
+  long long n_sub;       // substep index within the macro step
+  long long remaining;   // substeps still to run
+  double t_macro, dt_f;
+  unsigned cur_mask;
+  int lstar, active, reconcile;
+};
+
+constexpr int kMaxBatch = 1024;
+
+struct BatchArgs {
+  BatchInst* inst;
+  int n;
+  int* stage_pre;        // [4][kMaxBatch + 1]: prefix sums of the active octants of each stage
+  int* prol_pre;         // [4][kMaxBatch + 1]: prefix sums of the octants to prolong
+  int* zip_pre;          // [kMaxBatch + 1]: octants of instances that reconcile this round
+  int* hang_pre;         // [kMaxLevel + 2][kMaxBatch + 1]: their hanging-node octants per level
+};
+
+cudaError_t prepare_batch_kernels();  // outside any stream capture
+cudaError_t launch_batch_round(const BatchArgs& a, int pmax, int lmax_all, int grid_stage, int grid_prolong,
+                               int grid_sync, int mixed, cudaStream_t s);
+
 cudaError_t upload_tables(const Tables* rk4, const Tables* rk3, const double W[13][7], const double E[4][4]);
 cudaError_t launch_stage(const StageArgs& a, int count, cudaStream_t s);
 cudaError_t launch_prolong(const ProlongArgs& a, cudaStream_t s);

@@ -51,7 +51,8 @@ class Stats(C.Structure):
 EXPORTS = ["octree_build", "octree_size", "octree_export", "octree_destroy", "lts_plan_create", "lts_plan_destroy",
            "lts_plan_stats", "lts_set_initial", "lts_set_state", "lts_get_state", "lts_get_stage",
            "lts_run_substeps", "lts_advance", "gts_steps", "gts_advance", "lts_export_o2o", "lts_export_pad_map",
-           "lts_export_node_map", "lts_export_pad_map_static", "lts_set_profiling", "lts_kernel_stats", "lts_strerror", "lts_last_error"]
+           "lts_export_node_map", "lts_export_pad_map_static", "lts_set_profiling", "lts_kernel_stats", "lts_batch_create", "lts_batch_destroy", "lts_batch_run",
+           "lts_batch_set_grid", "lts_batch_stats", "lts_strerror", "lts_last_error"]
 
 
 def library_path():
@@ -92,6 +93,11 @@ def load(path=None):
         "lts_set_profiling": ([vp, C.c_int], st),
         "lts_kernel_stats": ([vp, C.POINTER(i64), C.POINTER(C.c_double), C.POINTER(C.c_double),
                               C.POINTER(C.c_double), C.POINTER(i64), C.c_int], st),
+        "lts_batch_create": ([C.POINTER(vp), C.c_int, C.POINTER(vp)], st),
+        "lts_batch_destroy": ([vp], None),
+        "lts_batch_run": ([vp, C.POINTER(i64), C.c_int], st),
+        "lts_batch_set_grid": ([vp, C.c_int, C.c_int, C.c_int], st),
+        "lts_batch_stats": ([vp, C.POINTER(i64), C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], st),
         "lts_strerror": ([st], C.c_char_p),
         "lts_last_error": ([], C.c_char_p),
     }
@@ -301,3 +307,57 @@ class Plan:
         _check(_lib.lts_kernel_stats(self.h, C.byref(n), C.byref(ms), C.byref(fl), C.byref(by), C.byref(ns),
                                      1 if reset else 0), "lts_kernel_stats")
         return dict(launches=n.value, ms=ms.value, flops=fl.value, bytes=by.value, node_stages=ns.value)
+
+
+class Batch:
+    """lts_batch_*: several plans advanced together, one persistent launch per stage."""
+
+    def __init__(self, plans):
+        L = load()
+        self.plans = list(plans)
+        arr = (C.c_void_p * len(self.plans))(*[p.h.value for p in self.plans])
+        h = C.c_void_p()
+        _check(L.lts_batch_create(arr, len(self.plans), C.byref(h)), "lts_batch_create")
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.lts_batch_destroy(self.h)
+            self.h = None
+
+    def run(self, substeps, graph=True):
+        """advance plan i by substeps[i] substeps (asynchronous)"""
+        arr = np.ascontiguousarray(substeps, dtype=np.int64)
+        assert len(arr) == len(self.plans)
+        _check(_lib.lts_batch_run(self.h, arr.ctypes.data_as(C.POINTER(C.c_int64)), 1 if graph else 0),
+               "lts_batch_run")
+
+    def set_grid(self, stage, prolong, sync):
+        _check(_lib.lts_batch_set_grid(self.h, stage, prolong, sync), "lts_batch_set_grid")
+
+    def stats(self):
+        n = C.c_int64()
+        g = [C.c_int(), C.c_int(), C.c_int()]
+        _check(_lib.lts_batch_stats(self.h, C.byref(n), *[C.byref(x) for x in g]), "lts_batch_stats")
+        return dict(launches=n.value, grid_stage=g[0].value, grid_prolong=g[1].value, grid_sync=g[2].value)
+
+    def autotune(self, rounds=4, candidates=None):
+        """Choose the persistent grid sizes by timing `rounds` rounds for each candidate
+        (advances the plans: re-set their state afterwards)."""
+        import time
+        torch = self.plans[0].torch
+        sms = torch.cuda.get_device_properties(self.plans[0].device).multi_processor_count
+        candidates = candidates or [(sms * a, sms * b, sms * 8) for a in (2, 3, 4, 6) for b in (4, 6)]
+        best = None
+        for c in candidates:
+            self.set_grid(*c)
+            self.run([rounds] * len(self.plans), graph=True)    # capture + warm
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            self.run([rounds] * len(self.plans), graph=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            if best is None or dt < best[0]:
+                best = (dt, c)
+        self.set_grid(*best[1])
+        return dict(grid=best[1], seconds=best[0])

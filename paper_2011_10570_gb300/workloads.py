@@ -116,3 +116,27 @@ def uniform(level, pde=PDE_ADVECTION, rk=4):
     w["prob"]["rk"] = rk
     w["name"] = "uniform_l%d_%s" % (level, "adv" if pde == PDE_ADVECTION else "wave")
     return w
+
+
+def batch_instances(seed=3, n=64, lmax_range=(6, 11), f_range=(1.0, 20.0)):
+    """Independent instances for batching: each is advection of a Gaussian or the 1-D
+    wave, on [-1,1]^3 with levels 3..l_max (l_max uniform in lmax_range) refined within
+    f finest-octant edges of a random centre (f log-uniform in f_range, which gives
+    trees of roughly 1k to 50k octants)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n):
+        L = int(rng.integers(lmax_range[0], lmax_range[1] + 1))
+        f = float(np.exp(rng.uniform(np.log(f_range[0]), np.log(f_range[1]))))
+        c = tuple(float(v) for v in rng.uniform(-0.5, 0.5, 3))
+        r = f * 2.0 / 2 ** L
+        if rng.uniform() < 0.5:
+            w = advection_gauss(l_min=3, l_max=L, radius=r, width=0.02)
+            w["spec"]["centers"] = [c]
+            w["prob"]["ic_params"] = [c[0], c[1], c[2], 0.02]
+        else:
+            w = wave_planar(l_min=3, l_max=L, radius=r, s0=c[0], width=0.02)
+            w["spec"]["centers"] = [c]
+        w["name"] = "batch%02d_%s_l3-%d" % (i, "adv" if w["prob"]["pde"] == PDE_ADVECTION else "wave", L)
+        out.append(w)
+    return out

@@ -1,0 +1,84 @@
+"""Batching (many independent solves advanced together, one persistent launch per
+stage, rounds captured in a CUDA graph): every instance ends exactly where it ends
+when run alone, for instances of different PDEs, RK schemes, level ranges and
+substep counts (whole and partial macro steps)."""
+import numpy as np
+import pytest
+
+from paper_2011_10570_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2011_10570_gb300 import build, ltsoct
+    build.build()
+    ltsoct.load()
+    return ltsoct
+
+
+def instances():
+    return [W.advection_gauss(l_min=2, l_max=4), W.advection_gauss(l_min=2, l_max=3, rk=3),
+            W.wave_planar(l_min=2, l_max=4), W.wave_shell(l_min=3, l_max=5, half=4.0, radius=1.5, width=0.2),
+            W.advection_gauss(l_min=1, l_max=6, radius=1e-3)]
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_batch_equals_instances_alone(lt, graph):
+    ws = instances()
+    substeps = [9, 7, 16, 5, 40]
+    alone, batched = [], []
+    for w in ws:
+        a = lt.Plan(lt.Octree(w["spec"]), w["prob"])
+        b = lt.Plan(lt.Octree(w["spec"]), w["prob"])
+        a.set_initial(0.0)
+        b.set_initial(0.0)
+        alone.append(a)
+        batched.append(b)
+    for p, n in zip(alone, substeps):
+        p.run_substeps(n)
+    batch = lt.Batch(batched)
+    batch.run(substeps[:2] + [0, 0, 0], graph=graph)     # a first call, some plans idle
+    batch.run([0, 0] + substeps[2:], graph=graph)
+    for a, b, n in zip(alone, batched, substeps):
+        assert a.stats()["time"] == b.stats()["time"]
+        assert a.stats()["substep"] == b.stats()["substep"]
+        ua, ub = a.get_state(), b.get_state()
+        err = np.abs(ua - ub).max() / np.abs(ua).max()
+        assert err <= 1e-13, err
+    # the plans continue normally after the batch
+    for a, b in zip(alone, batched):
+        a.run_substeps(3)
+        b.run_substeps(3)
+        assert np.abs(a.get_state() - b.get_state()).max() <= 1e-13 * np.abs(a.get_state()).max()
+
+
+def test_batch_matches_oracle(lt, orc):
+    ws = instances()[:3]
+    plans = [lt.Plan(lt.Octree(w["spec"]), w["prob"]) for w in ws]
+    for p in plans:
+        p.set_initial(0.0)
+    batch = lt.Batch(plans)
+    tune = batch.autotune(rounds=2)
+    assert len(tune["grid"]) == 3
+    for p in plans:
+        p.set_initial(0.0)
+    batch.run([8, 8, 8])
+    for w, p in zip(ws, plans):
+        sol = orc.Solver(orc.Tree.build(w["spec"]), w["spec"], w["prob"])
+        sol.set_initial(0.0)
+        sol.lts_substeps(8)
+        ref = sol.state()
+        assert np.abs(p.get_state() - ref).max() / np.abs(ref).max() <= 1e-12
+
+
+def test_batch_rejects_mixed_streams_or_precision(lt):
+    w = W.advection_gauss(l_min=2, l_max=3)
+    a = lt.Plan(lt.Octree(w["spec"]), w["prob"])
+    b = lt.Plan(lt.Octree(w["spec"]), dict(w["prob"], precision=1))
+    with pytest.raises(lt.LtsError):
+        lt.Batch([a, b])
