@@ -191,7 +191,7 @@ def run_batch(args):
     from paper_2011_10570_gb300 import build, ltsoct, workloads
     build.build()
     torch.cuda.set_device(0)
-    ws = workloads.batch_instances(seed=3, n=args.batch)
+    ws = workloads.batch_instances(seed=3, n=args.batch, f_range=(1.0, args.batch_fmax))
     stream = torch.cuda.current_stream()
     plans = [ltsoct.Plan(ltsoct.Octree(w["spec"]), w["prob"], stream=stream) for w in ws]
     sts = [p.stats() for p in plans]
@@ -232,7 +232,8 @@ def run_batch(args):
         "metric": "batched LTS octant-node updates/s", "value": work / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
         "steps": rounds, "warmup": args.warmup, "ms_per_step": ms / rounds, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "batch of %d instances (seed 3)" % len(plans), "octants_min": min(n_oct),
+        "config": {"workload": "batch of %d instances (seed 3, f <= %g)" % (len(plans), args.batch_fmax),
+                   "octants_min": min(n_oct),
                    "octants_median": int(np.median(n_oct)), "octants_max": max(n_oct),
                    "levels": "3..6-11", "step": "one round: one substep of every instance"},
         "gpu_launches": launches, "graph": True, "autotuned_grid": tune["grid"],
@@ -253,6 +254,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--batch", type=int, default=0, help="batched mode: number of instances (64 for the C4 workload)")
     ap.add_argument("--rounds", type=int, default=64, help="batched mode: timed rounds")
+    ap.add_argument("--batch-fmax", type=float, default=20.0,
+                    help="batched mode: refinement radius range in finest-octant edges (20: 1k-50k octants)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="mixed: FP32 stages and right-hand side, FP64 state and time corrections")
     ap.add_argument("--lmax", type=int, default=9,

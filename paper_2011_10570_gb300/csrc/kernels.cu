@@ -871,19 +871,35 @@ __global__ void batch_round_end(BatchArgs B) {
   }
 }
 
+// copies an argument block into shared memory (all threads of the CTA)
+template <typename T>
+__device__ __forceinline__ void copy_args(T* dst, const T* src) {
+  static_assert(sizeof(T) % 8 == 0, "argument blocks are 8-byte multiples");
+  const unsigned long long* s = reinterpret_cast<const unsigned long long*>(src);
+  unsigned long long* d = reinterpret_cast<unsigned long long*>(dst);
+  for (int q = threadIdx.x; q < int(sizeof(T) / 8); q += blockDim.x) d[q] = __ldg(s + q);
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kThreads, 4) batch_stage_kernel(const __grid_constant__ BatchArgs B, int stage) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ StageArgs args;  // the current instance's arguments
   const int* pre = B.stage_pre + stage * (kMaxBatch + 1);
   const int total = pre[B.n];
+  int cur = -1;
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
     const int i = batch_find(pre, B.n + 1, item);
-    const StageArgs& A = B.inst[i].st[stage];
-    const int b = A.first + (item - pre[i]);
-    if (A.nf == 1)
-      stage_octant<1, R>(*reinterpret_cast<StageSmem<1, R>*>(smem_raw), A, b);
+    if (i != cur) {
+      __syncthreads();
+      copy_args(&args, &B.inst[i].st[stage]);
+      __syncthreads();
+      cur = i;
+    }
+    const int b = args.first + (item - pre[i]);
+    if (args.nf == 1)
+      stage_octant<1, R>(*reinterpret_cast<StageSmem<1, R>*>(smem_raw), args, b);
     else
-      stage_octant<2, R>(*reinterpret_cast<StageSmem<2, R>*>(smem_raw), A, b);
+      stage_octant<2, R>(*reinterpret_cast<StageSmem<2, R>*>(smem_raw), args, b);
     __syncthreads();
   }
 }
@@ -891,16 +907,23 @@ __global__ void __launch_bounds__(kThreads, 4) batch_stage_kernel(const __grid_c
 template <typename R>
 __global__ void __launch_bounds__(256) batch_prolong_kernel(const __grid_constant__ BatchArgs B, int stage) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ ProlongArgs args;
   const int* pre = B.prol_pre + stage * (kMaxBatch + 1);
   const int total = pre[B.n];
+  int cur = -1;
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
     const int i = batch_find(pre, B.n + 1, item);
-    const ProlongArgs& A = B.inst[i].pr[stage];
-    const int b = A.list[item - pre[i]];
-    if (A.nf == 1)
-      prolong_octant<1, R>(*reinterpret_cast<ProlongSmem<1, R>*>(smem_raw), A, b);
+    if (i != cur) {
+      __syncthreads();
+      copy_args(&args, &B.inst[i].pr[stage]);
+      __syncthreads();
+      cur = i;
+    }
+    const int b = args.list[item - pre[i]];
+    if (args.nf == 1)
+      prolong_octant<1, R>(*reinterpret_cast<ProlongSmem<1, R>*>(smem_raw), args, b);
     else
-      prolong_octant<2, R>(*reinterpret_cast<ProlongSmem<2, R>*>(smem_raw), A, b);
+      prolong_octant<2, R>(*reinterpret_cast<ProlongSmem<2, R>*>(smem_raw), args, b);
     __syncthreads();
   }
 }
