@@ -243,6 +243,30 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """Serving (NEXT-3): a Poisson stream of wave solves, continuous batching against
+    first-come-first-served one-at-a-time solving, per arrival rate."""
+    import torch
+
+    from paper_2011_10570_gb300 import build, serve, workloads
+    build.build()
+    torch.cuda.set_device(0)
+    out = {"metric": "served LTS solves: p50/p99 latency and throughput", "n_gpus": 1, "dtype": "f64",
+           "data": "synthetic", "rates": []}
+    for rate in args.serve_rates:
+        raw = workloads.serving_requests(seed=4, n=args.serve_n, rate=rate)
+        reqs = [serve.Request(r["rid"], r["arrival"], r["work"], r["t_end"]) for r in raw]
+        server = serve.Server(slots=args.serve_slots, chunk=args.serve_chunk, keep_results=False)
+        res_b, wall_b = server.serve(reqs, realtime=True)
+        res_1, wall_1 = serve.serve_one_at_a_time(reqs, realtime=True, keep_results=False)
+        octs = sorted(r.octants for r in res_b)
+        out["rates"].append({"rate_per_s": rate, "continuous_batching": serve.summary(res_b, wall_b),
+                             "one_at_a_time": serve.summary(res_1, wall_1),
+                             "octants_min_median_max": [octs[0], octs[len(octs) // 2], octs[-1]]})
+        print(json.dumps(out["rates"][-1]), flush=True)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -256,6 +280,11 @@ def main():
     ap.add_argument("--rounds", type=int, default=64, help="batched mode: timed rounds")
     ap.add_argument("--batch-fmax", type=float, default=20.0,
                     help="batched mode: refinement radius range in finest-octant edges (20: 1k-50k octants)")
+    ap.add_argument("--serve", action="store_true", help="serving mode: Poisson stream, continuous batching")
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[0.5, 2.0])
+    ap.add_argument("--serve-n", type=int, default=16)
+    ap.add_argument("--serve-slots", type=int, default=16)
+    ap.add_argument("--serve-chunk", type=int, default=8)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="mixed: FP32 stages and right-hand side, FP64 state and time corrections")
     ap.add_argument("--lmax", type=int, default=9,
@@ -264,6 +293,8 @@ def main():
 
     if args.batch:
         return run_batch(args)
+    if args.serve:
+        return run_serve(args)
     from paper_2011_10570_gb300 import workloads
     w = workloads.wave_shell(l_max=args.lmax)
     if args.precision == "mixed":

@@ -207,9 +207,17 @@ lts_status lts_kernel_stats(lts_plan* plan, int64_t* launches, double* ms, doubl
  * pointers to them (they must outlive it).  Up to 1024 plans. */
 typedef struct lts_batch lts_batch;
 lts_status lts_batch_create(lts_plan* const* plans, int n, lts_batch** out);
+/* An empty batch of n_slots slots on `stream` (cudaStream_t) for plans of one precision
+ * (0 FP64, 1 mixed).  Plans join and leave between runs with attach / detach (continuous
+ * batching); every run launches all 4 stages and all levels, so one captured round
+ * serves any membership.  A detached plan keeps its state and can run alone again. */
+lts_status lts_batch_create_slots(int n_slots, void* stream, int precision, lts_batch** out);
+lts_status lts_batch_attach(lts_batch* batch, int slot, lts_plan* plan);
+lts_status lts_batch_detach(lts_batch* batch, int slot);
 void lts_batch_destroy(lts_batch* batch);
-/* Advance plan i by substeps[i] substeps (host array of n counts), in max(substeps)
- * rounds.  use_graph: replay one captured round.  Asynchronous on the plans' stream. */
+/* Advance the plan in slot i by substeps[i] substeps (host array, one count per slot;
+ * 0 for empty slots), in max(substeps) rounds.  use_graph: replay one captured round.
+ * Asynchronous on the plans' stream. */
 lts_status lts_batch_run(lts_batch* batch, const int64_t* substeps, int use_graph);
 /* Grid sizes of the persistent launches (CTAs); set by an autotuner or by hand. */
 lts_status lts_batch_set_grid(lts_batch* batch, int grid_stage, int grid_prolong, int grid_sync);

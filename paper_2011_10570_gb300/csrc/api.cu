@@ -871,6 +871,7 @@ struct lts_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int64_t launches = 0;
+  bool slots = false;                // created empty with fixed capacity (attach / detach)
 };
 
 namespace {
@@ -914,100 +915,158 @@ void advance_host_schedule(lts_plan* P, int64_t n) {
 
 }  // namespace
 
-extern "C" {
+namespace {
 
-lts_status lts_batch_create(lts_plan* const* plans, int n, lts_batch** out) {
-  if (!plans || !out || n < 1 || n > ltsoct::kMaxBatch) return fail(LTS_EINVAL, "lts_batch_create: 1..1024 plans");
-  *out = nullptr;
-  lts_batch* B = new (std::nothrow) lts_batch();
-  if (!B) return fail(LTS_ENOMEM, "lts_batch_create: out of host memory");
-  B->stream = plans[0]->stream;
-  B->mixed = plans[0]->mixed;
-  for (int i = 0; i < n; ++i) {
-    lts_plan* P = plans[i];
-    if (!P || P->stream != B->stream || P->mixed != B->mixed) {
-      delete B;
-      return fail(LTS_EINVAL, "lts_batch_create: plans must be valid and share one stream and one precision");
-    }
-    B->plans.push_back(P);
-    B->pmax = std::max(B->pmax, P->p);
-    B->lmax_all = std::max(B->lmax_all, P->lmax);
+// the device descriptor of plan P in a batch
+ltsoct::BatchInst batch_descriptor(lts_plan* P) {
+  ltsoct::BatchInst I;
+  std::memset(&I, 0, sizeof(I));
+  for (int s = 0; s < 4; ++s) {
+    const int ss = std::min(s, P->p - 1);
+    I.st[s] = stage_args(P, ss, 0, P->lmin, 0);
+    ltsoct::ProlongArgs& a = I.pr[s];
+    a.tree = I.st[s].tree;
+    a.box = P->d_up_box;
+    a.up_slot = P->d_up_slot;
+    a.up = P->d_up;
+    a.u[0] = P->d_u[0];
+    a.u[1] = P->d_u[1];
+    a.K = P->d_K;
+    a.Uin = I.st[s].Uin;
+    a.fstride = P->N * kNV;
+    a.nf = P->nf;
+    a.stage = ss;
+    a.gts = 0;
+    a.mixed = P->mixed;
+    for (int l = 0; l < 32; ++l) a.lc[l] = I.st[s].lc[l];
+    for (int r = 0; r < 4; ++r) a.om[r] = I.st[s].om[r];
   }
-  std::vector<ltsoct::BatchInst> h(n);
-  for (int i = 0; i < n; ++i) {
-    lts_plan* P = plans[i];
-    ltsoct::BatchInst& I = h[i];
-    std::memset(&I, 0, sizeof(I));
-    for (int s = 0; s < 4; ++s) {
-      const int ss = std::min(s, P->p - 1);
-      I.st[s] = stage_args(P, ss, 0, P->lmin, 0);
-      ltsoct::ProlongArgs& a = I.pr[s];
-      a.tree = I.st[s].tree;
-      a.box = P->d_up_box;
-      a.up_slot = P->d_up_slot;
-      a.up = P->d_up;
-      a.u[0] = P->d_u[0];
-      a.u[1] = P->d_u[1];
-      a.K = P->d_K;
-      a.Uin = I.st[s].Uin;
-      a.fstride = P->N * kNV;
-      a.nf = P->nf;
-      a.stage = ss;
-      a.gts = 0;
-      a.mixed = P->mixed;
-      for (int l = 0; l < 32; ++l) a.lc[l] = I.st[s].lc[l];
-      for (int r = 0; r < 4; ++r) a.om[r] = I.st[s].om[r];
-    }
-    for (ltsoct::SyncArgs* y : {&I.zip, &I.hang}) {
-      y->tree = I.st[0].tree;
-      y->vb[0] = P->d_u[0];
-      y->vb[1] = P->d_u[1];
-      y->elem = 8;
-      y->fstride = P->N * kNV;
-      y->nf = P->nf;
-      y->list = nullptr;
-      y->err = P->d_err;
-    }
-    I.up_list = P->d_up_list;
-    I.hang_list = P->d_hang;
-    for (int l = 0; l < 34; ++l) {
-      I.off[l] = int(P->off[l]);
-      I.up_off[l] = int(P->up_off[l]);
-      I.hang_off[l] = int(P->hang_off[l]);
-    }
-    I.n = int(P->N);
-    I.nf = P->nf;
-    I.p = P->p;
-    I.lmin = P->lmin;
-    I.lmax = P->lmax;
-    I.nsub_macro = int64_t(1) << (P->lmax - P->lmin);
-    I.n_sub = P->n_sub;
-    I.remaining = 0;
-    I.t_macro = P->t_macro;
-    I.dt_f = P->dt_f;
-    I.cur_mask = P->cur_mask;
+  for (ltsoct::SyncArgs* y : {&I.zip, &I.hang}) {
+    y->tree = I.st[0].tree;
+    y->vb[0] = P->d_u[0];
+    y->vb[1] = P->d_u[1];
+    y->elem = 8;
+    y->fstride = P->N * kNV;
+    y->nf = P->nf;
+    y->list = nullptr;
+    y->err = P->d_err;
   }
+  I.up_list = P->d_up_list;
+  I.hang_list = P->d_hang;
+  for (int l = 0; l < 34; ++l) {
+    I.off[l] = int(P->off[l]);
+    I.up_off[l] = int(P->up_off[l]);
+    I.hang_off[l] = int(P->hang_off[l]);
+  }
+  I.n = int(P->N);
+  I.nf = P->nf;
+  I.p = P->p;
+  I.lmin = P->lmin;
+  I.lmax = P->lmax;
+  I.nsub_macro = int64_t(1) << (P->lmax - P->lmin);
+  I.n_sub = P->n_sub;
+  I.t_macro = P->t_macro;
+  I.dt_f = P->dt_f;
+  I.cur_mask = P->cur_mask;
+  return I;
+}
+
+lts_status batch_alloc(lts_batch* B, int n_slots) {
   const size_t pre_ints = size_t(ltsoct::kMaxBatch + 1) * (4 + 4 + 1 + ltsoct::kMaxLevel + 2);
+  std::vector<ltsoct::BatchInst> empty(n_slots);
+  std::memset(empty.data(), 0, sizeof(ltsoct::BatchInst) * n_slots);
   cudaError_t e = ltsoct::prepare_batch_kernels();
-  if (e == cudaSuccess) e = cudaMalloc(&B->d_inst, sizeof(ltsoct::BatchInst) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&B->d_inst, sizeof(ltsoct::BatchInst) * n_slots);
   if (e == cudaSuccess) e = cudaMalloc(&B->d_pre, sizeof(int) * pre_ints);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_out, cudaEventDisableTiming);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(B->d_inst, h.data(), sizeof(ltsoct::BatchInst) * n, cudaMemcpyHostToDevice, B->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(B->d_pre, 0, sizeof(int) * pre_ints, B->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
-  if (e != cudaSuccess) {
-    lts_batch_destroy(B);
-    return cuda_fail(e, "lts_batch_create");
-  }
+    e = cudaMemcpyAsync(B->d_inst, empty.data(), sizeof(ltsoct::BatchInst) * n_slots, cudaMemcpyHostToDevice, B->cap);
+  if (e == cudaSuccess) e = cudaMemsetAsync(B->d_pre, 0, sizeof(int) * pre_ints, B->cap);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(B->cap);
+  if (e != cudaSuccess) return cuda_fail(e, "batch allocation");
+  B->plans.assign(n_slots, nullptr);
   B->args.inst = B->d_inst;
-  B->args.n = n;
+  B->args.n = n_slots;
   B->args.stage_pre = B->d_pre;
   B->args.prol_pre = B->d_pre + 4 * (ltsoct::kMaxBatch + 1);
   B->args.zip_pre = B->d_pre + 8 * (ltsoct::kMaxBatch + 1);
   B->args.hang_pre = B->d_pre + 9 * (ltsoct::kMaxBatch + 1);
+  return LTS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lts_status lts_batch_create_slots(int n_slots, void* stream, int precision, lts_batch** out) {
+  if (!out || n_slots < 1 || n_slots > ltsoct::kMaxBatch || (precision != 0 && precision != 1))
+    return fail(LTS_EINVAL, "lts_batch_create_slots: 1..1024 slots, precision 0 or 1");
+  *out = nullptr;
+  lts_batch* B = new (std::nothrow) lts_batch();
+  if (!B) return fail(LTS_ENOMEM, "lts_batch_create_slots: out of host memory");
+  B->stream = static_cast<cudaStream_t>(stream);
+  B->mixed = precision;
+  B->pmax = 4;                       // every stage and every level is launched, so that
+  B->lmax_all = ltsoct::kMaxLevel;   // one captured round serves any membership
+  B->slots = true;
+  lts_status st = batch_alloc(B, n_slots);
+  if (st != LTS_OK) {
+    lts_batch_destroy(B);
+    return st;
+  }
+  *out = B;
+  return LTS_OK;
+}
+
+lts_status lts_batch_attach(lts_batch* B, int slot, lts_plan* P) {
+  if (!B || !P || slot < 0 || slot >= int(B->plans.size())) return fail(LTS_EINVAL, "lts_batch_attach: bad argument");
+  if (B->plans[slot]) return fail(LTS_ESTATE, "lts_batch_attach: slot is occupied");
+  if (P->stream != B->stream || P->mixed != B->mixed)
+    return fail(LTS_EINVAL, "lts_batch_attach: the plan's stream or precision differs from the batch's");
+  if (!B->slots && (P->p > B->pmax || P->lmax > B->lmax_all))
+    return fail(LTS_EINVAL, "lts_batch_attach: plan needs more stages or levels than the batch launches");
+  ltsoct::BatchInst I = batch_descriptor(P);
+  // ordered after the plan's own work and after earlier rounds
+  CK(cudaEventRecord(B->ev_in, B->stream), "cudaEventRecord");
+  CK(cudaStreamWaitEvent(B->cap, B->ev_in, 0), "cudaStreamWaitEvent");
+  CK(cudaMemcpyAsync(B->d_inst + slot, &I, sizeof(I), cudaMemcpyHostToDevice, B->cap), "copy");
+  CK(cudaStreamSynchronize(B->cap), "cudaStreamSynchronize");
+  B->plans[slot] = P;
+  return LTS_OK;
+}
+
+lts_status lts_batch_detach(lts_batch* B, int slot) {
+  if (!B || slot < 0 || slot >= int(B->plans.size())) return fail(LTS_EINVAL, "lts_batch_detach: bad argument");
+  ltsoct::BatchInst I;
+  std::memset(&I, 0, sizeof(I));
+  CK(cudaMemcpyAsync(B->d_inst + slot, &I, sizeof(I), cudaMemcpyHostToDevice, B->cap), "copy");
+  CK(cudaStreamSynchronize(B->cap), "cudaStreamSynchronize");
+  B->plans[slot] = nullptr;
+  return LTS_OK;
+}
+
+lts_status lts_batch_create(lts_plan* const* plans, int n, lts_batch** out) {
+  if (!plans || !out || n < 1 || n > ltsoct::kMaxBatch) return fail(LTS_EINVAL, "lts_batch_create: 1..1024 plans");
+  *out = nullptr;
+  for (int i = 0; i < n; ++i)
+    if (!plans[i] || plans[i]->stream != plans[0]->stream || plans[i]->mixed != plans[0]->mixed)
+      return fail(LTS_EINVAL, "lts_batch_create: plans must be valid and share one stream and one precision");
+  lts_batch* B = new (std::nothrow) lts_batch();
+  if (!B) return fail(LTS_ENOMEM, "lts_batch_create: out of host memory");
+  B->stream = plans[0]->stream;
+  B->mixed = plans[0]->mixed;
+  for (int i = 0; i < n; ++i) {
+    B->pmax = std::max(B->pmax, plans[i]->p);
+    B->lmax_all = std::max(B->lmax_all, plans[i]->lmax);
+  }
+  lts_status st = batch_alloc(B, n);
+  for (int i = 0; st == LTS_OK && i < n; ++i) st = lts_batch_attach(B, i, plans[i]);
+  if (st != LTS_OK) {
+    lts_batch_destroy(B);
+    return st;
+  }
   *out = B;
   return LTS_OK;
 }
@@ -1047,6 +1106,7 @@ lts_status lts_batch_run(lts_batch* B, const int64_t* substeps, int use_graph) {
   int64_t rounds = 0;
   for (int i = 0; i < n; ++i) {
     if (substeps[i] < 0) return fail(LTS_EINVAL, "lts_batch_run: negative substep count");
+    if (substeps[i] > 0 && !B->plans[i]) return fail(LTS_EINVAL, "lts_batch_run: substeps for an empty slot");
     rounds = std::max(rounds, substeps[i]);
   }
   // the plans' work so far precedes the rounds
@@ -1055,6 +1115,7 @@ lts_status lts_batch_run(lts_batch* B, const int64_t* substeps, int use_graph) {
   for (int i = 0; i < n; ++i) {
     ltsoct::BatchInst* I = B->d_inst + i;
     lts_plan* P = B->plans[i];
+    if (!P) continue;
     // the host schedule of the plan is authoritative at the start of a run
     const long long nsub = P->n_sub, rem = substeps[i];
     const double tm = P->t_macro;
@@ -1071,9 +1132,8 @@ lts_status lts_batch_run(lts_batch* B, const int64_t* substeps, int use_graph) {
   }
   CK(cudaEventRecord(B->ev_out, B->cap), "cudaEventRecord");
   CK(cudaStreamWaitEvent(B->stream, B->ev_out, 0), "cudaStreamWaitEvent");
-  for (int i = 0; i < n; ++i) {
-    advance_host_schedule(B->plans[i], substeps[i]);
-  }
+  for (int i = 0; i < n; ++i)
+    if (B->plans[i]) advance_host_schedule(B->plans[i], substeps[i]);
   return LTS_OK;
 }
 

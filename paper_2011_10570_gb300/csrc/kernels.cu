@@ -886,8 +886,11 @@ __global__ void __launch_bounds__(kThreads, 4) batch_stage_kernel(const __grid_c
   __shared__ StageArgs args;  // the current instance's arguments
   const int* pre = B.stage_pre + stage * (kMaxBatch + 1);
   const int total = pre[B.n];
+  // a contiguous block of work items per CTA: few switches between instances
+  const int per = (total + gridDim.x - 1) / gridDim.x;
+  const int end = min(total, (blockIdx.x + 1) * per);
   int cur = -1;
-  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+  for (int item = blockIdx.x * per; item < end; ++item) {
     const int i = batch_find(pre, B.n + 1, item);
     if (i != cur) {
       __syncthreads();
@@ -910,8 +913,10 @@ __global__ void __launch_bounds__(256) batch_prolong_kernel(const __grid_constan
   __shared__ ProlongArgs args;
   const int* pre = B.prol_pre + stage * (kMaxBatch + 1);
   const int total = pre[B.n];
+  const int per = (total + gridDim.x - 1) / gridDim.x;
+  const int end = min(total, (blockIdx.x + 1) * per);
   int cur = -1;
-  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+  for (int item = blockIdx.x * per; item < end; ++item) {
     const int i = batch_find(pre, B.n + 1, item);
     if (i != cur) {
       __syncthreads();

@@ -52,7 +52,8 @@ EXPORTS = ["octree_build", "octree_size", "octree_export", "octree_destroy", "lt
            "lts_plan_stats", "lts_set_initial", "lts_set_state", "lts_get_state", "lts_get_stage",
            "lts_run_substeps", "lts_advance", "gts_steps", "gts_advance", "lts_export_o2o", "lts_export_pad_map",
            "lts_export_node_map", "lts_export_pad_map_static", "lts_set_profiling", "lts_kernel_stats", "lts_batch_create", "lts_batch_destroy", "lts_batch_run",
-           "lts_batch_set_grid", "lts_batch_stats", "lts_strerror", "lts_last_error"]
+           "lts_batch_set_grid", "lts_batch_stats", "lts_batch_create_slots", "lts_batch_attach",
+           "lts_batch_detach", "lts_strerror", "lts_last_error"]
 
 
 def library_path():
@@ -98,6 +99,9 @@ def load(path=None):
         "lts_batch_run": ([vp, C.POINTER(i64), C.c_int], st),
         "lts_batch_set_grid": ([vp, C.c_int, C.c_int, C.c_int], st),
         "lts_batch_stats": ([vp, C.POINTER(i64), C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], st),
+        "lts_batch_create_slots": ([C.c_int, vp, C.c_int, C.POINTER(vp)], st),
+        "lts_batch_attach": ([vp, C.c_int, vp], st),
+        "lts_batch_detach": ([vp, C.c_int], st),
         "lts_strerror": ([st], C.c_char_p),
         "lts_last_error": ([], C.c_char_p),
     }
@@ -310,15 +314,37 @@ class Plan:
 
 
 class Batch:
-    """lts_batch_*: several plans advanced together, one persistent launch per stage."""
+    """lts_batch_*: several plans advanced together, one persistent launch per stage.
+    Batch(plans) binds a fixed list; Batch.slots(n, stream, precision) creates an empty
+    batch whose slots are filled and emptied with attach / detach."""
 
-    def __init__(self, plans):
+    def __init__(self, plans=None, _handle=None, _n=0):
         L = load()
+        if _handle is not None:
+            self.h = _handle
+            self.plans = [None] * _n
+            return
         self.plans = list(plans)
         arr = (C.c_void_p * len(self.plans))(*[p.h.value for p in self.plans])
         h = C.c_void_p()
         _check(L.lts_batch_create(arr, len(self.plans), C.byref(h)), "lts_batch_create")
         self.h = h
+
+    @classmethod
+    def slots(cls, n, stream, precision=0):
+        L = load()
+        h = C.c_void_p()
+        _check(L.lts_batch_create_slots(n, C.c_void_p(stream.cuda_stream), precision, C.byref(h)),
+               "lts_batch_create_slots")
+        return cls(_handle=h, _n=n)
+
+    def attach(self, slot, plan):
+        _check(_lib.lts_batch_attach(self.h, slot, plan.h), "lts_batch_attach")
+        self.plans[slot] = plan
+
+    def detach(self, slot):
+        _check(_lib.lts_batch_detach(self.h, slot), "lts_batch_detach")
+        self.plans[slot] = None
 
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:
@@ -345,16 +371,18 @@ class Batch:
         """Choose the persistent grid sizes by timing `rounds` rounds for each candidate
         (advances the plans: re-set their state afterwards)."""
         import time
-        torch = self.plans[0].torch
-        sms = torch.cuda.get_device_properties(self.plans[0].device).multi_processor_count
+        live = [p for p in self.plans if p is not None]
+        torch = live[0].torch
+        sms = torch.cuda.get_device_properties(live[0].device).multi_processor_count
         candidates = candidates or [(sms * a, sms * b, sms * 8) for a in (2, 3, 4, 6) for b in (4, 6)]
         best = None
         for c in candidates:
             self.set_grid(*c)
-            self.run([rounds] * len(self.plans), graph=True)    # capture + warm
+            steps = [rounds if p is not None else 0 for p in self.plans]
+            self.run(steps, graph=True)    # capture + warm
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            self.run([rounds] * len(self.plans), graph=True)
+            self.run(steps, graph=True)
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
             if best is None or dt < best[0]:

@@ -1,0 +1,176 @@
+"""Continuous batching of LTS solves on one GPU.
+
+Requests (an octree refinement spec, a problem and an end time) arrive over time.
+The server keeps every admitted solve resident on the device (octree tables, RK
+state) in a slot of a batch (``lts_batch_create_slots``), and advances all of them
+together in rounds: each round performs one LTS substep (Alg. 2, Fig. blk_loop)
+of every resident solve, with one persistent launch per RK stage covering the
+active levels of all of them.  Between rounds of a chunk the server
+  * retires solves that reached their end time (result copied to the host,
+    device memory returned, slot freed), and
+  * admits waiting requests while a slot is free and the device-memory budget
+    holds their estimated footprint.
+Latency is arrival to result; throughput is node-updates per second of wall time.
+
+``serve_one_at_a_time`` solves the same stream first-come-first-served, one
+request at a time, for comparison.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import ltsoct
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float          # seconds after the start of the stream
+    work: dict              # {"spec": ..., "prob": ...}
+    t_end: float
+
+
+@dataclass
+class Result:
+    rid: int
+    arrival: float
+    admitted: float
+    finished: float
+    octants: int
+    substeps: int
+    node_updates: float
+    state: np.ndarray = field(repr=False, default=None)
+
+    @property
+    def latency(self):
+        return self.finished - self.arrival
+
+
+def state_bytes(n_octants, nf, precision, p=4):
+    """Device bytes of a plan: state (2 copies, FP64), RK stages and 2 stage-input
+    buffers in the stage type, prolonged inputs (at most one slot per octant) and tables."""
+    es = 4 if precision == 1 else 8
+    per_octant = 343 * nf * (2 * 8 + (p + 2) * es) + 2197 * nf * es + 27 * 4 + 64
+    return int(n_octants * per_octant)
+
+
+def substeps_to(plan, t_end):
+    """whole macro steps from the plan's current time up to (about) t_end"""
+    st = plan.stats()
+    n_macro = max(1, int(round((t_end - st["time"]) / st["dt_coarsest"])))
+    return n_macro * (1 << (st["l_max"] - st["l_min"]))
+
+
+def node_updates(st, n_sub0, n):
+    lmin, lmax = st["l_min"], st["l_max"]
+    counts = st["octants_per_level"]
+    total, k = 0, n_sub0
+    for _ in range(n):
+        lstar = next(l for l in range(lmin, lmax + 1) if k % (1 << (lmax - l)) == 0)
+        total += 343 * sum(counts[lstar:lmax + 1])
+        k = (k + 1) % (1 << (lmax - lmin))
+    return float(total)
+
+
+class Server:
+    def __init__(self, slots=16, hbm_budget=64 << 30, chunk=8, precision=0, keep_results=True):
+        import torch
+        self.torch = torch
+        self.stream = torch.cuda.current_stream()
+        self.batch = ltsoct.Batch.slots(slots, self.stream, precision)
+        self.nslots = slots
+        self.budget = hbm_budget
+        self.chunk = chunk
+        self.precision = precision
+        self.keep = keep_results
+
+    def serve(self, requests, realtime=True):
+        """Serve `requests` (sorted by arrival).  With realtime, arrivals are honoured
+        against the wall clock; otherwise every request is available at once."""
+        torch = self.torch
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        active = {}                      # slot -> [req, plan, remaining, admitted, est, updates]
+        used = 0
+        results = []
+        t0 = time.perf_counter()
+        now = lambda: time.perf_counter() - t0
+        while pending or active:
+            # admit while a slot is free and the budget holds
+            while pending and (not realtime or pending[0].arrival <= now()) and len(active) < self.nslots:
+                req = pending[0]
+                tree = ltsoct.Octree(req.work["spec"])
+                nf = 2 if req.work["prob"]["pde"] == 1 else 1
+                est = state_bytes(len(tree), nf, self.precision)
+                if used + est > self.budget and active:
+                    break                # wait for memory to be freed
+                pending.popleft()
+                prob = dict(req.work["prob"], precision=self.precision)
+                plan = ltsoct.Plan(tree, prob, stream=self.stream)
+                plan.set_initial(0.0)
+                n = substeps_to(plan, req.t_end)
+                slot = next(s for s in range(self.nslots) if s not in active)
+                self.batch.attach(slot, plan)
+                active[slot] = [req, plan, n, now(), est, node_updates(plan.stats(), 0, n)]
+                used += est
+            if not active:
+                if pending:
+                    time.sleep(max(0.0, min(0.01, pending[0].arrival - now())))
+                continue
+            steps = [0] * self.nslots
+            k = min(self.chunk, min(a[2] for a in active.values()))
+            for s, a in active.items():
+                steps[s] = min(k, a[2])
+            self.batch.run(steps, graph=True)
+            torch.cuda.current_stream().synchronize()
+            for s in list(active):
+                a = active[s]
+                a[2] -= steps[s]
+                if a[2] == 0:
+                    req, plan = a[0], a[1]
+                    state = plan.get_state() if self.keep else None
+                    t = now()
+                    st = plan.stats()
+                    results.append(Result(req.rid, req.arrival, a[3], t, st["n_octants"],
+                                          int(round(st["time"] / st["dt_finest"])), a[5], state))
+                    self.batch.detach(s)
+                    used -= a[4]
+                    del active[s]
+                    del plan
+        return sorted(results, key=lambda r: r.rid), now()
+
+
+def serve_one_at_a_time(requests, precision=0, realtime=True, keep_results=True):
+    """First come, first served, one solve on the GPU at a time (no batching)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    results = []
+    t0 = time.perf_counter()
+    now = lambda: time.perf_counter() - t0
+    for req in sorted(requests, key=lambda r: r.arrival):
+        if realtime and req.arrival > now():
+            time.sleep(req.arrival - now())
+        admitted = now()
+        plan = ltsoct.Plan(ltsoct.Octree(req.work["spec"]), dict(req.work["prob"], precision=precision),
+                           stream=stream)
+        plan.set_initial(0.0)
+        n = substeps_to(plan, req.t_end)
+        plan.run_substeps(n)
+        state = plan.get_state() if keep_results else None
+        st = plan.stats()
+        results.append(Result(req.rid, req.arrival, admitted, now(), st["n_octants"], n,
+                              node_updates(st, 0, n), state))
+        del plan
+    return results, now()
+
+
+def summary(results, wall):
+    lat = np.array([r.latency for r in results])
+    work = sum(r.node_updates for r in results)
+    return {"requests": len(results), "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)), "mean_latency_s": float(lat.mean()),
+            "throughput_node_updates_per_s": work / wall, "requests_per_s": len(results) / wall,
+            "wall_s": wall}

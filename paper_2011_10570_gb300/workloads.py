@@ -140,3 +140,22 @@ def batch_instances(seed=3, n=64, lmax_range=(6, 11), f_range=(1.0, 20.0)):
         w["name"] = "batch%02d_%s_l3-%d" % (i, "adv" if w["prob"]["pde"] == PDE_ADVECTION else "wave", L)
         out.append(w)
     return out
+
+
+def serving_requests(seed=4, n=24, rate=1.0, lmax_choices=(5, 6)):
+    """A Poisson stream of wave-equation solves: arrivals with exponential gaps of mean
+    1/rate seconds; each a shell of radius R in [2,6] on [-10,10]^3, refined on levels
+    3..l_max around a band in [0,5] (about 1k to 200k octants), end time in [0.5, 5]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += float(rng.exponential(1.0 / rate))
+        L = int(rng.choice(lmax_choices))
+        R = float(rng.uniform(2.0, 6.0))
+        band = float(rng.uniform(0.0, 5.0))
+        t_end = float(rng.uniform(0.5, 5.0))
+        w = wave_shell(l_min=3, l_max=L, radius=R, band=band, seed=seed * 1000 + i)
+        out.append(dict(rid=i, arrival=t, work=dict(spec=w["spec"], prob=w["prob"]), t_end=t_end,
+                        name="req%02d_l3-%d" % (i, L)))
+    return out
