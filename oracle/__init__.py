@@ -56,7 +56,8 @@ class Refine(C.Structure):
 class Problem(C.Structure):
     _fields_ = [("pde", C.c_int), ("adv", C.c_double * 3), ("cfl", C.c_double),
                 ("ko_sigma", C.c_double), ("rk", C.c_int), ("bc", C.c_int), ("ic", C.c_int),
-                ("ic_params", C.c_double * 160)]
+                ("ic_params", C.c_double * 160), ("nl_c", C.c_double), ("orbit", C.c_int),
+                ("orbit_params", C.c_double * 4)]
 
 
 def lib():
@@ -160,6 +161,10 @@ def make_problem(prob: dict) -> Problem:
     params = list(prob.get("ic_params", []))
     for i, v in enumerate(params):
         p.ic_params[i] = v
+    p.nl_c = prob.get("nl_c", 0.0)
+    p.orbit = int(prob.get("orbit", 0))
+    for i, v in enumerate(prob.get("orbit_params", [])):
+        p.orbit_params[i] = v
     return p
 
 

@@ -87,9 +87,41 @@ static int64_t radius_sq_ceil(double r, double lo, double hi) {
   return (int64_t)ceil(rl * rl);
 }
 
+/* kind 2: distance from the box to the circle of radius R around c in the plane
+ * z = c_z: with rho the distance from the axis, d^2 = drho^2 + dz^2 where drho is the
+ * distance from R to the box's range of rho and dz the box's distance to the plane */
+static int circle_pred(const orc_refine* s, const int64_t a[3], int64_t e) {
+  int64_t cc[3];
+  for (int d = 0; d < 3; ++d) cc[d] = to_lattice(s->centers[0][d], s->lo, s->hi);
+  int64_t rmin2 = 0, rmax2 = 0;
+  for (int d = 0; d < 2; ++d) {
+    int64_t lo = a[d], hi = a[d] + e, dn = 0;
+    if (cc[d] < lo) dn = lo - cc[d];
+    if (cc[d] > hi) dn = cc[d] - hi;
+    rmin2 += dn * dn;
+    int64_t f1 = cc[d] - lo, f2 = hi - cc[d];
+    if (f1 < 0) f1 = -f1;
+    if (f2 < 0) f2 = -f2;
+    int64_t df = f1 > f2 ? f1 : f2;
+    rmax2 += df * df;
+  }
+  int64_t dz = 0;
+  if (cc[2] < a[2]) dz = a[2] - cc[2];
+  if (cc[2] > a[2] + e) dz = cc[2] - a[2] - e;
+  double R = s->radius / (s->hi - s->lo) * (double)ROOT_EDGE;
+  double b = s->band / (s->hi - s->lo) * (double)ROOT_EDGE;
+  double rmin = sqrt((double)rmin2), rmax = sqrt((double)rmax2);
+  double dr = 0.0;
+  if (rmin - R > dr) dr = rmin - R;
+  if (R - rmax > dr) dr = R - rmax;
+  double dzd = (double)dz;
+  return dr * dr + dzd * dzd <= b * b;
+}
+
 int orc_refine_pred(const orc_refine* s, int32_t x, int32_t y, int32_t z, int level) {
   int64_t e = edge_of(level);
   int64_t a[3] = {x, y, z};
+  if (s->kind == 2) return circle_pred(s, a, e);
   int ncent = s->kind == 1 ? 1 : s->n_centers;
   for (int c = 0; c < ncent; ++c) {
     int64_t cc[3];
@@ -1188,6 +1220,27 @@ static void compute_stage(orc_solver* s, int64_t b, int st, int gts, int lstar, 
           double phi = Tp[tix(ii, jj, kk)];
           kout[n] = phi + kos * koc;
           kout[NV + n] = lap + kos * kop;
+          if (s->pr.nl_c != 0.0 || s->pr.orbit) {
+            /* eq. phi: -c sin(2 chi)/r^2 (taken as 0 at r = 0); reading R14: orbiting
+             * Gaussian sources at the stage time t_b + c_s dt_b */
+            int64_t P[3] = {6 * (int64_t)o->x + ii * e, 6 * (int64_t)o->y + jj * e, 6 * (int64_t)o->z + kk * e};
+            double x[3];
+            pos6_to_x(s, P, x);
+            double src = 0.0;
+            if (s->pr.nl_c != 0.0) {
+              double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+              if (r2 > 0.0) src -= s->pr.nl_c * sin(2.0 * Tc[tix(ii, jj, kk)]) / r2;
+            }
+            if (s->pr.orbit) {
+              const double* op = s->pr.orbit_params;
+              double ts = tb + s->c[st] * dtb;
+              double c1 = op[0] * cos(op[1] * ts), s1 = op[0] * sin(op[1] * ts);
+              double d1 = (x[0] - c1) * (x[0] - c1) + (x[1] - s1) * (x[1] - s1) + x[2] * x[2];
+              double d2 = (x[0] + c1) * (x[0] + c1) + (x[1] + s1) * (x[1] + s1) + x[2] * x[2];
+              src += op[3] * (exp(-d1 / op[2]) + exp(-d2 / op[2]));
+            }
+            kout[NV + n] += src;
+          }
           if (s->pr.bc == ORC_BC_RADIATIVE) {
             int64_t P[3] = {6 * (int64_t)o->x + ii * e, 6 * (int64_t)o->y + jj * e, 6 * (int64_t)o->z + kk * e};
             int on_bnd = 0;

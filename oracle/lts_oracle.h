@@ -30,7 +30,8 @@ extern "C" {
 typedef struct {
   double lo, hi;          /* cube domain [lo,hi]^3 */
   int l_min, l_max;       /* refinement levels */
-  int kind;               /* 0: balls of `radius` around centers; 1: shell |x-c0| in [radius-band, radius+band] */
+  int kind;               /* 0: balls of `radius` around centers; 1: shell |x-c0| in [radius-band, radius+band];
+                             2: within `band` of the circle of `radius` around c0 in the plane z = c0.z */
   int n_centers;
   double centers[8][3];
   double radius, band;
@@ -43,7 +44,8 @@ enum {
   ORC_IC_ADV_POLY = 1,    /* p[0..63] c[i + 4 j + 16 k] : u = sum c x^i y^j z^k at x - a t */
   ORC_IC_WAVE_SHELL = 2,  /* p[0] R, p[1] w, p[2] amp, p[3] nmodes, p[4] kscale, p[5+5m..] eps, kx, ky, kz, theta */
   ORC_IC_WAVE_PLANAR = 3, /* p[0] s0, p[1] w : chi = (f(x-t) + f(x+t))/2, f = exp(-(s-s0)^2/w) */
-  ORC_IC_WAVE_POLY = 4    /* p[0..63] cubic P, p[64..127] cubic Q : chi = P + tQ + t^2/2 lap P + t^3/6 lap Q */
+  ORC_IC_WAVE_POLY = 4,   /* p[0..63] cubic P, p[64..127] cubic Q : chi = P + tQ + t^2/2 lap P + t^3/6 lap Q */
+  ORC_IC_WAVE_REST = 5    /* chi = phi = 0 */
 };
 
 typedef struct {
@@ -55,6 +57,11 @@ typedef struct {
   int bc;
   int ic;
   double ic_params[160];
+  double nl_c;             /* wave: phi_t += -nl_c sin(2 chi) / r^2 (eq. phi), 0 at r = 0 */
+  int orbit;               /* wave: 1 adds two Gaussian sources on a circular orbit (reading R14) */
+  double orbit_params[4];  /* orbit radius, angular speed, width w, amplitude A:
+                              phi_t += A sum_{i=1,2} exp(-|x - x_i(t)|^2 / w),
+                              x_1 = radius (cos wt, sin wt, 0), x_2 = -x_1 */
 } orc_problem;
 
 typedef struct orc_tree orc_tree;

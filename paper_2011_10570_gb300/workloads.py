@@ -21,8 +21,8 @@ import numpy as np
 
 PDE_ADVECTION, PDE_WAVE = 0, 1
 BC_EXACT, BC_RADIATIVE = 0, 1
-IC_ADV_GAUSS, IC_ADV_POLY, IC_WAVE_SHELL, IC_WAVE_PLANAR, IC_WAVE_POLY = 0, 1, 2, 3, 4
-REFINE_BALLS, REFINE_SHELL = 0, 1
+IC_ADV_GAUSS, IC_ADV_POLY, IC_WAVE_SHELL, IC_WAVE_PLANAR, IC_WAVE_POLY, IC_WAVE_REST = 0, 1, 2, 3, 4, 5
+REFINE_BALLS, REFINE_SHELL, REFINE_CIRCLE = 0, 1, 2
 
 
 def advection_gauss(l_min=3, l_max=5, radius=0.3, t_end=0.25, cfl=0.25, ko_sigma=0.1, rk=4, width=0.05):
@@ -62,6 +62,29 @@ def wave_shell(l_min=4, l_max=9, band=0.0, seed=1, amp=1e-3, radius=2.0, width=0
     prob = dict(pde=PDE_WAVE, adv=(0.0, 0.0, 0.0), cfl=cfl, ko_sigma=ko_sigma, rk=rk, bc=bc,
                 ic=IC_WAVE_SHELL, ic_params=params)
     return dict(name="wave_shell_l%d-%d" % (l_min, l_max), spec=spec, prob=prob, t_end=t_end)
+
+
+def wave_nonlinear(l_min=4, l_max=9, c=1.0, **kw):
+    """The shell data of ``wave_shell`` evolved with the non-linear source -c sin(2 chi)/r^2
+    of eq. phi (the paper's non-linear runs use c = 1)."""
+    w = wave_shell(l_min=l_min, l_max=l_max, **kw)
+    w["prob"]["nl_c"] = c
+    w["name"] = "wave_nonlinear_l%d-%d" % (l_min, l_max)
+    return w
+
+
+def wave_orbit(l_min=3, l_max=12, band=0.042, half=10.0, radius=1.0, omega=0.5, width=0.05, amp=1.0,
+               t_end=1.0, cfl=0.25, ko_sigma=0.1, rk=4, precision=1):
+    """Wave equation at rest driven by two Gaussian sources on a circular orbit:
+    phi_t += amp sum_i exp(-|x - x_i(t)|^2 / width), x_1 = radius (cos omega t, sin omega t, 0),
+    x_2 = -x_1, on [-half,half]^3 with levels l_min..l_max refined within `band` of the orbit
+    circle, radiative outer boundary, mixed precision by default."""
+    spec = dict(lo=-half, hi=half, l_min=l_min, l_max=l_max, kind=REFINE_CIRCLE, centers=[(0.0, 0.0, 0.0)],
+                radius=radius, band=band)
+    prob = dict(pde=PDE_WAVE, adv=(0.0, 0.0, 0.0), cfl=cfl, ko_sigma=ko_sigma, rk=rk, bc=BC_RADIATIVE,
+                ic=IC_WAVE_REST, ic_params=[], orbit=1, orbit_params=[radius, omega, width, amp],
+                precision=precision)
+    return dict(name="wave_orbit_l%d-%d" % (l_min, l_max), spec=spec, prob=prob, t_end=t_end)
 
 
 def random_cubic(seed, scale=1.0):
