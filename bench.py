@@ -31,7 +31,7 @@ UNIT = "node-updates/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x flops/FMA x max clock
 # DRAM bytes (read + write) per node-stage of stage_kernel<2>, from the ncu capture of
 # profiles/stage_kernel_wave_l4-8.md; set to None whenever the kernel changes after it
-STAGE_DRAM_BYTES_PER_NODE_STAGE = 85.0
+STAGE_DRAM_BYTES_PER_NODE_STAGE = None
 
 
 def measured_peaks():
@@ -256,13 +256,18 @@ def run_serve(args):
     for rate in args.serve_rates:
         raw = workloads.serving_requests(seed=4, n=args.serve_n, rate=rate)
         reqs = [serve.Request(r["rid"], r["arrival"], r["work"], r["t_end"]) for r in raw]
-        server = serve.Server(slots=args.serve_slots, chunk=args.serve_chunk, keep_results=False)
-        res_b, wall_b = server.serve(reqs, realtime=True)
+        row = {"rate_per_s": rate}
+        for sat in args.serve_saturation:
+            server = serve.Server(slots=args.serve_slots, chunk=args.serve_chunk, keep_results=False,
+                                  saturation=sat)
+            res_b, wall_b = server.serve(reqs, realtime=True)
+            row["continuous_batching_sat%g" % sat] = serve.summary(res_b, wall_b)
+            del server
         res_1, wall_1 = serve.serve_one_at_a_time(reqs, realtime=True, keep_results=False)
-        octs = sorted(r.octants for r in res_b)
-        out["rates"].append({"rate_per_s": rate, "continuous_batching": serve.summary(res_b, wall_b),
-                             "one_at_a_time": serve.summary(res_1, wall_1),
-                             "octants_min_median_max": [octs[0], octs[len(octs) // 2], octs[-1]]})
+        octs = sorted(r.octants for r in res_1)
+        row["one_at_a_time"] = serve.summary(res_1, wall_1)
+        row["octants_min_median_max"] = [octs[0], octs[len(octs) // 2], octs[-1]]
+        out["rates"].append(row)
         print(json.dumps(out["rates"][-1]), flush=True)
     print(json.dumps(out), flush=True)
 
@@ -283,9 +288,16 @@ def main():
     ap.add_argument("--serve", action="store_true", help="serving mode: Poisson stream, continuous batching")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[0.5, 2.0])
     ap.add_argument("--serve-n", type=int, default=16)
+    ap.add_argument("--serve-saturation", type=float, nargs="+", default=[8192.0],
+                    help="admission limit on the resident solves' mean active octants per substep")
     ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--serve-chunk", type=int, default=8)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+    ap.add_argument("--workload", default="shell", choices=["shell", "nonlinear", "orbit"],
+                    help="shell: linear wave, levels 4..9 (the benchmark configuration); nonlinear: the same "
+                         "with the -sin(2 chi)/r^2 source; orbit: two orbiting sources, levels 3..12")
+    ap.add_argument("--substeps", type=int, default=0,
+                    help="substeps per step (default: a macro step; 64 for the orbit workload)")
+    ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
                     help="mixed: FP32 stages and right-hand side, FP64 state and time corrections")
     ap.add_argument("--lmax", type=int, default=9,
                     help="finest level of the wave workload (9: the benchmark configuration; 8: the profiling case)")
@@ -296,9 +308,15 @@ def main():
     if args.serve:
         return run_serve(args)
     from paper_2011_10570_gb300 import workloads
-    w = workloads.wave_shell(l_max=args.lmax)
-    if args.precision == "mixed":
-        w["prob"]["precision"] = 1
+    if args.workload == "orbit":
+        w = workloads.wave_orbit()
+    elif args.workload == "nonlinear":
+        w = workloads.wave_nonlinear(l_max=args.lmax)
+    else:
+        w = workloads.wave_shell(l_max=args.lmax)
+    if args.precision is None:
+        args.precision = "mixed" if args.workload == "orbit" else "fp64"
+    w["prob"]["precision"] = 1 if args.precision == "mixed" else 0
     world, rank, local, pg = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, w, world, rank, pg)
@@ -319,12 +337,15 @@ def main():
     st = plan.stats()
     n = st["n_octants"]
     L = st["l_max"] - st["l_min"]
-    nsub = 2 ** L
-    work_nodes = st["lts_work_per_macro"] * 343          # node-updates per macro step
+    # a step: one macro step (2^L substeps), or a window of k substeps of it when a
+    # macro step is too long to time several of (the orbit workload: 512 substeps)
+    nsub = args.substeps if args.substeps else (64 if args.workload == "orbit" else 2 ** L)
     plan.set_initial(0.0)
     for _ in range(args.warmup):
         plan.run_substeps(nsub)
     torch.cuda.synchronize()
+    n_sub0 = plan.stats()["substep"]
+    work_timed = schedule_work(st, n_sub0, args.steps * nsub)   # node-updates of the timed substeps
 
     # device-resident timed region (CUDA events on the plan's stream)
     plan.set_profiling(True)
@@ -348,7 +369,7 @@ def main():
         t = torch.tensor([ms], dtype=torch.float64)
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         ms = float(t.item())
-    value = world * args.steps * work_nodes / (ms / 1e3)
+    value = world * work_timed / (ms / 1e3)
 
     # end to end through the C ABI with host buffers: H2D of the state, one macro
     # step, D2H of the result, every step
@@ -371,7 +392,8 @@ def main():
         t = torch.tensor([e2e_s], dtype=torch.float64)
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e_value = world * e2e_steps * work_nodes / e2e_s if e2e_steps else None
+    # every e2e step restarts from a synchronised state: the first window of a macro step
+    e2e_value = world * e2e_steps * schedule_work(st, 0, nsub) / e2e_s if e2e_steps else None
     state_bytes = host.nbytes
 
     # GTS over the same physical time (2^L global steps per macro step)
@@ -386,8 +408,13 @@ def main():
         g1.record(stream)
         torch.cuda.synchronize()
         gms = g0.elapsed_time(g1)
-        gts = {"ms_per_macro_step": gms, "lts_ms_per_macro_step": ms / args.steps,
+        # LTS: the timed steps; GTS: nsub global steps of dt_f (the same physical time
+        # per step when a step is a macro step)
+        gts = {"ms_per_step": gms, "lts_ms_per_step": ms / args.steps, "steps_of_dt_finest": nsub,
                "lts_speedup_measured": gms / (ms / args.steps), "lts_speedup_model": st["model_speedup"]}
+        if nsub != 2 ** L:
+            gts["note"] = ("a step is %d of the %d substeps of a macro step: the LTS window also holds the "
+                           "coarse levels' steps of substep 0 when it starts a macro step" % (nsub, 2 ** L))
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -395,8 +422,9 @@ def main():
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32 stages / f64 state",
         "data": "synthetic",
         "config": {"workload": w["name"], "octants": n, "levels": "%d..%d" % (st["l_min"], st["l_max"]),
-                   "fields": st["nf"], "rk": 4, "substeps_per_step": nsub, "parallelism": "replicas",
-                   "l2": "inputs larger than L2 (state arrays 847 MB each, 6 resident)"},
+                   "fields": st["nf"], "rk": 4, "substeps_per_step": nsub, "substeps_per_macro_step": 2 ** L,
+                   "parallelism": "replicas",
+                   "l2": "inputs larger than L2 (state arrays %d MB each)" % (st["nf"] * n * 343 * 8 // 2 ** 20)},
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                 "d2h_bytes_per_step": state_bytes},

@@ -55,7 +55,10 @@ typedef struct lts_plan lts_plan;
  * library uses an integer geometric predicate so that trees are reproducible
  * bit for bit: an octant of level l < l_max is split if
  *   kind 0: its closed box comes within `radius` of any of the n_centers points;
- *   kind 1: its closed box meets the shell radius-band <= |x - centers[0]| <= radius+band.
+ *   kind 1: its closed box meets the shell radius-band <= |x - centers[0]| <= radius+band;
+ *   kind 2: its closed box comes within `band` of the circle of `radius` around
+ *           centers[0] in the plane z = centers[0].z (distance evaluated in IEEE
+ *           doubles from the box's exact lattice extents, no contraction).
  * Octants of level < l_min are always split.  Centers and radii are mapped to
  * lattice units as llround((c - lo)/(hi - lo) * 2^20) and floor/ceil of
  * (r/(hi - lo) * 2^20)^2; the tests are exact int64 comparisons. */
@@ -74,11 +77,12 @@ enum {
   LTS_IC_ADV_GAUSS = 0,   /* ic_params[0..2] x0, [3] w: u = exp(-|x - x0 - a t|^2 / w) */
   LTS_IC_WAVE_SHELL = 2,  /* [0] R, [1] w, [2] amp, [3] nmodes (<= 4), [4] kscale, [5+5m..] eps, kx, ky, kz, theta:
                              chi = exp(-(r-R)^2/w) (1 + amp sum eps sin(kscale k.x + theta)), phi = 0 */
-  LTS_IC_WAVE_PLANAR = 3  /* [0] s0, [1] w: chi = (f(x-t) + f(x+t))/2, f(s) = exp(-(s-s0)^2/w), phi = chi_t */
+  LTS_IC_WAVE_PLANAR = 3, /* [0] s0, [1] w: chi = (f(x-t) + f(x+t))/2, f(s) = exp(-(s-s0)^2/w), phi = chi_t */
+  LTS_IC_WAVE_REST = 5    /* chi = phi = 0 (a field at rest, driven by source terms) */
 };
 
 /* The problem (Sec. 4.2).  pde 0: u_t + adv . grad u = 0.  pde 1: chi_t = phi,
- * phi_t = lap chi (eqs. chi, phi with c = 0).  Both add Kreiss-Oliger dissipation
+ * phi_t = lap chi + sources (eqs. chi, phi; sources below).  Both add Kreiss-Oliger dissipation
  * (ko_sigma / (64 h)) sum_d delta_d^6.  bc 0 (exact): exterior ghosts are the
  * RK stage values of the closed-form solution named by `ic`; bc 1 (radiative,
  * wave only): exterior ghosts by cubic extrapolation and, at nodes on the domain
@@ -99,6 +103,16 @@ typedef struct {
   void* (*dev_alloc)(size_t bytes, void* ctx);  /* optional device allocator */
   void (*dev_free)(void* ptr, void* ctx);
   void* alloc_ctx;
+  /* source terms of the wave equation (pde 1 only; zero-initialised = none), added to
+   * phi_t at every node except boundary nodes under bc 1:
+   *   nl_c:  -nl_c sin(2 chi) / r^2 (eq. phi; the paper's non-linear runs use c = 1),
+   *          taken as 0 at r = 0;
+   *   orbit: 1 adds A sum_{i=1,2} exp(-|x - x_i(t)|^2 / w) with x_1 = R (cos W t, sin W t, 0),
+   *          x_2 = -x_1, orbit_params = {R, W, w > 0, A}, evaluated at the stage time
+   *          t_b + c_s dt of each RK stage.  Not in the paper: a driven workload. */
+  double nl_c;
+  int orbit;
+  double orbit_params[4];
 } lts_problem;
 
 typedef struct {

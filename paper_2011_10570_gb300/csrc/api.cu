@@ -214,6 +214,10 @@ ltsoct::StageArgs stage_args(const lts_plan* P, int stage, int first, int lstar,
   a.err = P->d_err;
   a.up = P->d_up;
   a.up_slot = P->d_up_slot;
+  a.nl_c = P->prob.nl_c;
+  a.orbit = P->prob.orbit;
+  for (int i = 0; i < 4; ++i) a.orb[i] = P->prob.orbit_params[i];
+  a.c_s = P->tab.c[stage];
   return a;
 }
 
@@ -350,14 +354,19 @@ bool supported(const lts_problem& p, std::string* why) {
       return *why = "exact boundary data for the wave equation needs ic = LTS_IC_WAVE_PLANAR", false;
   } else if (p.bc == LTS_BC_RADIATIVE) {
     if (p.pde != LTS_PDE_WAVE) return *why = "radiative boundary is for the wave equation", false;
-    if (p.ic != LTS_IC_WAVE_SHELL && p.ic != LTS_IC_WAVE_PLANAR)
-      return *why = "wave initial data must be LTS_IC_WAVE_SHELL or LTS_IC_WAVE_PLANAR", false;
+    if (p.ic != LTS_IC_WAVE_SHELL && p.ic != LTS_IC_WAVE_PLANAR && p.ic != LTS_IC_WAVE_REST)
+      return *why = "wave initial data must be LTS_IC_WAVE_SHELL, _PLANAR or _REST", false;
   } else {
     return *why = "bc must be 0 or 1", false;
   }
   if (p.precision != 0 && p.precision != 1) return *why = "precision must be 0 (FP64) or 1 (mixed)", false;
   if (p.ic == LTS_IC_WAVE_SHELL && (p.ic_params[3] < 0 || p.ic_params[3] > 4))
     return *why = "shell initial data takes at most 4 modes", false;
+  if ((p.nl_c != 0.0 || p.orbit != 0) && p.pde != LTS_PDE_WAVE)
+    return *why = "source terms are for the wave equation", false;
+  if (p.orbit != 0 && (p.orbit != 1 || !(p.orbit_params[2] > 0.0)))
+    return *why = "orbit must be 0 or 1, with width orbit_params[2] > 0", false;
+  if (!std::isfinite(p.nl_c)) return *why = "nl_c must be finite", false;
   return true;
 }
 
@@ -972,7 +981,7 @@ ltsoct::BatchInst batch_descriptor(lts_plan* P) {
 }
 
 lts_status batch_alloc(lts_batch* B, int n_slots) {
-  const size_t pre_ints = size_t(ltsoct::kMaxBatch + 1) * (4 + 4 + 1 + ltsoct::kMaxLevel + 2);
+  const size_t pre_ints = size_t(ltsoct::kMaxBatch + 1) * (4 + 4 + 1 + ltsoct::kMaxLevel + 2) + 8;
   std::vector<ltsoct::BatchInst> empty(n_slots);
   std::memset(empty.data(), 0, sizeof(ltsoct::BatchInst) * n_slots);
   cudaError_t e = ltsoct::prepare_batch_kernels();
@@ -993,6 +1002,7 @@ lts_status batch_alloc(lts_batch* B, int n_slots) {
   B->args.prol_pre = B->d_pre + 4 * (ltsoct::kMaxBatch + 1);
   B->args.zip_pre = B->d_pre + 8 * (ltsoct::kMaxBatch + 1);
   B->args.hang_pre = B->d_pre + 9 * (ltsoct::kMaxBatch + 1);
+  B->args.next_item = B->d_pre + (ltsoct::kMaxBatch + 1) * (4 + 4 + 1 + ltsoct::kMaxLevel + 2);
   return LTS_OK;
 }
 

@@ -51,16 +51,19 @@ struct Predicate {
   int64_t c[8][3];
   int64_t r2_out = 0;  // squared outer radius (floor)
   int64_t r2_in = 0;   // squared inner radius (ceil), shell only
+  double ring_r = 0, ring_b = 0;  // circle: radius and band in lattice units
 };
 
 Predicate make_predicate(const lts_refine_spec& s) {
   Predicate p;
   p.kind = s.kind;
-  p.n = s.kind == 1 ? 1 : s.n_centers;
+  p.n = s.kind == 0 ? s.n_centers : 1;
   const double scale = static_cast<double>(int64_t(1) << kDepth);
   const double ext = s.hi - s.lo;
   for (int i = 0; i < p.n; ++i)
     for (int d = 0; d < 3; ++d) p.c[i][d] = std::llround((s.centers[i][d] - s.lo) / ext * scale);
+  p.ring_r = s.radius / ext * scale;
+  p.ring_b = s.band / ext * scale;
   const double outer = s.kind == 1 ? s.radius + s.band : s.radius;
   const double ro = outer / ext * scale;
   p.r2_out = static_cast<int64_t>(std::floor(ro * ro));
@@ -90,9 +93,33 @@ inline void box_distances(const int64_t lo[3], int64_t edge, const int64_t c[3],
   *dmax2 = b;
 }
 
+// circle of radius R in the plane z = c_z around the axis through c: the box's
+// distance to it is sqrt(drho^2 + dz^2), drho the gap between R and the box's
+// range [rho_min, rho_max] of distances from the axis, dz its gap to the plane.
+// Evaluated in IEEE doubles (exact integer inputs, correctly rounded sqrt, no
+// contraction), so the decision is the same on every host.
+bool ring_holds(const Predicate& p, const int64_t lo[3], int64_t edge) {
+  int64_t near2 = 0, far2 = 0;
+  for (int d = 0; d < 2; ++d) {
+    const int64_t hi = lo[d] + edge, c = p.c[0][d];
+    const int64_t gap = c < lo[d] ? lo[d] - c : (c > hi ? c - hi : 0);
+    near2 += gap * gap;
+    const int64_t f = std::max(std::llabs(c - lo[d]), std::llabs(hi - c));
+    far2 += f * f;
+  }
+  const int64_t cz = p.c[0][2];
+  const int64_t dz = cz < lo[2] ? lo[2] - cz : (cz > lo[2] + edge ? cz - lo[2] - edge : 0);
+  const double rho_min = std::sqrt(static_cast<double>(near2));
+  const double rho_max = std::sqrt(static_cast<double>(far2));
+  const double drho = std::max(0.0, std::max(rho_min - p.ring_r, p.ring_r - rho_max));
+  const double z = static_cast<double>(dz);
+  return drho * drho + z * z <= p.ring_b * p.ring_b;
+}
+
 bool predicate_holds(const Predicate& p, const Oct& o) {
   const int64_t lo[3] = {o.x, o.y, o.z};
   const int64_t edge = int64_t(1) << (kDepth - o.l);
+  if (p.kind == 2) return ring_holds(p, lo, edge);
   for (int i = 0; i < p.n; ++i) {
     int64_t dmin2, dmax2;
     box_distances(lo, edge, p.c[i], &dmin2, &dmax2);
@@ -121,8 +148,8 @@ inline Oct child_of(const Oct& o, int c) {
 // refinement of the refined tree.
 bool build_octree(const lts_refine_spec& spec, std::vector<Oct>* leaves, std::string* err) {
   if (!(spec.hi > spec.lo) || spec.l_min < 0 || spec.l_max < spec.l_min || spec.l_max > kMaxLevel ||
-      spec.kind < 0 || spec.kind > 1 || (spec.kind == 0 && (spec.n_centers < 1 || spec.n_centers > 8))) {
-    *err = "octree_build: invalid refinement spec (need lo < hi, 0 <= l_min <= l_max <= 18, kind 0/1, 1..8 centers)";
+      spec.kind < 0 || spec.kind > 2 || (spec.kind == 0 && (spec.n_centers < 1 || spec.n_centers > 8))) {
+    *err = "octree_build: invalid refinement spec (need lo < hi, 0 <= l_min <= l_max <= 18, kind 0/1/2, 1..8 centers)";
     return false;
   }
   const Predicate pred = make_predicate(spec);

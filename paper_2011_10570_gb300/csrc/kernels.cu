@@ -228,6 +228,7 @@ struct StageSmem {
   int src[kNT];
   unsigned short code[kNT];  // rx | ry << 4 | rz << 8 | (level diff + 1) << 12 | exterior << 15
   NbrView nv;
+  double orb[2];             // orbit centre x_1 at this octant's stage time
 };
 
 constexpr unsigned kExterior = 1u << 15;
@@ -313,6 +314,35 @@ __device__ __noinline__ void radiative_rhs(const StageSmem<NF, R>& S, const Stag
   }
 }
 
+// source terms of phi_t at one node: -c sin(2 chi)/r^2 (eq. phi, 0 at r = 0) and the
+// two orbiting Gaussians centred at +-(cx, cy, 0), cx + i cy = R e^{i W t_s}
+// node position in the stage type (FP32 positions suffice for FP32 source terms)
+template <typename R>
+__device__ __forceinline__ R node_x(double lo, double ext, int P6) {
+  if constexpr (sizeof(R) == sizeof(double)) {
+    return lattice_to_x(lo, ext, P6);
+  } else {
+    return fmaf(float(ext) * (1.0f / (6.0f * float(1 << kDepth))), float(P6), float(lo));
+  }
+}
+
+template <typename R>
+__device__ __noinline__ R wave_source(const StageArgs& A, const int P6[3], R chi, double cx, double cy) {
+  const R x = node_x<R>(A.lo, A.ext, P6[0]), y = node_x<R>(A.lo, A.ext, P6[1]), z = node_x<R>(A.lo, A.ext, P6[2]);
+  R src = 0;
+  if (A.nl_c != 0.0) {
+    const R r2 = x * x + y * y + z * z;
+    if (r2 > R(0)) src = -R(A.nl_c) * sin(R(2) * chi) / r2;
+  }
+  if (A.orbit) {
+    const R ax = R(cx), ay = R(cy), inv_w = R(1) / R(A.orb[2]);
+    const R d1 = (x - ax) * (x - ax) + (y - ay) * (y - ay) + z * z;
+    const R d2 = (x + ax) * (x + ax) + (y + ay) * (y + ay) + z * z;
+    src += R(A.orb[3]) * (exp(-d1 * inv_w) + exp(-d2 * inv_w));
+  }
+  return src;
+}
+
 // One RK stage of octant b (Alg. 2 compute_stage, or Alg. 1 when A.gts): called by
 // every thread of a CTA of kThreads threads, with S in shared memory.
 template <int NF, typename R>
@@ -328,6 +358,13 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
 
   load_neighbours(A.tree, b, S.nv);
   if (tid < 4) S.om[tid] = A.om[tid];
+  if (tid == 0 && A.orbit) {
+    // x_1 = R (cos W t_s, sin W t_s, 0) at the stage time t_s = t_b + c_s dt of this level
+    double c, sn;
+    sincos(A.orb[1] * fma(A.c_s, A.lc[lb].dt, A.t_b), &sn, &c);
+    S.orb[0] = A.orb[0] * c;
+    S.orb[1] = A.orb[0] * sn;
+  }
   __syncthreads();
 
   // 1. source of every padded point (coarsest leaf containing it, then smallest Morton key)
@@ -472,6 +509,10 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
       const R kop = fma(R(-60), f0v, fma(R(15), F1, fma(R(-6), F2, F3)));
       kv[0] = fma(kos, koc, f0v);
       kv[NF - 1] = fma(kos, kop, lap);
+      if (A.nl_c != 0.0 || A.orbit) {
+        const int P6[3] = {6 * me.x + i * eb, 6 * me.y + j * eb, 6 * me.z + k * eb};
+        kv[NF - 1] += wave_source<R>(A, P6, c0v, S.orb[0], S.orb[1]);
+      }
       if (A.bc == LTS_BC_RADIATIVE && touches) {
         const int P6[3] = {6 * me.x + i * eb, 6 * me.y + j * eb, 6 * me.z + k * eb};
         const bool on_bnd = P6[0] == 0 || P6[1] == 0 || P6[2] == 0 || P6[0] == kLatt6 || P6[1] == kLatt6 ||
@@ -823,6 +864,7 @@ __global__ void batch_round_begin(BatchArgs B) {
     }
   }
   __syncthreads();
+  if (threadIdx.x < 8) B.next_item[threadIdx.x] = 0;
   if (threadIdx.x == 0) {
     for (int s = 0; s < 4; ++s) {
       int* sp = B.stage_pre + s * (kMaxBatch + 1);
@@ -880,20 +922,30 @@ __device__ __forceinline__ void copy_args(T* dst, const T* src) {
   for (int q = threadIdx.x; q < int(sizeof(T) / 8); q += blockDim.x) d[q] = __ldg(s + q);
 }
 
+// Work items (octant-stages of all instances, in instance order) are claimed one at
+// a time from a counter, so that CTAs that drew expensive octants (level interfaces,
+// the boundary) do not hold up the launch; a CTA re-reads an instance's arguments
+// into shared memory only when its next item belongs to another instance.
+__device__ __forceinline__ int claim_item(int* counter, int* slot) {
+  __syncthreads();
+  if (threadIdx.x == 0) *slot = atomicAdd(counter, 1);
+  __syncthreads();
+  return *slot;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kThreads, 4) batch_stage_kernel(const __grid_constant__ BatchArgs B, int stage) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ StageArgs args;  // the current instance's arguments
+  __shared__ int s_item;
   const int* pre = B.stage_pre + stage * (kMaxBatch + 1);
   const int total = pre[B.n];
-  // a contiguous block of work items per CTA: few switches between instances
-  const int per = (total + gridDim.x - 1) / gridDim.x;
-  const int end = min(total, (blockIdx.x + 1) * per);
   int cur = -1;
-  for (int item = blockIdx.x * per; item < end; ++item) {
+  for (;;) {
+    const int item = claim_item(B.next_item + 4 + stage, &s_item);
+    if (item >= total) break;
     const int i = batch_find(pre, B.n + 1, item);
     if (i != cur) {
-      __syncthreads();
       copy_args(&args, &B.inst[i].st[stage]);
       __syncthreads();
       cur = i;
@@ -903,7 +955,6 @@ __global__ void __launch_bounds__(kThreads, 4) batch_stage_kernel(const __grid_c
       stage_octant<1, R>(*reinterpret_cast<StageSmem<1, R>*>(smem_raw), args, b);
     else
       stage_octant<2, R>(*reinterpret_cast<StageSmem<2, R>*>(smem_raw), args, b);
-    __syncthreads();
   }
 }
 
@@ -911,15 +962,15 @@ template <typename R>
 __global__ void __launch_bounds__(256) batch_prolong_kernel(const __grid_constant__ BatchArgs B, int stage) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ ProlongArgs args;
+  __shared__ int s_item;
   const int* pre = B.prol_pre + stage * (kMaxBatch + 1);
   const int total = pre[B.n];
-  const int per = (total + gridDim.x - 1) / gridDim.x;
-  const int end = min(total, (blockIdx.x + 1) * per);
   int cur = -1;
-  for (int item = blockIdx.x * per; item < end; ++item) {
+  for (;;) {
+    const int item = claim_item(B.next_item + stage, &s_item);
+    if (item >= total) break;
     const int i = batch_find(pre, B.n + 1, item);
     if (i != cur) {
-      __syncthreads();
       copy_args(&args, &B.inst[i].pr[stage]);
       __syncthreads();
       cur = i;
@@ -929,7 +980,6 @@ __global__ void __launch_bounds__(256) batch_prolong_kernel(const __grid_constan
       prolong_octant<1, R>(*reinterpret_cast<ProlongSmem<1, R>*>(smem_raw), args, b);
     else
       prolong_octant<2, R>(*reinterpret_cast<ProlongSmem<2, R>*>(smem_raw), args, b);
-    __syncthreads();
   }
 }
 
@@ -1010,7 +1060,7 @@ __global__ void init_kernel(InitArgs A) {
       const double z = r - R;
       v0 = exp(-z * z / w) * (1.0 + amp * pert);
       v1 = 0.0;
-    } else {
+    } else if (A.ic != LTS_IC_WAVE_REST) {
       double d[2][5];
       exact_derivs(A.ic, A.icp, A.adv, x, A.t0, d);
       v0 = d[0][0];

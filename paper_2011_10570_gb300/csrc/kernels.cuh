@@ -64,6 +64,11 @@ struct StageArgs {
   const void* up;        // prolonged stage inputs of coarser sources, [slot][nf][2197], stage type
   int mixed;             // 1: FP32 stages, tile and right-hand side; FP64 state and corrections
   const int* up_slot;    // slot of an octant in `up` (-1: not a coarser source)
+  // wave source terms (eq. phi and the orbiting Gaussians); c_s is this stage's node
+  double nl_c;
+  int orbit;
+  double orb[4];         // radius, angular speed, width, amplitude
+  double c_s;
 };
 
 // Prolongation of the stage inputs of coarser sources (Fig. unzip, coarse -> fine)
@@ -165,6 +170,8 @@ struct BatchArgs {
   int* prol_pre;         // [4][kMaxBatch + 1]: prefix sums of the octants to prolong
   int* zip_pre;          // [kMaxBatch + 1]: octants of instances that reconcile this round
   int* hang_pre;         // [kMaxLevel + 2][kMaxBatch + 1]: their hanging-node octants per level
+  int* next_item;        // [2][4]: next unclaimed work item of the prolong / stage launch of each stage,
+                         // zeroed by batch_round_begin
 };
 
 cudaError_t prepare_batch_kernels();  // outside any stream capture

@@ -37,7 +37,8 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 class Problem(C.Structure):
     _fields_ = [("pde", C.c_int), ("adv", C.c_double * 3), ("cfl", C.c_double), ("ko_sigma", C.c_double),
                 ("rk", C.c_int), ("bc", C.c_int), ("ic", C.c_int), ("ic_params", C.c_double * 32),
-                ("precision", C.c_int), ("stream", C.c_void_p), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", C.c_void_p)]
+                ("precision", C.c_int), ("stream", C.c_void_p), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", C.c_void_p),
+                ("nl_c", C.c_double), ("orbit", C.c_int), ("orbit_params", C.c_double * 4)]
 
 
 class Stats(C.Structure):
@@ -193,6 +194,10 @@ class Plan:
         for i, v in enumerate(params):
             p.ic_params[i] = v
         p.precision = int(prob.get("precision", 0))
+        p.nl_c = float(prob.get("nl_c", 0.0))
+        p.orbit = int(prob.get("orbit", 0))
+        for i, v in enumerate(prob.get("orbit_params", ())):
+            p.orbit_params[i] = v
         p.stream = self.stream.cuda_stream
         dev, strm = self.device, self.stream
 

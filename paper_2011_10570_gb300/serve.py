@@ -5,11 +5,17 @@ The server keeps every admitted solve resident on the device (octree tables, RK
 state) in a slot of a batch (``lts_batch_create_slots``), and advances all of them
 together in rounds: each round performs one LTS substep (Alg. 2, Fig. blk_loop)
 of every resident solve, with one persistent launch per RK stage covering the
-active levels of all of them.  Between rounds of a chunk the server
+active levels of all of them.  Between chunks of rounds the server
   * retires solves that reached their end time (result copied to the host,
     device memory returned, slot freed), and
-  * admits waiting requests while a slot is free and the device-memory budget
-    holds their estimated footprint.
+  * admits waiting requests, first come first served, while a slot is free, the
+    device-memory budget holds their estimated footprint, and the GPU is not yet
+    saturated: the resident solves' mean active octants per substep (eq. w_nuts
+    over the 2^(l_max - l_min) substeps of a macro step) stay within `saturation`.
+    Batching adds throughput only while one substep of the resident solves does
+    not fill the GPU; past that point sharing it would only stretch every
+    request's latency, so further requests wait.
+A single resident solve runs on its own plan's kernels (no batch indirection).
 Latency is arrival to result; throughput is node-updates per second of wall time.
 
 ``serve_one_at_a_time`` solves the same stream first-come-first-served, one
@@ -65,6 +71,13 @@ def substeps_to(plan, t_end):
     return n_macro * (1 << (st["l_max"] - st["l_min"]))
 
 
+def mean_active_octants(levels):
+    """octants stepping in an average substep: sum_l n_l 2^(l - l_max) (eq. w_nuts / 2^L)"""
+    levels = np.asarray(levels)
+    lmax = int(levels.max())
+    return float(np.sum(np.ldexp(1.0, levels.astype(np.int64) - lmax)))
+
+
 def node_updates(st, n_sub0, n):
     lmin, lmax = st["l_min"], st["l_max"]
     counts = st["octants_per_level"]
@@ -77,7 +90,8 @@ def node_updates(st, n_sub0, n):
 
 
 class Server:
-    def __init__(self, slots=16, hbm_budget=64 << 30, chunk=8, precision=0, keep_results=True):
+    def __init__(self, slots=16, hbm_budget=64 << 30, chunk=8, precision=0, keep_results=True,
+                 saturation=8192.0):
         import torch
         self.torch = torch
         self.stream = torch.cuda.current_stream()
@@ -87,35 +101,47 @@ class Server:
         self.chunk = chunk
         self.precision = precision
         self.keep = keep_results
+        self.saturation = saturation
 
     def serve(self, requests, realtime=True):
         """Serve `requests` (sorted by arrival).  With realtime, arrivals are honoured
         against the wall clock; otherwise every request is available at once."""
         torch = self.torch
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
-        active = {}                      # slot -> [req, plan, remaining, admitted, est, updates]
+        active = {}                      # slot -> [req, plan, remaining, admitted, est, updates, load]
         used = 0
+        load = 0.0                       # mean active octants per substep of the resident solves
         results = []
+        trees = {}                       # rid -> (octree, device bytes, load), built once per request
         t0 = time.perf_counter()
         now = lambda: time.perf_counter() - t0
+
+        def prepare(req):
+            if req.rid not in trees:
+                tree = ltsoct.Octree(req.work["spec"])
+                nf = 2 if req.work["prob"]["pde"] == 1 else 1
+                trees[req.rid] = (tree, state_bytes(len(tree), nf, self.precision),
+                                  mean_active_octants(tree.export()[1]))
+            return trees[req.rid]
+
         while pending or active:
             # admit while a slot is free and the budget holds
             while pending and (not realtime or pending[0].arrival <= now()) and len(active) < self.nslots:
                 req = pending[0]
-                tree = ltsoct.Octree(req.work["spec"])
-                nf = 2 if req.work["prob"]["pde"] == 1 else 1
-                est = state_bytes(len(tree), nf, self.precision)
-                if used + est > self.budget and active:
-                    break                # wait for memory to be freed
+                tree, est, ld = prepare(req)
+                if active and (used + est > self.budget or load + ld > self.saturation):
+                    break                # wait for memory to be freed or the GPU to have room
                 pending.popleft()
+                del trees[req.rid]
                 prob = dict(req.work["prob"], precision=self.precision)
                 plan = ltsoct.Plan(tree, prob, stream=self.stream)
                 plan.set_initial(0.0)
                 n = substeps_to(plan, req.t_end)
                 slot = next(s for s in range(self.nslots) if s not in active)
                 self.batch.attach(slot, plan)
-                active[slot] = [req, plan, n, now(), est, node_updates(plan.stats(), 0, n)]
+                active[slot] = [req, plan, n, now(), est, node_updates(plan.stats(), 0, n), ld]
                 used += est
+                load += ld
             if not active:
                 if pending:
                     time.sleep(max(0.0, min(0.01, pending[0].arrival - now())))
@@ -124,7 +150,16 @@ class Server:
             k = min(self.chunk, min(a[2] for a in active.values()))
             for s, a in active.items():
                 steps[s] = min(k, a[2])
-            self.batch.run(steps, graph=True)
+            if len(active) == 1:
+                (s0, a0), = active.items()
+                a0[1].run_substeps(steps[s0])
+            else:
+                self.batch.run(steps, graph=True)
+            # host work while the GPU runs the chunk: octrees of requests that have arrived
+            for req in list(pending)[:self.nslots]:
+                if realtime and req.arrival > now():
+                    break
+                prepare(req)
             torch.cuda.current_stream().synchronize()
             for s in list(active):
                 a = active[s]
@@ -138,6 +173,7 @@ class Server:
                                           int(round(st["time"] / st["dt_finest"])), a[5], state))
                     self.batch.detach(s)
                     used -= a[4]
+                    load -= a[6]
                     del active[s]
                     del plan
         return sorted(results, key=lambda r: r.rid), now()

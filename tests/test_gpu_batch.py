@@ -24,13 +24,15 @@ def lt():
 def instances():
     return [W.advection_gauss(l_min=2, l_max=4), W.advection_gauss(l_min=2, l_max=3, rk=3),
             W.wave_planar(l_min=2, l_max=4), W.wave_shell(l_min=3, l_max=5, half=4.0, radius=1.5, width=0.2),
-            W.advection_gauss(l_min=1, l_max=6, radius=1e-3)]
+            W.advection_gauss(l_min=1, l_max=6, radius=1e-3),
+            W.wave_nonlinear(l_min=2, l_max=4, half=4.0, radius=1.5, width=0.2),
+            W.wave_orbit(l_min=2, l_max=4, band=0.2, half=2.0, omega=3.0, precision=0)]
 
 
 @pytest.mark.parametrize("graph", [True, False])
 def test_batch_equals_instances_alone(lt, graph):
     ws = instances()
-    substeps = [9, 7, 16, 5, 40]
+    substeps = [9, 7, 16, 5, 40, 6, 11]
     alone, batched = [], []
     for w in ws:
         a = lt.Plan(lt.Octree(w["spec"]), w["prob"])
@@ -42,7 +44,7 @@ def test_batch_equals_instances_alone(lt, graph):
     for p, n in zip(alone, substeps):
         p.run_substeps(n)
     batch = lt.Batch(batched)
-    batch.run(substeps[:2] + [0, 0, 0], graph=graph)     # a first call, some plans idle
+    batch.run(substeps[:2] + [0] * (len(ws) - 2), graph=graph)     # a first call, some plans idle
     batch.run([0, 0] + substeps[2:], graph=graph)
     for a, b, n in zip(alone, batched, substeps):
         assert a.stats()["time"] == b.stats()["time"]

@@ -55,9 +55,30 @@ def test_budget_limits_resident_solves(srv):
     from paper_2011_10570_gb300 import ltsoct
     sizes = [srv.state_bytes(len(ltsoct.Octree(r.work["spec"])), 2 if r.work["prob"]["pde"] == 1 else 1, 0)
              for r in reqs]
-    # room for the largest request only: they run one after the other
-    server = srv.Server(slots=4, chunk=4, hbm_budget=max(sizes))
+    # room for the largest request alone: whenever a request is admitted, the solves
+    # resident at that moment and it fit the budget together
+    budget = max(sizes)
+    server = srv.Server(slots=4, chunk=4, hbm_budget=budget)
+    res, _ = server.serve(reqs, realtime=False)
+    size = {r.rid: sz for r, sz in zip(reqs, sizes)}
+    for r in res:
+        resident = [q for q in res if q.rid != r.rid and q.admitted <= r.admitted < q.finished]
+        assert sum(size[q.rid] for q in resident) + size[r.rid] <= budget or not resident
+    assert len(res) == 3
+
+
+def test_saturated_gpu_serves_first_come_first_served(srv):
+    """With a saturation threshold below any one solve's load, a request is admitted
+    only when the GPU is free: the server degenerates to one solve at a time, and the
+    results are still those of solving each request alone."""
+    ws, t_ends = small_requests()
+    reqs = [srv.Request(i, 0.0, dict(spec=w["spec"], prob=w["prob"]), t) for i, (w, t) in
+            enumerate(zip(ws[:3], t_ends[:3]))]
+    server = srv.Server(slots=4, chunk=4, saturation=1.0)
     res, _ = server.serve(reqs, realtime=False)
     spans = sorted((r.admitted, r.finished) for r in res)
     for (a0, f0), (a1, f1) in zip(spans[:-1], spans[1:]):
         assert a1 >= f0 - 1e-9
+    alone, _ = srv.serve_one_at_a_time(reqs, realtime=False)
+    for a, b in zip(alone, res):
+        assert np.array_equal(a.state, b.state)
