@@ -66,6 +66,7 @@ struct lts_plan {
   int* d_up_slot = nullptr;
   void* d_up = nullptr;                 // prolonged stage inputs [slot][nf][2197], stage type
   int* d_err = nullptr;
+  unsigned* d_padmap = nullptr;  // [N][2197] padding map, built once by padmap_kernel
   int64_t launches = 0;               // every kernel launched by the plan
   size_t bytes = 0;
   cudaStream_t stream = nullptr;
@@ -214,6 +215,7 @@ ltsoct::StageArgs stage_args(const lts_plan* P, int stage, int first, int lstar,
   a.err = P->d_err;
   a.up = P->d_up;
   a.up_slot = P->d_up_slot;
+  a.padmap = P->d_padmap;
   a.nl_c = P->prob.nl_c;
   a.orbit = P->prob.orbit;
   for (int i = 0; i < 4; ++i) a.orb[i] = P->prob.orbit_params[i];
@@ -544,8 +546,9 @@ lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_
   P->d_up_box = static_cast<int*>(dev_alloc(P, sizeof(int) * nup));
   P->d_up_slot = static_cast<int*>(dev_alloc(P, sizeof(int) * P->N));
   P->d_up = dev_alloc(P, P->es * nup * P->nf * ltsoct::kNT);
+  P->d_padmap = static_cast<unsigned*>(dev_alloc(P, sizeof(unsigned) * size_t(P->N) * ltsoct::kNT));
   if (!P->d_oct || !P->d_nbr || !P->d_fine || !P->d_hang || !P->d_u[0] || !P->d_u[1] || !P->d_K || !P->d_err ||
-      !P->d_U[0] || !P->d_U[1] || !P->d_up_list || !P->d_up_box || !P->d_up_slot || !P->d_up) {
+      !P->d_U[0] || !P->d_U[1] || !P->d_up_list || !P->d_up_box || !P->d_up_slot || !P->d_up || !P->d_padmap) {
     release(P);
     delete P;
     return fail(LTS_ENOMEM, "lts_plan_create: device allocation failed");
@@ -571,13 +574,24 @@ lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_
   cudaError_t e6 = cudaMemsetAsync(P->d_u[0], 0, fbytes, P->stream);
   cudaError_t e7 = cudaMemsetAsync(P->d_u[1], 0, fbytes, P->stream);
   cudaError_t e9 = cudaMemsetAsync(P->d_err, 0, sizeof(int) * 4, P->stream);
+  cudaError_t e13 = (e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess && e9 == cudaSuccess)
+                        ? ltsoct::launch_padmap(dev_tree(P), P->d_padmap, P->d_err, P->stream)
+                        : cudaErrorInvalidValue;
+  if (e13 == cudaSuccess) P->launches++;
+  int herr = 0;
+  cudaError_t e14 = cudaMemcpyAsync(&herr, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, P->stream);
   cudaError_t e8 = cudaStreamSynchronize(P->stream);
-  for (cudaError_t e : {e1, e2, e3, e4, e5, e6, e7, e9, e10, e11, e12, e8})
+  for (cudaError_t e : {e1, e2, e3, e4, e5, e6, e7, e9, e10, e11, e12, e13, e14, e8})
     if (e != cudaSuccess) {
       release(P);
       delete P;
       return cuda_fail(e, "lts_plan_create: upload");
     }
+  if (herr) {
+    release(P);
+    delete P;
+    return fail(LTS_EINTERNAL, "lts_plan_create: padding map: a source lay outside its octant (unbalanced tree)");
+  }
   *out = P;
   return LTS_OK;
 }
@@ -776,6 +790,7 @@ static lts_status export_map(lts_plan* P, const int32_t* octs, int64_t n, int32_
   a.nodes = nodes;
   a.src = d_src;
   a.r = d_r;
+  a.padmap = P->d_padmap;
   CK(ltsoct::launch_maps(a, P->stream), "map kernel launch");
   P->launches++;
   CK(cudaMemcpyAsync(src, d_src, sizeof(int) * n * npts, cudaMemcpyDeviceToHost, P->stream), "copy");
@@ -819,6 +834,7 @@ lts_status lts_export_pad_map_static(lts_plan* P, const int32_t* octs, int64_t n
   a.nodes = 0;
   a.src = d_src;  // every element the copies below read is written by the kernel
   a.r = d_r;
+  a.padmap = P->d_padmap;
   CK(ltsoct::launch_maps(a, P->stream), "map kernel launch");
   P->launches++;
   CK(cudaMemcpyAsync(src, d_src, sizeof(int) * n * ltsoct::kNT, cudaMemcpyDeviceToHost, P->stream), "copy");

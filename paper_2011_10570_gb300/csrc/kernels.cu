@@ -89,25 +89,38 @@ __device__ __forceinline__ void axis_candidates(int i, int& d0, int& d1) {
   }
 }
 
-// (i,j,k) in the octant's node units, i in [-3, 9]; returns -1 outside the domain
-__device__ int resolve_source(const NbrView& nv, int i, int j, int k, int self, bool with_self) {
+// slot of a source in the neighbour view: d (0..26, 13 = the octant itself) for the
+// leaf covering neighbour box d, 27 + 8 d + c for child c of a split box d
+constexpr unsigned kSlotNone = 255u;
+
+// (i,j,k) in the octant's node units, i in [-3, 9]; returns -1 outside the domain.
+// With `slot`, also reports the source's slot (kSlotNone outside the domain).
+__device__ int resolve_source(const NbrView& nv, int i, int j, int k, int self, bool with_self,
+                              unsigned* slot = nullptr) {
   int x0, x1, y0, y1, z0, z1;
   axis_candidates(i, x0, x1);
   axis_candidates(j, y0, y1);
   axis_candidates(k, z0, z1);
   int best = INT_MAX;
+  unsigned best_slot = kSlotNone;
   for (int dz = z0; dz <= z1; ++dz)
     for (int dy = y0; dy <= y1; ++dy)
       for (int dx = x0; dx <= x1; ++dx) {
         const int d = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
         if (d == 13) {
-          if (with_self) best = min(best, self);
+          if (with_self && self < best) {
+            best = self;
+            best_slot = 13u;
+          }
           continue;
         }
         const int e = nv.nbr[d];
         if (e == -1) continue;
         if (e >= 0) {
-          best = min(best, e);
+          if (e < best) {
+            best = e;
+            best_slot = unsigned(d);
+          }
           continue;
         }
         // split neighbour box: children whose closed boxes contain the point
@@ -119,10 +132,22 @@ __device__ int resolve_source(const NbrView& nv, int i, int j, int k, int self, 
           for (int hy = hy0; hy <= hy1; ++hy)
             for (int hx = hx0; hx <= hx1; ++hx) {
               const int leaf = nv.kids[d][hx + 2 * hy + 4 * hz];
-              if (leaf >= 0) best = min(best, leaf);
+              if (leaf >= 0 && leaf < best) {
+                best = leaf;
+                best_slot = 27u + 8u * unsigned(d) + unsigned(hx + 2 * hy + 4 * hz);
+              }
             }
       }
+  if (slot) *slot = best_slot;
   return best == INT_MAX ? -1 : best;
+}
+
+// the leaf in a slot of the neighbour view (-1 for kSlotNone)
+__device__ __forceinline__ int slot_leaf(const NbrView& nv, unsigned slot, int self) {
+  if (slot == 13u) return self;
+  if (slot < 27u) return nv.nbr[slot];
+  if (slot < kSlotNone) return (&nv.kids[0][0])[slot - 27u];
+  return -1;
 }
 
 // half-node coordinate of lattice6 coordinate P in a source with anchor a, level l
@@ -367,34 +392,15 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
   }
   __syncthreads();
 
-  // 1. source of every padded point (coarsest leaf containing it, then smallest Morton key)
-  for (int q = tid; q < kNT; q += blockDim.x) {
-    const int i = q % 13 - 3, j = (q / 13) % 13 - 3, k = q / 169 - 3;
-    int src;
-    unsigned code;
-    if (i >= 0 && i <= 6 && j >= 0 && j <= 6 && k >= 0 && k <= 6) {
-      src = b;
-      code = unsigned(2 * i) | unsigned(2 * j) << 4 | unsigned(2 * k) << 8 | 1u << 12;
-    } else {
-      src = resolve_source(S.nv, i, j, k, b, false);
-      if (src < 0) {
-        code = kExterior;
-      } else {
-        const int4 so = A.tree.oct[src];
-        const int rx = half_node(6 * me.x + i * eb, so.x, so.w);
-        const int ry = half_node(6 * me.y + j * eb, so.y, so.w);
-        const int rz = half_node(6 * me.z + k * eb, so.z, so.w);
-        if (unsigned(rx) > 12u || unsigned(ry) > 12u || unsigned(rz) > 12u || unsigned(so.w - lb + 1) > 2u) {
-          atomicOr(A.err, 1);  // never on a balanced tree: report and use a zero ghost
-          src = -1;
-          code = kExterior;
-        } else {
-          code = unsigned(rx) | unsigned(ry) << 4 | unsigned(rz) << 8 | unsigned(so.w - lb + 1) << 12;
-        }
-      }
+  // 1. source of every padded point (coarsest leaf containing it, then smallest Morton
+  //    key), from the plan's padding map: slot in the neighbour view and half-node code
+  {
+    const unsigned* __restrict__ pm = A.padmap + (long long)b * kNT;
+    for (int q = tid; q < kNT; q += blockDim.x) {
+      const unsigned e = __ldg(pm + q);
+      S.src[q] = slot_leaf(S.nv, e & 255u, b);
+      S.code[q] = static_cast<unsigned short>(e >> 8);
     }
-    S.src[q] = src;
-    S.code[q] = static_cast<unsigned short>(code);
   }
   __syncthreads();
 
@@ -1080,7 +1086,59 @@ cudaError_t launch_init(const InitArgs& a, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// Map export (parity checks): the same resolver the stage and sync kernels use
+// Padding map (Fig. unzip): for every octant and padded point, the source's slot in
+// the octant's neighbour view and the point's half-node code in the source.  The
+// tree is static, so this is resolved once per plan instead of at every stage.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) padmap_kernel(const DevTree T, unsigned* __restrict__ out, int* err) {
+  __shared__ NbrView nv;
+  for (int b = blockIdx.x; b < T.n; b += gridDim.x) {
+    __syncthreads();
+    load_neighbours(T, b, nv);
+    __syncthreads();
+    const int4 me = T.oct[b];
+    const int lb = me.w;
+    const int eb = 1 << (kDepth - lb);
+    for (int q = threadIdx.x; q < kNT; q += blockDim.x) {
+      const int i = q % 13 - 3, j = (q / 13) % 13 - 3, k = q / 169 - 3;
+      unsigned slot, code;
+      if (i >= 0 && i <= 6 && j >= 0 && j <= 6 && k >= 0 && k <= 6) {
+        slot = 13u;
+        code = unsigned(2 * i) | unsigned(2 * j) << 4 | unsigned(2 * k) << 8 | 1u << 12;
+      } else {
+        const int src = resolve_source(nv, i, j, k, b, false, &slot);
+        if (src < 0) {
+          slot = kSlotNone;
+          code = kExterior;
+        } else {
+          const int4 so = T.oct[src];
+          const int rx = half_node(6 * me.x + i * eb, so.x, so.w);
+          const int ry = half_node(6 * me.y + j * eb, so.y, so.w);
+          const int rz = half_node(6 * me.z + k * eb, so.z, so.w);
+          if (unsigned(rx) > 12u || unsigned(ry) > 12u || unsigned(rz) > 12u || unsigned(so.w - lb + 1) > 2u) {
+            atomicOr(err, 1);  // never on a balanced tree: reported, and the point becomes a zero ghost
+            slot = kSlotNone;
+            code = kExterior;
+          } else {
+            code = unsigned(rx) | unsigned(ry) << 4 | unsigned(rz) << 8 | unsigned(so.w - lb + 1) << 12;
+          }
+        }
+      }
+      out[(long long)b * kNT + q] = slot | code << 8;
+    }
+  }
+}
+
+cudaError_t launch_padmap(const DevTree& t, unsigned* out, int* err, cudaStream_t s) {
+  if (t.n <= 0) return cudaSuccess;
+  const int blocks = t.n < 152 * 8 ? t.n : 152 * 8;
+  padmap_kernel<<<blocks, 256, 0, s>>>(t, out, err);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Map export (parity checks).  Padding maps are decoded from the plan's padding
+// map (what the stage kernel reads); node maps use the resolver of the sync kernels.
 // ---------------------------------------------------------------------------
 __global__ void maps_kernel(MapArgs A) {
   __shared__ SyncSmem S;
@@ -1090,6 +1148,19 @@ __global__ void maps_kernel(MapArgs A) {
   const int4 me = A.tree.oct[b];
   const int eb = 1 << (kDepth - me.w);
   const int npts = A.nodes ? kNV : kNT;
+  if (!A.nodes && A.padmap) {
+    for (int q = threadIdx.x; q < kNT; q += blockDim.x) {
+      const unsigned e = A.padmap[(long long)b * kNT + q];
+      const int src = slot_leaf(S.nv, e & 255u, b);
+      const unsigned code = e >> 8;
+      const long long o = (long long)blockIdx.x * kNT + q;
+      A.src[o] = src;
+      A.r[o * 3 + 0] = src >= 0 ? int(code & 15u) : -1;
+      A.r[o * 3 + 1] = src >= 0 ? int((code >> 4) & 15u) : -1;
+      A.r[o * 3 + 2] = src >= 0 ? int((code >> 8) & 15u) : -1;
+    }
+    return;
+  }
   for (int q = threadIdx.x; q < npts; q += blockDim.x) {
     int i, j, k;
     if (A.nodes) {

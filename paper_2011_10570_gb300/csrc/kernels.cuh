@@ -64,6 +64,7 @@ struct StageArgs {
   const void* up;        // prolonged stage inputs of coarser sources, [slot][nf][2197], stage type
   int mixed;             // 1: FP32 stages, tile and right-hand side; FP64 state and corrections
   const int* up_slot;    // slot of an octant in `up` (-1: not a coarser source)
+  const unsigned* padmap;  // [N][2197]: source slot | half-node code << 8 per padded point
   // wave source terms (eq. phi and the orbiting Gaussians); c_s is this stage's node
   double nl_c;
   int orbit;
@@ -135,6 +136,7 @@ struct MapArgs {
   int nodes;             // 0: 2197 padded points, 1: 343 nodes
   int* src;
   int* r;
+  const unsigned* padmap;  // padding maps: decode this plan's padding map (nullptr: resolve)
 };
 
 // ---- batches: many instances advanced together ------------------------------
@@ -186,6 +188,7 @@ cudaError_t launch_sync_hanging(const SyncArgs& a, cudaStream_t s);
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
 cudaError_t launch_init(const InitArgs& a, cudaStream_t s);
 cudaError_t launch_maps(const MapArgs& a, cudaStream_t s);
+cudaError_t launch_padmap(const DevTree& t, unsigned* out, int* err, cudaStream_t s);
 cudaError_t launch_widen(const float* in, double* out, long long n, cudaStream_t s);
 
 // allocation-free padding-map export: largest octant list one call accepts

@@ -58,9 +58,10 @@ class Result:
 
 def state_bytes(n_octants, nf, precision, p=4):
     """Device bytes of a plan: state (2 copies, FP64), RK stages and 2 stage-input
-    buffers in the stage type, prolonged inputs (at most one slot per octant) and tables."""
+    buffers in the stage type, prolonged inputs (at most one slot per octant), the
+    padding map (4 bytes per padded point) and tables."""
     es = 4 if precision == 1 else 8
-    per_octant = 343 * nf * (2 * 8 + (p + 2) * es) + 2197 * nf * es + 27 * 4 + 64
+    per_octant = 343 * nf * (2 * 8 + (p + 2) * es) + 2197 * nf * es + 2197 * 4 + 27 * 4 + 64
     return int(n_octants * per_octant)
 
 
