@@ -67,6 +67,15 @@ struct lts_plan {
   void* d_up = nullptr;                 // prolonged stage inputs [slot][nf][2197], stage type
   int* d_err = nullptr;
   unsigned* d_padmap = nullptr;  // [N][2197] padding map, built once by padmap_kernel
+  // octree-to-block decomposition (Sec. 3.2.5): complete sibling groups are stepped as
+  // one 13^3-node block by block_kernel, the other octants one by one by stage_kernel
+  bool blocking = true;
+  std::vector<int32_t> grp, single;     // first octant of each group / the other octants, level order
+  int64_t grp_off[34] = {}, single_off[34] = {};
+  int* d_grp = nullptr;
+  int* d_single = nullptr;
+  int* d_gsrc = nullptr;                // [G][19^3]
+  unsigned short* d_gcode = nullptr;    // [G][19^3]
   int64_t launches = 0;               // every kernel launched by the plan
   size_t bytes = 0;
   cudaStream_t stream = nullptr;
@@ -160,6 +169,51 @@ lts_status sync_fields(lts_plan* P, void* vb0, void* vb1, unsigned sel, int elem
   return LTS_OK;
 }
 
+// Prolongation plan of one coarser source: the class mask `cls` (bit cx + 3 cy + 9 cz)
+// re-expressed in the frame of the cheapest pass order, with the order's index in
+// bits 27-29 (orders as in ltsoct::kProlongOrders).  Cost model: pass 1 interpolates
+// 7 x 7 source lines at each odd position of its axis, pass 2 7 lines per odd
+// position of the plane it needs, pass 3 every odd point of the set, 7 multiply-adds
+// each; a class spans 4 / 5 / 4 positions, two of them odd.
+uint32_t prolong_plan_word(uint32_t cls) {
+  static const int kN[3] = {4, 5, 4}, kOdd[3] = {2, 2, 2};
+  int64_t best_cost = INT64_MAX;
+  uint32_t best = 0;
+  for (int o = 0; o < 6; ++o) {
+    const int* ax = ltsoct::kProlongOrders[o];  // pass axes a, b, c
+    uint32_t m = 0;                             // mask in the (a, b, c) frame
+    for (int c2 = 0; c2 < 3; ++c2)
+      for (int c1 = 0; c1 < 3; ++c1)
+        for (int c0 = 0; c0 < 3; ++c0) {
+          int c[3];
+          c[ax[0]] = c0;
+          c[ax[1]] = c1;
+          c[ax[2]] = c2;
+          if (cls >> (c[0] + 3 * c[1] + 9 * c[2]) & 1u) m |= 1u << (c0 + 3 * c1 + 9 * c2);
+        }
+    int64_t cost = 0;
+    for (int ca = 0; ca < 3; ++ca) {
+      bool any_a = false;
+      for (int cb = 0; cb < 3; ++cb) {
+        bool any_ab = false;
+        for (int cc = 0; cc < 3; ++cc)
+          if (m >> (ca + 3 * cb + 9 * cc) & 1u) {
+            any_ab = true;
+            cost += int64_t(kN[ca]) * kN[cb] * kOdd[cc] * 7;
+          }
+        if (any_ab) cost += int64_t(kN[ca]) * kOdd[cb] * 49;
+        any_a = any_a || any_ab;
+      }
+      if (any_a) cost += int64_t(kOdd[ca]) * 343;
+    }
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = m | uint32_t(o) << 27;
+    }
+  }
+  return best;
+}
+
 ltsoct::StageTerms terms_of(const double* row, int p) {
   ltsoct::StageTerms t{};
   for (int j = 0; j < p; ++j)
@@ -216,6 +270,9 @@ ltsoct::StageArgs stage_args(const lts_plan* P, int stage, int first, int lstar,
   a.up = P->d_up;
   a.up_slot = P->d_up_slot;
   a.padmap = P->d_padmap;
+  a.grp = P->d_grp;
+  a.gsrc = P->d_gsrc;
+  a.gcode = P->d_gcode;
   a.nl_c = P->prob.nl_c;
   a.orbit = P->prob.orbit;
   for (int i = 0; i < 4; ++i) a.orb[i] = P->prob.orbit_params[i];
@@ -255,15 +312,33 @@ lts_status launch_prolong_for(lts_plan* P, const ltsoct::StageArgs& sa, int lsta
   return LTS_OK;
 }
 
-lts_status launch_stage_timed(lts_plan* P, const ltsoct::StageArgs& a, int count) {
+// one RK stage of the octants of levels >= lstar: complete sibling groups by the
+// block kernel, the other octants by the stage kernel (or every octant by the stage
+// kernel when blocking is off)
+lts_status launch_stage_timed(lts_plan* P, const ltsoct::StageArgs& a, int lstar) {
+  const int count = int(P->N - P->off[lstar]);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (P->profiling) {
     CK(cudaEventCreate(&e0), "cudaEventCreate");
     CK(cudaEventCreate(&e1), "cudaEventCreate");
     CK(cudaEventRecord(e0, P->stream), "cudaEventRecord");
   }
-  CK(ltsoct::launch_stage(a, count, P->stream), "stage kernel launch");
-  if (count > 0) P->launches++;
+  if (P->blocking) {
+    ltsoct::StageArgs ab = a;
+    ab.first = int(P->grp_off[lstar]);
+    const int ng = int(int64_t(P->grp.size()) - P->grp_off[lstar]);
+    CK(ltsoct::launch_block(ab, ng, P->stream), "block kernel launch");
+    if (ng > 0) P->launches++;
+    ltsoct::StageArgs as = a;
+    as.list = P->d_single;
+    as.first = int(P->single_off[lstar]);
+    const int ns = int(int64_t(P->single.size()) - P->single_off[lstar]);
+    CK(ltsoct::launch_stage(as, ns, P->stream), "stage kernel launch");
+    if (ns > 0) P->launches++;
+  } else {
+    CK(ltsoct::launch_stage(a, count, P->stream), "stage kernel launch");
+    if (count > 0) P->launches++;
+  }
   if (P->profiling) {
     CK(cudaEventRecord(e1, P->stream), "cudaEventRecord");
     P->events.emplace_back(e0, e1);
@@ -281,12 +356,11 @@ int active_level(const lts_plan* P, int64_t n) {
 lts_status lts_substep(lts_plan* P) {
   const int lstar = active_level(P, P->n_sub);
   const int first = int(P->off[lstar]);
-  const int count = int(P->N - first);
   for (int s = 0; s < P->p; ++s) {
     const ltsoct::StageArgs sa = stage_args(P, s, first, lstar, 0);
     lts_status st = launch_prolong_for(P, sa, lstar);
     if (st != LTS_OK) return st;
-    st = launch_stage_timed(P, sa, count);
+    st = launch_stage_timed(P, sa, lstar);
     if (st != LTS_OK) return st;
   }
   // the active levels completed a step: their state now lives in the other buffer
@@ -307,7 +381,7 @@ lts_status gts_step(lts_plan* P) {
     const ltsoct::StageArgs sa = stage_args(P, s, 0, P->lmin, 1);
     lts_status st = launch_prolong_for(P, sa, P->lmin);
     if (st != LTS_OK) return st;
-    st = launch_stage_timed(P, sa, int(P->N));
+    st = launch_stage_timed(P, sa, P->lmin);
     if (st != LTS_OK) return st;
     void* Ks = static_cast<char*>(P->d_K) + s * kstride_bytes;
     st = sync_fields(P, Ks, Ks, 0u, int(P->es));
@@ -487,30 +561,68 @@ lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_
     while (P->hang_off[l + 1] < int64_t(P->hang.size()) && P->octs[P->hang[P->hang_off[l + 1]]].l == l)
       P->hang_off[l + 1]++;
   }
-  // coarser sources: octants with a split neighbour box; the box of half-node
-  // positions their finer neighbours read lies within 3 half-node units of the
-  // faces, edges and corners those neighbours touch
+  // coarser sources: octants with a split neighbour box.  The half-node positions
+  // their finer neighbours read lie within 3 half-node units of the faces, edges
+  // and corners those neighbours touch: per axis, a direction -1 / 0 / +1 covers the
+  // classes {low} / {low, mid, high} / {high} of r in [0,3] / [4,8] / [9,12], so the
+  // set read is a union of class boxes, kept as a 27-bit mask.  The interpolation
+  // passes run in the axis order with the fewest multiply-adds for that set.
   P->up_slot.assign(P->N, -1);
   for (int64_t b = 0; b < P->N; ++b) {
-    int lo[3] = {13, 13, 13}, hi[3] = {-1, -1, -1};
+    uint32_t cls = 0;
     for (int d = 0; d < 27; ++d) {
       if (d == 13 || P->nb.nbr[b * 27 + d] > -2) continue;
       const int dd[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
-      for (int a = 0; a < 3; ++a) {
-        const int l0 = dd[a] > 0 ? 9 : 0, h0 = dd[a] < 0 ? 3 : 12;
-        lo[a] = std::min(lo[a], l0);
-        hi[a] = std::max(hi[a], h0);
-      }
+      for (int cz = 0; cz < 3; ++cz)
+        for (int cy = 0; cy < 3; ++cy)
+          for (int cx = 0; cx < 3; ++cx) {
+            const int c[3] = {cx, cy, cz};
+            bool in = true;
+            for (int a = 0; a < 3; ++a) in = in && (dd[a] == 0 || c[a] == dd[a] + 1);
+            if (in) cls |= 1u << (cx + 3 * cy + 9 * cz);
+          }
     }
-    if (hi[0] < 0) continue;
+    if (!cls) continue;
     P->up_slot[b] = int32_t(P->up_list.size());
     P->up_list.push_back(int32_t(b));
-    P->up_box.push_back(lo[0] | hi[0] << 4 | lo[1] << 8 | hi[1] << 12 | lo[2] << 16 | hi[2] << 20);
+    P->up_box.push_back(int32_t(prolong_plan_word(cls)));
   }
   for (int l = 0; l <= 32; ++l) {
     P->up_off[l + 1] = P->up_off[l];
     while (P->up_off[l + 1] < int64_t(P->up_list.size()) && P->octs[P->up_list[P->up_off[l + 1]]].l == l)
       P->up_off[l + 1]++;
+  }
+  // blocks: complete sibling groups (8 consecutive octants of one level, siblings being
+  // adjacent in Morton order, whose anchors are the 8 children of one parent) that no
+  // coarser leaf touches
+  for (int64_t b = 0; b < P->N;) {
+    const ltsoct::Oct& o = P->octs[b];
+    const int32_t e = int32_t(1) << (ltsoct::kDepth - o.l);
+    bool group = o.l > 0 && b + 7 < P->N && ((o.x / e) & 1) == 0 && ((o.y / e) & 1) == 0 && ((o.z / e) & 1) == 0;
+    for (int c = 1; c < 8 && group; ++c) {
+      const ltsoct::Oct& q = P->octs[b + c];
+      group = q.l == o.l && q.x == o.x + (c & 1) * e && q.y == o.y + ((c >> 1) & 1) * e && q.z == o.z + ((c >> 2) & 1) * e;
+    }
+    for (int c = 0; c < 8 && group; ++c)
+      for (int d = 0; d < 27 && group; ++d) {
+        const int n = P->nb.nbr[(b + c) * 27 + d];
+        group = n < 0 || P->octs[n].l >= o.l;
+      }
+    if (group) {
+      P->grp.push_back(int32_t(b));
+      b += 8;
+    } else {
+      P->single.push_back(int32_t(b));
+      b += 1;
+    }
+  }
+  for (int l = 0; l <= 32; ++l) {
+    P->grp_off[l + 1] = P->grp_off[l];
+    while (P->grp_off[l + 1] < int64_t(P->grp.size()) && P->octs[P->grp[P->grp_off[l + 1]]].l == l)
+      P->grp_off[l + 1]++;
+    P->single_off[l + 1] = P->single_off[l];
+    while (P->single_off[l + 1] < int64_t(P->single.size()) && P->octs[P->single[P->single_off[l + 1]]].l == l)
+      P->single_off[l + 1]++;
   }
   // reading of the CFL condition (Sec. 3.4): dt_f = cfl * node spacing of the finest level
   const double h_f = (P->spec.hi - P->spec.lo) / (6.0 * double(int64_t(1) << P->lmax));
@@ -547,8 +659,14 @@ lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_
   P->d_up_slot = static_cast<int*>(dev_alloc(P, sizeof(int) * P->N));
   P->d_up = dev_alloc(P, P->es * nup * P->nf * ltsoct::kNT);
   P->d_padmap = static_cast<unsigned*>(dev_alloc(P, sizeof(unsigned) * size_t(P->N) * ltsoct::kNT));
+  const size_t ng = std::max<size_t>(P->grp.size(), 1);
+  P->d_grp = static_cast<int*>(dev_alloc(P, sizeof(int) * ng));
+  P->d_single = static_cast<int*>(dev_alloc(P, sizeof(int) * std::max<size_t>(P->single.size(), 1)));
+  P->d_gsrc = static_cast<int*>(dev_alloc(P, sizeof(int) * ng * ltsoct::kBT));
+  P->d_gcode = static_cast<unsigned short*>(dev_alloc(P, sizeof(unsigned short) * ng * ltsoct::kBT));
   if (!P->d_oct || !P->d_nbr || !P->d_fine || !P->d_hang || !P->d_u[0] || !P->d_u[1] || !P->d_K || !P->d_err ||
-      !P->d_U[0] || !P->d_U[1] || !P->d_up_list || !P->d_up_box || !P->d_up_slot || !P->d_up || !P->d_padmap) {
+      !P->d_U[0] || !P->d_U[1] || !P->d_up_list || !P->d_up_box || !P->d_up_slot || !P->d_up || !P->d_padmap ||
+      !P->d_grp || !P->d_single || !P->d_gsrc || !P->d_gcode) {
     release(P);
     delete P;
     return fail(LTS_ENOMEM, "lts_plan_create: device allocation failed");
@@ -578,10 +696,21 @@ lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_
                         ? ltsoct::launch_padmap(dev_tree(P), P->d_padmap, P->d_err, P->stream)
                         : cudaErrorInvalidValue;
   if (e13 == cudaSuccess) P->launches++;
+  cudaError_t e15 = P->grp.empty() ? cudaSuccess
+                                   : cudaMemcpyAsync(P->d_grp, P->grp.data(), sizeof(int) * P->grp.size(),
+                                                     cudaMemcpyHostToDevice, P->stream);
+  cudaError_t e16 = P->single.empty() ? cudaSuccess
+                                      : cudaMemcpyAsync(P->d_single, P->single.data(), sizeof(int) * P->single.size(),
+                                                        cudaMemcpyHostToDevice, P->stream);
+  cudaError_t e17 = (e13 == cudaSuccess && e15 == cudaSuccess)
+                        ? ltsoct::launch_groupmap(dev_tree(P), P->d_grp, int(P->grp.size()), P->d_padmap, P->d_gsrc,
+                                                  P->d_gcode, P->stream)
+                        : cudaErrorInvalidValue;
+  if (e17 == cudaSuccess && !P->grp.empty()) P->launches++;
   int herr = 0;
   cudaError_t e14 = cudaMemcpyAsync(&herr, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, P->stream);
   cudaError_t e8 = cudaStreamSynchronize(P->stream);
-  for (cudaError_t e : {e1, e2, e3, e4, e5, e6, e7, e9, e10, e11, e12, e13, e14, e8})
+  for (cudaError_t e : {e1, e2, e3, e4, e5, e6, e7, e9, e10, e11, e12, e13, e15, e16, e17, e14, e8})
     if (e != cudaSuccess) {
       release(P);
       delete P;
@@ -620,6 +749,7 @@ lts_status lts_plan_stats(const lts_plan* P, lts_stats* out) {
   out->gts_work_per_macro = P->w_gts;
   out->device_bytes = P->bytes;
   out->kernel_launches = P->launches;
+  out->blocked_octants = int64_t(P->grp.size()) * 8;
   return LTS_OK;
 }
 
@@ -840,6 +970,12 @@ lts_status lts_export_pad_map_static(lts_plan* P, const int32_t* octs, int64_t n
   CK(cudaMemcpyAsync(src, d_src, sizeof(int) * n * ltsoct::kNT, cudaMemcpyDeviceToHost, P->stream), "copy");
   CK(cudaMemcpyAsync(r, d_r, sizeof(int) * n * ltsoct::kNT * 3, cudaMemcpyDeviceToHost, P->stream), "copy");
   CK(cudaStreamSynchronize(P->stream), "cudaStreamSynchronize");
+  return LTS_OK;
+}
+
+lts_status lts_set_blocking(lts_plan* P, int on) {
+  if (!P) return fail(LTS_EINVAL, "lts_set_blocking: null plan");
+  P->blocking = on != 0;
   return LTS_OK;
 }
 

@@ -318,29 +318,63 @@ __device__ __noinline__ void fill_extrapolated(StageSmem<NF, R>& S, int4 me, int
   }
 }
 
-// radiative right-hand side at a node on the domain boundary
-template <int NF, typename R>
-__device__ __noinline__ void radiative_rhs(const StageSmem<NF, R>& S, const StageArgs& A, int c0, const int P6[3],
-                                           R inv12h, R kv[NF]) {
+// radiative right-hand side at a node on the domain boundary; T[f] are the padded
+// tiles (y stride SY, z stride SZ), c0 the node's tile index
+template <int NF, typename R, int SY, int SZ>
+__device__ __noinline__ void radiative_rhs(const R* const* T, const StageArgs& A, int c0, const int P6[3], R inv12h,
+                                           R kv[NF]) {
   const R x[3] = {R(lattice_to_x(A.lo, A.ext, P6[0])), R(lattice_to_x(A.lo, A.ext, P6[1])),
                   R(lattice_to_x(A.lo, A.ext, P6[2]))};
   const R r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-  const int st[3] = {1, 13, 169};
+  const int st[3] = {1, SY, SZ};
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
-    const R* T = S.T[f];
+    const R* Tf = T[f];
     R xd = 0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const R d1 = fma(R(8), T[c0 + st[a]] - T[c0 - st[a]], T[c0 - 2 * st[a]] - T[c0 + 2 * st[a]]) * inv12h;
+      const R d1 = fma(R(8), Tf[c0 + st[a]] - Tf[c0 - st[a]], Tf[c0 - 2 * st[a]] - Tf[c0 + 2 * st[a]]) * inv12h;
       xd = fma(x[a], d1, xd);
     }
-    kv[f] = -(xd + (f == 0 ? R(1) : R(2)) * T[c0]) / r;
+    kv[f] = -(xd + (f == 0 ? R(1) : R(2)) * Tf[c0]) / r;
   }
 }
 
-// source terms of phi_t at one node: -c sin(2 chi)/r^2 (eq. phi, 0 at r = 0) and the
-// two orbiting Gaussians centred at +-(cx, cy, 0), cx + i cy = R e^{i W t_s}
+// right-hand side at one node from its padded tile: advection (4th-order D1) or the
+// wave equation (4th-order Laplacian), plus Kreiss-Oliger dissipation; symmetric pair
+// sums at distance 1, 2, 3 are shared by the derivative and the dissipation
+template <int NF, typename R, int SY, int SZ>
+__device__ __forceinline__ void rhs_node(const R* const* Tt, int c0, const StageArgs& A, R kos, R inv12h, R inv12h2,
+                                         R kv[NF]) {
+  if (A.pde == LTS_PDE_ADVECTION) {
+    const R* T = Tt[0];
+    const R uc = T[c0];
+    const R P1 = (T[c0 - 1] + T[c0 + 1]) + (T[c0 - SY] + T[c0 + SY]) + (T[c0 - SZ] + T[c0 + SZ]);
+    const R P2 = (T[c0 - 2] + T[c0 + 2]) + (T[c0 - 2 * SY] + T[c0 + 2 * SY]) + (T[c0 - 2 * SZ] + T[c0 + 2 * SZ]);
+    const R P3 = (T[c0 - 3] + T[c0 + 3]) + (T[c0 - 3 * SY] + T[c0 + 3 * SY]) + (T[c0 - 3 * SZ] + T[c0 + 3 * SZ]);
+    R d1s = R(A.adv[0]) * fma(R(8), T[c0 + 1] - T[c0 - 1], T[c0 - 2] - T[c0 + 2]);
+    d1s = fma(R(A.adv[1]), fma(R(8), T[c0 + SY] - T[c0 - SY], T[c0 - 2 * SY] - T[c0 + 2 * SY]), d1s);
+    d1s = fma(R(A.adv[2]), fma(R(8), T[c0 + SZ] - T[c0 - SZ], T[c0 - 2 * SZ] - T[c0 + 2 * SZ]), d1s);
+    const R ko = fma(R(-60), uc, fma(R(15), P1, fma(R(-6), P2, P3)));
+    kv[0] = fma(kos, ko, -inv12h * d1s);
+  } else {
+    const R* Tc = Tt[0];
+    const R* Tp = Tt[NF - 1];
+    const R c0v = Tc[c0], f0v = Tp[c0];
+    const R C1 = (Tc[c0 - 1] + Tc[c0 + 1]) + (Tc[c0 - SY] + Tc[c0 + SY]) + (Tc[c0 - SZ] + Tc[c0 + SZ]);
+    const R C2 = (Tc[c0 - 2] + Tc[c0 + 2]) + (Tc[c0 - 2 * SY] + Tc[c0 + 2 * SY]) + (Tc[c0 - 2 * SZ] + Tc[c0 + 2 * SZ]);
+    const R C3 = (Tc[c0 - 3] + Tc[c0 + 3]) + (Tc[c0 - 3 * SY] + Tc[c0 + 3 * SY]) + (Tc[c0 - 3 * SZ] + Tc[c0 + 3 * SZ]);
+    const R F1 = (Tp[c0 - 1] + Tp[c0 + 1]) + (Tp[c0 - SY] + Tp[c0 + SY]) + (Tp[c0 - SZ] + Tp[c0 + SZ]);
+    const R F2 = (Tp[c0 - 2] + Tp[c0 + 2]) + (Tp[c0 - 2 * SY] + Tp[c0 + 2 * SY]) + (Tp[c0 - 2 * SZ] + Tp[c0 + 2 * SZ]);
+    const R F3 = (Tp[c0 - 3] + Tp[c0 + 3]) + (Tp[c0 - 3 * SY] + Tp[c0 + 3 * SY]) + (Tp[c0 - 3 * SZ] + Tp[c0 + 3 * SZ]);
+    const R lap = fma(R(-90), c0v, fma(R(16), C1, -C2)) * inv12h2;
+    const R koc = fma(R(-60), c0v, fma(R(15), C1, fma(R(-6), C2, C3)));
+    const R kop = fma(R(-60), f0v, fma(R(15), F1, fma(R(-6), F2, F3)));
+    kv[0] = fma(kos, koc, f0v);
+    kv[NF - 1] = fma(kos, kop, lap);
+  }
+}
+
 // node position in the stage type (FP32 positions suffice for FP32 source terms)
 template <typename R>
 __device__ __forceinline__ R node_x(double lo, double ext, int P6) {
@@ -488,42 +522,20 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
     const int c0 = (i + 3) + 13 * (j + 3) + 169 * (k + 3);
     const R kos = R(lc.kos), inv12h = R(lc.inv12h), inv12h2 = R(lc.inv12h2);
     R kv[NF];
-    if (A.pde == LTS_PDE_ADVECTION) {
-      const R* T = S.T[0];
-      const R uc = T[c0];
-      // symmetric pair sums at distance 1, 2, 3 (Kreiss-Oliger) and the D1 differences
-      const R P1 = (T[c0 - 1] + T[c0 + 1]) + (T[c0 - 13] + T[c0 + 13]) + (T[c0 - 169] + T[c0 + 169]);
-      const R P2 = (T[c0 - 2] + T[c0 + 2]) + (T[c0 - 26] + T[c0 + 26]) + (T[c0 - 338] + T[c0 + 338]);
-      const R P3 = (T[c0 - 3] + T[c0 + 3]) + (T[c0 - 39] + T[c0 + 39]) + (T[c0 - 507] + T[c0 + 507]);
-      R d1s = R(A.adv[0]) * fma(R(8), T[c0 + 1] - T[c0 - 1], T[c0 - 2] - T[c0 + 2]);
-      d1s = fma(R(A.adv[1]), fma(R(8), T[c0 + 13] - T[c0 - 13], T[c0 - 26] - T[c0 + 26]), d1s);
-      d1s = fma(R(A.adv[2]), fma(R(8), T[c0 + 169] - T[c0 - 169], T[c0 - 338] - T[c0 + 338]), d1s);
-      const R ko = fma(R(-60), uc, fma(R(15), P1, fma(R(-6), P2, P3)));
-      kv[0] = fma(kos, ko, -inv12h * d1s);
-    } else {
-      const R* Tc = S.T[0];
-      const R* Tp = S.T[NF - 1];
-      const R c0v = Tc[c0], f0v = Tp[c0];
-      const R C1 = (Tc[c0 - 1] + Tc[c0 + 1]) + (Tc[c0 - 13] + Tc[c0 + 13]) + (Tc[c0 - 169] + Tc[c0 + 169]);
-      const R C2 = (Tc[c0 - 2] + Tc[c0 + 2]) + (Tc[c0 - 26] + Tc[c0 + 26]) + (Tc[c0 - 338] + Tc[c0 + 338]);
-      const R C3 = (Tc[c0 - 3] + Tc[c0 + 3]) + (Tc[c0 - 39] + Tc[c0 + 39]) + (Tc[c0 - 507] + Tc[c0 + 507]);
-      const R F1 = (Tp[c0 - 1] + Tp[c0 + 1]) + (Tp[c0 - 13] + Tp[c0 + 13]) + (Tp[c0 - 169] + Tp[c0 + 169]);
-      const R F2 = (Tp[c0 - 2] + Tp[c0 + 2]) + (Tp[c0 - 26] + Tp[c0 + 26]) + (Tp[c0 - 338] + Tp[c0 + 338]);
-      const R F3 = (Tp[c0 - 3] + Tp[c0 + 3]) + (Tp[c0 - 39] + Tp[c0 + 39]) + (Tp[c0 - 507] + Tp[c0 + 507]);
-      const R lap = fma(R(-90), c0v, fma(R(16), C1, -C2)) * inv12h2;
-      const R koc = fma(R(-60), c0v, fma(R(15), C1, fma(R(-6), C2, C3)));
-      const R kop = fma(R(-60), f0v, fma(R(15), F1, fma(R(-6), F2, F3)));
-      kv[0] = fma(kos, koc, f0v);
-      kv[NF - 1] = fma(kos, kop, lap);
+    const R* Tt[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) Tt[f] = S.T[f];
+    rhs_node<NF, R, 13, 169>(Tt, c0, A, kos, inv12h, inv12h2, kv);
+    if (A.pde != LTS_PDE_ADVECTION) {
       if (A.nl_c != 0.0 || A.orbit) {
         const int P6[3] = {6 * me.x + i * eb, 6 * me.y + j * eb, 6 * me.z + k * eb};
-        kv[NF - 1] += wave_source<R>(A, P6, c0v, S.orb[0], S.orb[1]);
+        kv[NF - 1] += wave_source<R>(A, P6, Tt[0][c0], S.orb[0], S.orb[1]);
       }
       if (A.bc == LTS_BC_RADIATIVE && touches) {
         const int P6[3] = {6 * me.x + i * eb, 6 * me.y + j * eb, 6 * me.z + k * eb};
         const bool on_bnd = P6[0] == 0 || P6[1] == 0 || P6[2] == 0 || P6[0] == kLatt6 || P6[1] == kLatt6 ||
                             P6[2] == kLatt6;
-        if (on_bnd) radiative_rhs<NF, R>(S, A, c0, P6, inv12h, kv);
+        if (on_bnd) radiative_rhs<NF, R, 13, 169>(Tt, A, c0, P6, inv12h, kv);
       }
     }
     const long long node = (long long)b * kNV + tid;
@@ -554,7 +566,311 @@ template <int NF, typename R>
 __global__ void __launch_bounds__(kThreads, 4) stage_kernel(const __grid_constant__ StageArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StageSmem<NF, R>& S = *reinterpret_cast<StageSmem<NF, R>*>(smem_raw);
-  stage_octant<NF, R>(S, A, A.first + blockIdx.x);
+  stage_octant<NF, R>(S, A, A.list ? A.list[A.first + blockIdx.x] : A.first + blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// Block kernel: one RK stage of a complete sibling group (the 8 children of one
+// parent, all leaves of the same level), stepped as one block of 13^3 nodes with a
+// 19^3 padded tile (the octree-to-block decomposition of Sec. 3.2.5).  Every padded
+// point takes the value the children's own padded tiles would take (the padding
+// rule is a property of the point), and shared face nodes of siblings hold equal
+// values, so each node is computed once and written to each of its 1, 2, 4 or 8
+// octant copies: the results equal those of stage_kernel bit for bit, with 2.5
+// instead of 6.4 gathered points and 0.8 instead of 1 right-hand side per node.
+// ---------------------------------------------------------------------------
+constexpr int kBlockThreads = 448;  // 14 warps: the 2197 block nodes in five passes
+
+template <int NF, typename R>
+struct BlockSmem {
+  R T[NF][kBT];
+  StageTerms om[4];
+  double orb[2];
+};
+
+// exact boundary data at the exterior points of the block tile (as fill_exact)
+template <int NF, typename R>
+__device__ __noinline__ void block_fill_exact(BlockSmem<NF, R>& S, const StageArgs& A, int4 me, int eb, double dtb) {
+  for (int q = threadIdx.x; q < kBT; q += blockDim.x) {
+    const int i = q % kBW - 3, j = (q / kBW) % kBW - 3, k = q / (kBW * kBW) - 3;
+    const int P6[3] = {6 * me.x + i * eb, 6 * me.y + j * eb, 6 * me.z + k * eb};
+    bool ext = false;
+    for (int a = 0; a < 3; ++a) ext = ext || P6[a] < 0 || P6[a] > kLatt6;
+    if (!ext) continue;
+    const double x[3] = {lattice_to_x(A.lo, A.ext, P6[0]), lattice_to_x(A.lo, A.ext, P6[1]),
+                         lattice_to_x(A.lo, A.ext, P6[2])};
+    double d[2][5];
+    exact_derivs(A.ic, A.icp, A.adv, x, A.t_b, d);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      double v = d[f][0], dtp = 1.0;
+      for (int m = 0; m < A.p; ++m) {
+        dtp *= dtb;
+        v = fma(A.gamma[m] * dtp, d[f][m + 1], v);
+      }
+      S.T[f][q] = static_cast<R>(v);
+    }
+  }
+}
+
+// cubic extrapolation along the outward normal, x then y then z (as fill_extrapolated)
+template <int NF, typename R>
+__device__ __noinline__ void block_fill_extrapolated(BlockSmem<NF, R>& S, int4 me, int eb2) {
+  const int anchor[3] = {me.x, me.y, me.z};
+  constexpr int kRoot = 1 << kDepth;
+  constexpr int kLast = 12;  // last node of the block
+  for (int a = 0; a < 3; ++a) {
+    const bool lo_b = anchor[a] == 0, hi_b = anchor[a] + eb2 == kRoot;
+    if (lo_b || hi_b) {
+      const int b1 = (a + 1) % 3, b2 = (a + 2) % 3;
+      const int str = a == 0 ? 1 : (a == 1 ? kBW : kBW * kBW);
+      const int str1 = b1 == 0 ? 1 : (b1 == 1 ? kBW : kBW * kBW);
+      const int str2 = b2 == 0 ? 1 : (b2 == 1 ? kBW : kBW * kBW);
+      for (int t = threadIdx.x; t < kBW * kBW * 3; t += blockDim.x) {
+        const int v1 = t % kBW - 3, v2 = (t / kBW) % kBW - 3, m = t / (kBW * kBW) + 1;
+        const bool ext1 = (anchor[b1] == 0 && v1 < 0) || (anchor[b1] + eb2 == kRoot && v1 > kLast);
+        const bool ext2 = (anchor[b2] == 0 && v2 < 0) || (anchor[b2] + eb2 == kRoot && v2 > kLast);
+        if ((b1 > a && ext1) || (b2 > a && ext2)) continue;
+        const int base = 3 * str + (v1 + 3) * str1 + (v2 + 3) * str2;  // index 0 along axis a
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          if (lo_b) {
+            R v = 0;
+            for (int qq = 0; qq < 4; ++qq) v = fma(R(c_E[m][qq]), S.T[f][base + qq * str], v);
+            S.T[f][base - m * str] = v;
+          }
+          if (hi_b) {
+            R v = 0;
+            for (int qq = 0; qq < 4; ++qq) v = fma(R(c_E[m][qq]), S.T[f][base + (kLast - qq) * str], v);
+            S.T[f][base + (kLast + m) * str] = v;
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int NF, typename R>
+__global__ void __launch_bounds__(kBlockThreads, (sizeof(R) == 8 ? 2 : 3))
+    block_kernel(const __grid_constant__ StageArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  BlockSmem<NF, R>& S = *reinterpret_cast<BlockSmem<NF, R>*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int g = A.first + blockIdx.x;
+  const int b0 = A.grp[g];
+  const int p = A.p;
+  const int s = A.stage;
+  const int4 me = A.tree.oct[b0];  // child 0: its anchor is the parent's
+  const int lb = me.w;
+  const int eb = 1 << (kDepth - lb);
+  const long long kstride = (long long)A.nf * A.fstride;
+  R* __restrict__ K = static_cast<R*>(A.K);
+  if (tid < 4) S.om[tid] = A.om[tid];
+  if (tid == 0 && A.orbit) {
+    double c, sn;
+    sincos(A.orb[1] * fma(A.c_s, A.lc[lb].dt, A.t_b), &sn, &c);
+    S.orb[0] = A.orb[0] * c;
+    S.orb[1] = A.orb[0] * sn;
+  }
+
+  // 1. gathers (as stage_kernel step 2), batched for memory parallelism
+  const int* __restrict__ gs = A.gsrc + (long long)g * kBT;
+  const unsigned short* __restrict__ gc = A.gcode + (long long)g * kBT;
+  const R* Uin = static_cast<const R*>(A.Uin);
+  const double* u0 = A.u[(A.cur_mask >> lb) & 1];
+  const R* up_all = static_cast<const R*>(A.up);
+  constexpr int kB = 4;
+  for (int q0 = 0; q0 < kBT; q0 += kB * kBlockThreads) {
+    R v[kB][NF];
+#pragma unroll
+    for (int it = 0; it < kB; ++it) {
+      const int q = q0 + tid + it * kBlockThreads;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) v[it][f] = 0;
+      if (q < kBT) {
+        const unsigned code = __ldg(gc + q);
+        if (!(code & kExterior)) {
+          const int rx = code & 15, ry = (code >> 4) & 15, rz = (code >> 8) & 15;
+          const int rel_code = (code >> 12) & 3;  // 0 coarser, 1 same, 2 finer
+          const int src = __ldg(gs + q);
+          if (rel_code == 0) {
+            const R* up = up_all + (long long)__ldg(A.up_slot + src) * NF * kNT + rx + 13 * ry + 169 * rz;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) v[it][f] = __ldg(up + f * kNT);
+          } else if (rel_code == 1 || A.gts) {
+            const long long off = (long long)src * kNV + (rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1);
+            if (s == 0) {
+#pragma unroll
+              for (int f = 0; f < NF; ++f) v[it][f] = static_cast<R>(__ldg(u0 + f * A.fstride + off));
+            } else {
+#pragma unroll
+              for (int f = 0; f < NF; ++f) v[it][f] = __ldg(Uin + f * A.fstride + off);
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < kB; ++it) {
+      const int q = q0 + tid + it * kBlockThreads;
+      if (q < kBT) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) S.T[f][q] = v[it][f];
+      }
+    }
+  }
+  __syncthreads();
+
+  // 2. finer sources with the coarse<-fine correction of eq. fc_1 (FP64)
+  if (!A.gts) {
+    for (int q = tid; q < kBT; q += blockDim.x) {
+      const unsigned code = __ldg(gc + q);
+      if ((code & kExterior) || ((code >> 12) & 3) != 2) continue;
+      const int rx = code & 15, ry = (code >> 4) & 15, rz = (code >> 8) & 15;
+      const int ls = lb + 1;
+      const double* ub = A.u[(A.cur_mask >> ls) & 1];
+      const long long off = (long long)__ldg(gs + q) * kNV + (rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1);
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+        S.T[f][q] = static_cast<R>(corrected_value<R>(ub + f * A.fstride + off, K + f * A.fstride + off, kstride,
+                                                      S.om[1], A.lc[ls].dt));
+    }
+  }
+  __syncthreads();
+
+  // 3. physical boundary
+  const LevelConst lc = A.lc[lb];
+  constexpr int kRoot = 1 << kDepth;
+  const int eb2 = 2 * eb;
+  const bool touches = me.x == 0 || me.y == 0 || me.z == 0 || me.x + eb2 == kRoot || me.y + eb2 == kRoot ||
+                       me.z + eb2 == kRoot;
+  if (touches) {
+    if (A.bc == LTS_BC_EXACT)
+      block_fill_exact<NF, R>(S, A, me, eb, lc.dt);
+    else
+      block_fill_extrapolated<NF, R>(S, me, eb2);
+  }
+  __syncthreads();
+
+  // 4. right-hand side at the 13^3 block nodes; stage, next stage input and RK update
+  //    (FP64) written to every octant copy of the node
+  const R kos = R(lc.kos), inv12h = R(lc.inv12h), inv12h2 = R(lc.inv12h2);
+  const R* Tt[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) Tt[f] = S.T[f];
+  R* Uout = static_cast<R*>(A.Uout);
+  for (int n = tid; n < 13 * 13 * 13; n += kBlockThreads) {
+    const int i = n % 13, j = (n / 13) % 13, k = n / 169;
+    const int c0 = (i + 3) + kBW * (j + 3) + kBW * kBW * (k + 3);
+    R kv[NF];
+    rhs_node<NF, R, kBW, kBW * kBW>(Tt, c0, A, kos, inv12h, inv12h2, kv);
+    if (A.pde != LTS_PDE_ADVECTION) {
+      if (A.nl_c != 0.0 || A.orbit) {
+        const int P6[3] = {6 * me.x + i * eb, 6 * me.y + j * eb, 6 * me.z + k * eb};
+        kv[NF - 1] += wave_source<R>(A, P6, Tt[0][c0], S.orb[0], S.orb[1]);
+      }
+      if (A.bc == LTS_BC_RADIATIVE && touches) {
+        const int P6[3] = {6 * me.x + i * eb, 6 * me.y + j * eb, 6 * me.z + k * eb};
+        const bool on_bnd = P6[0] == 0 || P6[1] == 0 || P6[2] == 0 || P6[0] == kLatt6 || P6[1] == kLatt6 ||
+                            P6[2] == kLatt6;
+        if (on_bnd) radiative_rhs<NF, R, kBW, kBW * kBW>(Tt, A, c0, P6, inv12h, kv);
+      }
+    }
+    // octant copies of the node: child c = cx + 2 cy + 4 cz with local node (i - 6 cx, ...);
+    // a coordinate of 6 lies on the face shared by children 0 and 1 of that axis
+    const int cx0 = i > 6, cx1 = i >= 6, cy0 = j > 6, cy1 = j >= 6, cz0 = k > 6, cz1 = k >= 6;
+    const long long own = (long long)(b0 + cx0 + 2 * cy0 + 4 * cz0) * kNV + (i - 6 * cx0) + 7 * (j - 6 * cy0) +
+                          49 * (k - 6 * cz0);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const long long fo = f * A.fstride;
+      const double kd = static_cast<double>(kv[f]);
+      R uout = 0;
+      double unew = 0.0;
+      if (s < p - 1) {
+        double acc = 0.0;
+        for (int q = 0; q < A.next.n; ++q)
+          acc = fma(A.next.w[q],
+                    A.next.j[q] == s ? kd : static_cast<double>(K[(long long)A.next.j[q] * kstride + fo + own]), acc);
+        uout = static_cast<R>(fma(lc.dt, acc, u0[fo + own]));
+      } else if (A.write_update) {
+        double acc = 0.0;
+        for (int q = 0; q < p - 1; ++q) acc = fma(A.w[q], static_cast<double>(K[(long long)q * kstride + fo + own]), acc);
+        acc = fma(A.w[p - 1], kd, acc);
+        unew = fma(lc.dt, acc, u0[fo + own]);
+      }
+      double* unext = A.u[((A.cur_mask >> lb) & 1) ^ 1];
+      for (int cz = cz0; cz <= cz1; ++cz)
+        for (int cy = cy0; cy <= cy1; ++cy)
+          for (int cx = cx0; cx <= cx1; ++cx) {
+            const long long o = fo + (long long)(b0 + cx + 2 * cy + 4 * cz) * kNV + (i - 6 * cx) + 7 * (j - 6 * cy) +
+                                49 * (k - 6 * cz);
+            K[(long long)s * kstride + o] = kv[f];
+            if (s < p - 1)
+              Uout[o] = uout;
+            else if (A.write_update)
+              unext[o] = unew;
+          }
+    }
+  }
+}
+
+template <int NF, typename R>
+static cudaError_t launch_block_t(const StageArgs& a, int count, cudaStream_t s) {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(block_kernel<NF, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(BlockSmem<NF, R>));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  block_kernel<NF, R><<<count, kBlockThreads, sizeof(BlockSmem<NF, R>), s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_block(const StageArgs& a, int count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  if (a.nf == 1) return a.mixed ? launch_block_t<1, float>(a, count, s) : launch_block_t<1, double>(a, count, s);
+  return a.mixed ? launch_block_t<2, float>(a, count, s) : launch_block_t<2, double>(a, count, s);
+}
+
+// Padding of every sibling group's block tile: the point p in [-3, 15]^3 (child node
+// units from the parent's anchor) lies in the padded tile of child c (c_a = 1 iff
+// p_a > 6) at local coordinate p - 6 c in [-3, 9]; its source and code are that
+// child's padding-map entry, with the slot resolved to the leaf.
+__global__ void __launch_bounds__(256) groupmap_kernel(const DevTree T, const int* __restrict__ grp, int count,
+                                                       const unsigned* __restrict__ padmap, int* __restrict__ gsrc,
+                                                       unsigned short* __restrict__ gcode) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)count * kBT;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int g = int(e / kBT), q = int(e - (long long)g * kBT);
+    const int px = q % kBW - 3, py = (q / kBW) % kBW - 3, pz = q / (kBW * kBW) - 3;
+    const int cx = px > 6, cy = py > 6, cz = pz > 6;
+    const int c = grp[g] + cx + 2 * cy + 4 * cz;
+    const int lq = (px - 6 * cx + 3) + 13 * (py - 6 * cy + 3) + 169 * (pz - 6 * cz + 3);
+    const unsigned w = padmap[(long long)c * kNT + lq];
+    const unsigned slot = w & 255u;
+    int src = -1;
+    if (slot == 13u) {
+      src = c;
+    } else if (slot < 27u) {
+      src = T.nbr[(long long)c * 27 + slot];
+    } else if (slot < kSlotNone) {
+      const int d = int(slot - 27u) >> 3, ch = int(slot - 27u) & 7;
+      const int box = T.nbr[(long long)c * 27 + d];
+      src = box <= -2 ? T.fine[(long long)(-box - 2) * 8 + ch] : -1;
+    }
+    gsrc[e] = src;
+    gcode[e] = static_cast<unsigned short>(w >> 8);
+  }
+}
+
+cudaError_t launch_groupmap(const DevTree& t, const int* grp, int count, const unsigned* padmap, int* gsrc,
+                            unsigned short* gcode, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  groupmap_kernel<<<152 * 8, 256, 0, s>>>(t, grp, count, padmap, gsrc, gcode);
+  return cudaGetLastError();
 }
 
 template <int NF, typename R>
@@ -586,21 +902,51 @@ cudaError_t launch_stage(const StageArgs& a, int count, cudaStream_t s) {
 template <int NF, typename R>
 struct ProlongSmem {
   R V[NF][kNV];
-  R X1[NF][13 * 49];      // [rx][z][y]
-  R X2[NF][13 * 13 * 7];  // [rx][ry][z]
+  R X1[NF][13 * 49];      // [ra][jc][jb] in the frame of the pass axes a, b, c
+  R X2[NF][13 * 13 * 7];  // [ra][rb][jc]
   R W[13][7];
 };
 
-// Prolongation of octant b for one stage; called by every thread of a CTA.
+// class of a half-node coordinate: 0 for [0,3], 1 for [4,8], 2 for [9,12]
+__device__ __forceinline__ int half_class(int r) { return r <= 3 ? 0 : (r >= 9 ? 2 : 1); }
+
+// lowest / highest coordinate of the classes in a 3-bit set
+__device__ __forceinline__ int class_lo(unsigned m) { return (m & 1u) ? 0 : ((m & 2u) ? 4 : 9); }
+__device__ __forceinline__ int class_hi(unsigned m) { return (m & 4u) ? 12 : ((m & 2u) ? 8 : 3); }
+
+// Prolongation of octant b for one stage; called by every thread of a CTA.  The
+// passes run along axes a, b, c (a permutation of x, y, z chosen per source on the
+// host); V, X1 and X2 hold the source's values in that frame, and only positions
+// whose class box is in the source's set (or its projections) are computed.
 template <int NF, typename R>
 __device__ void prolong_octant(ProlongSmem<NF, R>& S, const ProlongArgs& A, const int b) {
   const int tid = threadIdx.x;
   const int slot = A.up_slot[b];
   const int lb = A.tree.oct[b].w;
   const int rel = A.gts ? 0 : (lb >= A.lstar ? 2 : 3);
-  const int bx = A.box[slot];
-  const int rx0 = bx & 15, ry0 = (bx >> 8) & 15, rz0 = (bx >> 16) & 15;
-  const int nrx = ((bx >> 4) & 15) - rx0 + 1, nry = ((bx >> 12) & 15) - ry0 + 1, nrz = ((bx >> 20) & 15) - rz0 + 1;
+  const unsigned word = unsigned(A.box[slot]);
+  const unsigned m = word & 0x7ffffffu;  // class mask, bit ca + 3 cb + 9 cc
+  const int order = int(word >> 27);
+  // pass axes (0 = x, 1 = y, 2 = z) of kProlongOrders[order]
+  const int pa = order >> 1, pb = (order == 0 || order == 5) ? 1 : (order == 1 || order == 3) ? 2 : 0;
+  const int pc = 3 - pa - pb;
+  // node strides 1, 7, 49 and half-node strides 1, 13, 169 of the pass axes
+  const int sna = pa == 0 ? 1 : (pa == 1 ? 7 : 49), snb = pb == 0 ? 1 : (pb == 1 ? 7 : 49);
+  const int snc = pc == 0 ? 1 : (pc == 1 ? 7 : 49);
+  // projections of the set: classes of a, and of (a, b) pairs
+  unsigned mab = 0;
+  for (int cc = 0; cc < 3; ++cc) mab |= (m >> (9 * cc)) & 0x1ffu;
+  const unsigned ma = (mab | mab >> 3 | mab >> 6) & 7u;
+  unsigned mb = 0, mc = 0;
+  for (int q = 0; q < 9; ++q) {
+    if (mab >> q & 1u) mb |= 1u << (q / 3);
+  }
+  for (int q = 0; q < 27; ++q) {
+    if (m >> q & 1u) mc |= 1u << (q / 9);
+  }
+  const int a0 = class_lo(ma), na = class_hi(ma) - a0 + 1;
+  const int b0 = class_lo(mb), nb = class_hi(mb) - b0 + 1;
+  const int c0 = class_lo(mc), nc = class_hi(mc) - c0 + 1;
   const long long kstride = (long long)A.nf * A.fstride;
   const R* K = static_cast<const R*>(A.K);
   for (int q = tid; q < 91; q += blockDim.x) S.W[q / 7][q % 7] = R(c_W[q / 7][q % 7]);
@@ -608,8 +954,9 @@ __device__ void prolong_octant(ProlongSmem<NF, R>& S, const ProlongArgs& A, cons
   const R* Uin = static_cast<const R*>(A.Uin);
   const double* ub = A.u[cur ^ (rel == 3 ? 1 : 0)];
   for (int t = tid; t < NF * kNV; t += blockDim.x) {
-    const int f = t / kNV, n = t - f * kNV;
-    const long long off = (long long)b * kNV + n;
+    const int f = t / kNV, n = t - f * kNV;  // n = ja + 7 jb + 49 jc in the pass frame
+    const int ja = n % 7, jb = (n / 7) % 7, jc = n / 49;
+    const long long off = (long long)b * kNV + ja * sna + jb * snb + jc * snc;
     R v;
     if (rel != 0)
       v = static_cast<R>(corrected_value<R>(ub + f * A.fstride + off, K + f * A.fstride + off, kstride, A.om[rel],
@@ -621,58 +968,66 @@ __device__ void prolong_octant(ProlongSmem<NF, R>& S, const ProlongArgs& A, cons
     S.V[f][n] = v;
   }
   __syncthreads();
-  for (int t = tid; t < NF * nrx * 49; t += blockDim.x) {
-    const int f = t / (nrx * 49), rem = t - f * nrx * 49;
-    const int rxi = rem / 49, yz = rem - rxi * 49;  // yz = y + 7 z
-    const int rx = rx0 + rxi;
-    const R* v = S.V[f] + 7 * yz;
+  // pass 1 (axis a): X1[ra][jb + 7 jc]
+  for (int t = tid; t < NF * na * 49; t += blockDim.x) {
+    const int f = t / (na * 49), rem = t - f * na * 49;
+    const int ri = rem / 49, bc = rem - ri * 49;
+    const int ra = a0 + ri;
+    if (!(ma >> half_class(ra) & 1u)) continue;
+    const R* v = S.V[f] + 7 * bc;
     R acc;
-    if (rx & 1) {
+    if (ra & 1) {
       acc = 0;
 #pragma unroll
-      for (int a = 0; a < 7; ++a) acc = fma(S.W[rx][a], v[a], acc);
+      for (int q = 0; q < 7; ++q) acc = fma(S.W[ra][q], v[q], acc);
     } else {
-      acc = v[rx >> 1];
+      acc = v[ra >> 1];
     }
-    S.X1[f][rem] = acc;
+    S.X1[f][ra * 49 + bc] = acc;
   }
   __syncthreads();
-  for (int t = tid; t < NF * nrx * nry * 7; t += blockDim.x) {
-    const int f = t / (nrx * nry * 7), rem = t - f * nrx * nry * 7;
-    const int z = rem % 7, ryi = (rem / 7) % nry, rxi = rem / (7 * nry);
-    const int ry = ry0 + ryi;
-    const R* x1 = S.X1[f] + rxi * 49 + 7 * z;  // [y]
+  // pass 2 (axis b): X2[ra][rb][jc]
+  for (int t = tid; t < NF * na * nb * 7; t += blockDim.x) {
+    const int f = t / (na * nb * 7), rem = t - f * na * nb * 7;
+    const int jc = rem % 7, rbi = (rem / 7) % nb, rai = rem / (7 * nb);
+    const int ra = a0 + rai, rb = b0 + rbi;
+    if (!(mab >> (half_class(ra) + 3 * half_class(rb)) & 1u)) continue;
+    const R* x1 = S.X1[f] + ra * 49 + 7 * jc;  // [jb]
     R acc;
-    if (ry & 1) {
+    if (rb & 1) {
       acc = 0;
 #pragma unroll
-      for (int bb = 0; bb < 7; ++bb) acc = fma(S.W[ry][bb], x1[bb], acc);
+      for (int q = 0; q < 7; ++q) acc = fma(S.W[rb][q], x1[q], acc);
     } else {
-      acc = x1[ry >> 1];
+      acc = x1[rb >> 1];
     }
-    S.X2[f][rem] = acc;
+    S.X2[f][(ra * 13 + rb) * 7 + jc] = acc;
   }
   __syncthreads();
+  // pass 3 (axis c): every position of the set, written at rx + 13 ry + 169 rz
   R* out = static_cast<R*>(A.up) + (long long)slot * NF * kNT;
-  for (int t = tid; t < NF * nrx * nry * nrz; t += blockDim.x) {
-    const int f = t / (nrx * nry * nrz), rem = t - f * nrx * nry * nrz;
-    const int rxi = rem % nrx, ryi = (rem / nrx) % nry, rzi = rem / (nrx * nry);
-    const int rz = rz0 + rzi;
-    const R* x2 = S.X2[f] + (rxi * nry + ryi) * 7;  // [z]
+  const int soa = pa == 0 ? 1 : (pa == 1 ? 13 : 169), sob = pb == 0 ? 1 : (pb == 1 ? 13 : 169);
+  const int soc = pc == 0 ? 1 : (pc == 1 ? 13 : 169);
+  for (int t = tid; t < NF * na * nb * nc; t += blockDim.x) {
+    const int f = t / (na * nb * nc), rem = t - f * na * nb * nc;
+    const int rai = rem % na, rbi = (rem / na) % nb, rci = rem / (na * nb);
+    const int ra = a0 + rai, rb = b0 + rbi, rc = c0 + rci;
+    if (!(m >> (half_class(ra) + 3 * half_class(rb) + 9 * half_class(rc)) & 1u)) continue;
+    const R* x2 = S.X2[f] + (ra * 13 + rb) * 7;  // [jc]
     R acc;
-    if (rz & 1) {
+    if (rc & 1) {
       acc = 0;
 #pragma unroll
-      for (int cc = 0; cc < 7; ++cc) acc = fma(S.W[rz][cc], x2[cc], acc);
+      for (int q = 0; q < 7; ++q) acc = fma(S.W[rc][q], x2[q], acc);
     } else {
-      acc = x2[rz >> 1];
+      acc = x2[rc >> 1];
     }
-    out[f * kNT + (rx0 + rxi) + 13 * (ry0 + ryi) + 169 * rz] = acc;
+    out[f * kNT + ra * soa + rb * sob + rc * soc] = acc;
   }
 }
 
 template <int NF, typename R>
-__global__ void __launch_bounds__(256) prolong_kernel(const __grid_constant__ ProlongArgs A) {
+__global__ void __launch_bounds__(256, 6) prolong_kernel(const __grid_constant__ ProlongArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ProlongSmem<NF, R>& S = *reinterpret_cast<ProlongSmem<NF, R>*>(smem_raw);
   prolong_octant<NF, R>(S, A, A.list[blockIdx.x]);

@@ -65,6 +65,12 @@ struct StageArgs {
   int mixed;             // 1: FP32 stages, tile and right-hand side; FP64 state and corrections
   const int* up_slot;    // slot of an octant in `up` (-1: not a coarser source)
   const unsigned* padmap;  // [N][2197]: source slot | half-node code << 8 per padded point
+  const int* list;         // stage_kernel: CTA x steps list[first + x] (nullptr: octant first + x)
+  // block kernel (Sec. 3.2.5 octree-to-block decomposition): CTA x steps the complete
+  // sibling group grp[first + x] (8 consecutive octants) as one 13^3-node block
+  const int* grp;
+  const int* gsrc;               // [G][19^3] source octant of every padded block point (-1: exterior)
+  const unsigned short* gcode;   // [G][19^3] its half-node code (as in the padding map)
   // wave source terms (eq. phi and the orbiting Gaussians); c_s is this stage's node
   double nl_c;
   int orbit;
@@ -80,7 +86,8 @@ struct ProlongArgs {
   DevTree tree;
   const int* list;       // octants to process (level order)
   int count;
-  const int* box;        // per slot: packed half-node box rx0 | rx1 << 4 | ry0 << 8 | ry1 << 12 | rz0 << 16 | rz1 << 20
+  const int* box;        // per slot: class mask of the half-node positions read (27 bits, in the
+                         // frame of the pass order) | pass order << 27 (kProlongOrders)
   const int* up_slot;
   void* up;
   const double* u[2];
@@ -94,6 +101,9 @@ struct ProlongArgs {
   LevelConst lc[32];
   StageTerms om[4];
 };
+
+// axis orders of the three interpolation passes of the prolongation
+constexpr int kProlongOrders[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
 
 struct SyncArgs {
   DevTree tree;
@@ -182,6 +192,11 @@ cudaError_t launch_batch_round(const BatchArgs& a, int pmax, int lmax_all, int g
 
 cudaError_t upload_tables(const Tables* rk4, const Tables* rk3, const double W[13][7], const double E[4][4]);
 cudaError_t launch_stage(const StageArgs& a, int count, cudaStream_t s);
+cudaError_t launch_block(const StageArgs& a, int count, cudaStream_t s);
+cudaError_t launch_groupmap(const DevTree& t, const int* grp, int count, const unsigned* padmap, int* gsrc,
+                            unsigned short* gcode, cudaStream_t s);
+constexpr int kBW = 19;               // padded block width of a sibling group: 13 nodes + 2 x 3
+constexpr int kBT = kBW * kBW * kBW;  // 6859 padded points
 cudaError_t launch_prolong(const ProlongArgs& a, cudaStream_t s);
 cudaError_t launch_sync_zip(const SyncArgs& a, cudaStream_t s);
 cudaError_t launch_sync_hanging(const SyncArgs& a, cudaStream_t s);

@@ -46,13 +46,14 @@ class Stats(C.Structure):
                 ("octants_per_level", C.c_int64 * 32), ("dt_finest", C.c_double), ("dt_coarsest", C.c_double),
                 ("time", C.c_double), ("substep", C.c_int64), ("model_speedup", C.c_double),
                 ("lts_work_per_macro", C.c_double), ("gts_work_per_macro", C.c_double),
-                ("device_bytes", C.c_size_t), ("kernel_launches", C.c_int64)]
+                ("device_bytes", C.c_size_t), ("kernel_launches", C.c_int64),
+                ("blocked_octants", C.c_int64)]
 
 
 EXPORTS = ["octree_build", "octree_size", "octree_export", "octree_destroy", "lts_plan_create", "lts_plan_destroy",
            "lts_plan_stats", "lts_set_initial", "lts_set_state", "lts_get_state", "lts_get_stage",
            "lts_run_substeps", "lts_advance", "gts_steps", "gts_advance", "lts_export_o2o", "lts_export_pad_map",
-           "lts_export_node_map", "lts_export_pad_map_static", "lts_set_profiling", "lts_kernel_stats", "lts_batch_create", "lts_batch_destroy", "lts_batch_run",
+           "lts_export_node_map", "lts_export_pad_map_static", "lts_set_blocking", "lts_set_profiling", "lts_kernel_stats", "lts_batch_create", "lts_batch_destroy", "lts_batch_run",
            "lts_batch_set_grid", "lts_batch_stats", "lts_batch_create_slots", "lts_batch_attach",
            "lts_batch_detach", "lts_strerror", "lts_last_error"]
 
@@ -92,6 +93,7 @@ def load(path=None):
         "lts_export_pad_map": ([vp, i32p, i64, i32p, i32p], st),
         "lts_export_node_map": ([vp, i32p, i64, i32p, i32p], st),
         "lts_export_pad_map_static": ([vp, i32p, i64, i32p, i32p], st),
+        "lts_set_blocking": ([vp, C.c_int], st),
         "lts_set_profiling": ([vp, C.c_int], st),
         "lts_kernel_stats": ([vp, C.POINTER(i64), C.POINTER(C.c_double), C.POINTER(C.c_double),
                               C.POINTER(C.c_double), C.POINTER(i64), C.c_int], st),
@@ -305,6 +307,10 @@ class Plan:
         r = np.zeros((len(octs), 343, 3), np.int32)
         _check(_lib.lts_export_node_map(self.h, _i32(octs), len(octs), _i32(src), _i32(r)), "lts_export_node_map")
         return src, r
+
+    def set_blocking(self, on=True):
+        """step complete sibling groups as 13^3-node blocks (default on; bit-identical results)"""
+        _check(_lib.lts_set_blocking(self.h, 1 if on else 0), "lts_set_blocking")
 
     def set_profiling(self, on=True):
         _check(_lib.lts_set_profiling(self.h, 1 if on else 0), "lts_set_profiling")

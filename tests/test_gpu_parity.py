@@ -283,3 +283,34 @@ def test_full_wave_first_substeps_sampled(lt, orc, full_wave):
         for idx in (idx1, idx0):
             dk = np.abs(k_gpu[j][:, idx] - kj[:, idx]) * dtl[None, idx, None]
             assert dk.max() / np.abs(u_gpu).max() <= TOL
+
+
+@pytest.mark.parametrize("name,mk", SMALL + [
+    ("nonlinear_l3-5", lambda: W.wave_nonlinear(l_min=3, l_max=5, half=4.0, radius=1.5, width=0.2)),
+    ("uniform_l3_wave", lambda: W.uniform(3, pde=W.PDE_WAVE)),
+    ("orbit_l2-5", lambda: W.wave_orbit(l_min=2, l_max=5, band=0.3, half=2.0, omega=3.0, precision=0)),
+    ("planar_mixed", lambda: dict(W.wave_planar(l_min=2, l_max=4),
+                                  prob=dict(W.wave_planar(l_min=2, l_max=4)["prob"], precision=1)))])
+def test_blocking_is_bit_identical(lt, name, mk):
+    """Sec. 3.2.5 blocks: stepping complete sibling groups as 13^3-node blocks gives the
+    same bits as stepping every octant alone, under LTS (all substep kinds, reconcile)
+    and GTS."""
+    w = mk()
+    gt = lt.Octree(w["spec"])
+    a, b = lt.Plan(gt, w["prob"]), lt.Plan(gt, w["prob"])
+    b.set_blocking(False)
+    st = a.stats()
+    if name.startswith(("uniform", "orbit")):
+        assert st["blocked_octants"] > 0
+    if name.startswith("uniform"):
+        assert st["blocked_octants"] == st["n_octants"]
+    nsub = 2 ** (st["l_max"] - st["l_min"])
+    for p in (a, b):
+        p.set_initial(0.0)
+        p.run_substeps(nsub + 3)
+    assert np.array_equal(a.get_state(), b.get_state())
+    for j in range(st["p"]):
+        assert np.array_equal(a.get_stage(j), b.get_stage(j))
+    for p in (a, b):
+        p.gts_steps(2)
+    assert np.array_equal(a.get_state(), b.get_state())
