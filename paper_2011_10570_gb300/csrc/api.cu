@@ -54,6 +54,7 @@ struct lts_plan {
   int* d_fine = nullptr;
   int* d_hang = nullptr;
   double* d_u[2] = {nullptr, nullptr};
+  float* d_us[2] = {nullptr, nullptr};  // mixed precision: FP32 copies of d_u
   void* d_K = nullptr;                  // RK stages, stage type
   void* d_U[2] = {nullptr, nullptr};    // stage inputs of the current and the next stage, stage type
   int mixed = 0;                        // 1: FP32 stage type
@@ -149,6 +150,10 @@ lts_status sync_fields(lts_plan* P, void* vb0, void* vb1, unsigned sel, int elem
   a.tree = dev_tree(P);
   a.vb[0] = vb0;
   a.vb[1] = vb1;
+  if (P->d_us[0] && vb0 == P->d_u[0]) {  // the FP64 state: keep its FP32 copies equal
+    a.shadow[0] = P->d_us[0];
+    a.shadow[1] = vb1 == P->d_u[1] ? P->d_us[1] : P->d_us[0];
+  }
   a.elem = elem;
   a.sel_mask = sel;
   a.fstride = P->N * kNV;
@@ -230,6 +235,8 @@ ltsoct::StageArgs stage_args(const lts_plan* P, int stage, int first, int lstar,
   a.tree = dev_tree(P);
   a.u[0] = P->d_u[0];
   a.u[1] = P->d_u[1];
+  a.us[0] = P->d_us[0];
+  a.us[1] = P->d_us[1];
   a.K = P->d_K;
   a.Uin = P->d_U[stage & 1];
   a.Uout = P->d_U[(stage + 1) & 1];
@@ -396,6 +403,8 @@ lts_status gts_step(lts_plan* P) {
   ltsoct::UpdateArgs ua{};
   ua.u[0] = P->d_u[0];
   ua.u[1] = P->d_u[1];
+  ua.us[0] = P->d_us[0];
+  ua.us[1] = P->d_us[1];
   ua.K = P->d_K;
   ua.mixed = P->mixed;
   ua.fstride = P->N * kNV;
@@ -648,6 +657,10 @@ lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_
   P->d_hang = static_cast<int*>(dev_alloc(P, sizeof(int) * std::max<size_t>(P->hang.size(), 1)));
   P->d_u[0] = static_cast<double*>(dev_alloc(P, fbytes));
   P->d_u[1] = static_cast<double*>(dev_alloc(P, fbytes));
+  if (P->mixed) {
+    P->d_us[0] = static_cast<float*>(dev_alloc(P, fbytes / 2));
+    P->d_us[1] = static_cast<float*>(dev_alloc(P, fbytes / 2));
+  }
   const size_t sbytes = size_t(P->N) * kNV * P->es * P->nf;  // one stage-type field set
   P->d_K = dev_alloc(P, sbytes * P->p);
   P->d_err = static_cast<int*>(dev_alloc(P, sizeof(int) * 4));
@@ -666,7 +679,8 @@ lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_
   P->d_gcode = static_cast<unsigned short*>(dev_alloc(P, sizeof(unsigned short) * ng * ltsoct::kBT));
   if (!P->d_oct || !P->d_nbr || !P->d_fine || !P->d_hang || !P->d_u[0] || !P->d_u[1] || !P->d_K || !P->d_err ||
       !P->d_U[0] || !P->d_U[1] || !P->d_up_list || !P->d_up_box || !P->d_up_slot || !P->d_up || !P->d_padmap ||
-      !P->d_grp || !P->d_single || !P->d_gsrc || !P->d_gcode) {
+      !P->d_grp || !P->d_single || !P->d_gsrc || !P->d_gcode ||
+      (P->mixed && (!P->d_us[0] || !P->d_us[1]))) {
     release(P);
     delete P;
     return fail(LTS_ENOMEM, "lts_plan_create: device allocation failed");
@@ -753,6 +767,14 @@ lts_status lts_plan_stats(const lts_plan* P, lts_stats* out) {
   return LTS_OK;
 }
 
+// mixed precision: the FP32 copy of the (synchronised) state in buffer 0
+static lts_status refresh_shadow(lts_plan* P) {
+  if (!P->d_us[0]) return LTS_OK;
+  CK(ltsoct::launch_narrow(P->d_u[0], P->d_us[0], int64_t(P->N) * kNV * P->nf, P->stream), "narrow kernel launch");
+  P->launches++;
+  return LTS_OK;
+}
+
 lts_status lts_set_initial(lts_plan* P, double t0) {
   if (!P) return fail(LTS_EINVAL, "lts_set_initial: null plan");
   ltsoct::InitArgs a{};
@@ -773,6 +795,8 @@ lts_status lts_set_initial(lts_plan* P, double t0) {
   // a synchronised state is the unzip of its shared-node values (hanging nodes interpolated)
   lts_status st = sync_fields(P, P->d_u[0], P->d_u[0], 0u, 8);
   if (st != LTS_OK) return st;
+  st = refresh_shadow(P);
+  if (st != LTS_OK) return st;
   P->cur_mask = 0;
   P->t_macro = t0;
   P->n_sub = 0;
@@ -786,6 +810,8 @@ lts_status lts_set_state(lts_plan* P, const double* u, double t0, int on_device)
      "lts_set_state copy");
   CK(cudaMemsetAsync(P->d_K, 0, size_t(P->N) * kNV * P->es * P->nf * P->p, P->stream), "memset");
   lts_status st = sync_fields(P, P->d_u[0], P->d_u[0], 0u, 8);
+  if (st != LTS_OK) return st;
+  st = refresh_shadow(P);
   if (st != LTS_OK) return st;
   P->cur_mask = 0;
   P->t_macro = t0;
@@ -1106,6 +1132,8 @@ ltsoct::BatchInst batch_descriptor(lts_plan* P) {
     y->tree = I.st[0].tree;
     y->vb[0] = P->d_u[0];
     y->vb[1] = P->d_u[1];
+    y->shadow[0] = P->d_us[0];
+    y->shadow[1] = P->d_us[1];
     y->elem = 8;
     y->fstride = P->N * kNV;
     y->nf = P->nf;

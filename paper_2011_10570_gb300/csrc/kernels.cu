@@ -375,6 +375,65 @@ __device__ __forceinline__ void rhs_node(const R* const* Tt, int c0, const Stage
   }
 }
 
+// a node of the state as a stage input: FP64 u, or in mixed precision its FP32 copy
+template <typename R>
+__device__ __forceinline__ R state_in(const double* __restrict__ u, const float* __restrict__ us, long long o) {
+  if constexpr (sizeof(R) == sizeof(double)) {
+    return __ldg(u + o);
+  } else {
+    return __ldg(us + o);
+  }
+}
+
+// Stage epilogue of one node-field (o its index in the field arrays): the next stage's
+// input u + dt sum_j a[s+1][j] k_j, or after the last stage the new state
+// u + dt sum_j w_j k_j.  FP64: all in FP64.  Mixed: the stage input in FP32 from the
+// FP32 copy of u; the new state accumulates the FP32 increment dt sum_j w_j k_j into
+// FP64 u (and refreshes the FP32 copy).
+struct EpilogueOut {
+  double unew;
+  double uin_d;
+  float unew_s;
+  float uin_f;
+};
+
+template <typename R>
+__device__ __forceinline__ EpilogueOut stage_epilogue(const StageArgs& A, const R* K, long long kstride, long long o,
+                                                      R kvf, const double* u0, const float* us0, double dt, int s,
+                                                      int p) {
+  EpilogueOut out{0.0, 0.0, 0.0f, 0.0f};
+  if constexpr (sizeof(R) == sizeof(double)) {
+    const double kd = kvf;
+    if (s < p - 1) {
+      double acc = 0.0;
+      for (int q = 0; q < A.next.n; ++q)
+        acc = fma(A.next.w[q], A.next.j[q] == s ? kd : static_cast<double>(K[(long long)A.next.j[q] * kstride + o]),
+                  acc);
+      out.uin_d = fma(dt, acc, u0[o]);
+    } else if (A.write_update) {
+      double acc = 0.0;
+      for (int q = 0; q < p - 1; ++q) acc = fma(A.w[q], static_cast<double>(K[(long long)q * kstride + o]), acc);
+      acc = fma(A.w[p - 1], kd, acc);
+      out.unew = fma(dt, acc, u0[o]);
+    }
+  } else {
+    if (s < p - 1) {
+      float acc = 0.0f;
+      for (int q = 0; q < A.next.n; ++q)
+        acc = fmaf(float(A.next.w[q]), A.next.j[q] == s ? float(kvf) : float(K[(long long)A.next.j[q] * kstride + o]),
+                   acc);
+      out.uin_f = fmaf(float(dt), acc, us0[o]);
+    } else if (A.write_update) {
+      float acc = 0.0f;
+      for (int q = 0; q < p - 1; ++q) acc = fmaf(float(A.w[q]), float(K[(long long)q * kstride + o]), acc);
+      acc = fmaf(float(A.w[p - 1]), float(kvf), acc);
+      out.unew = u0[o] + static_cast<double>(float(dt) * acc);
+      out.unew_s = static_cast<float>(out.unew);
+    }
+  }
+  return out;
+}
+
 // node position in the stage type (FP32 positions suffice for FP32 source terms)
 template <typename R>
 __device__ __forceinline__ R node_x(double lo, double ext, int P6) {
@@ -385,6 +444,8 @@ __device__ __forceinline__ R node_x(double lo, double ext, int P6) {
   }
 }
 
+// source terms of phi_t at one node: -c sin(2 chi)/r^2 (eq. phi, 0 at r = 0) and the
+// two orbiting Gaussians centred at +-(cx, cy, 0), cx + i cy = R e^{i W t_s}
 template <typename R>
 __device__ __noinline__ R wave_source(const StageArgs& A, const int P6[3], R chi, double cx, double cy) {
   const R x = node_x<R>(A.lo, A.ext, P6[0]), y = node_x<R>(A.lo, A.ext, P6[1]), z = node_x<R>(A.lo, A.ext, P6[2]);
@@ -444,6 +505,7 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
   //    stage 0 the stage input is the state u itself.
   const R* Uin = static_cast<const R*>(A.Uin);
   const double* u0 = A.u[(A.cur_mask >> lb) & 1];
+  const float* us0 = A.us[(A.cur_mask >> lb) & 1];
   const R* up_all = static_cast<const R*>(A.up);
   {
     R v[kPer][NF];
@@ -466,7 +528,7 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
             const long long off = (long long)src * kNV + (rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1);
             if (s == 0) {
 #pragma unroll
-              for (int f = 0; f < NF; ++f) v[it][f] = static_cast<R>(__ldg(u0 + f * A.fstride + off));
+              for (int f = 0; f < NF; ++f) v[it][f] = state_in<R>(u0, us0, f * A.fstride + off);
             } else {
 #pragma unroll
               for (int f = 0; f < NF; ++f) v[it][f] = __ldg(Uin + f * A.fstride + off);
@@ -516,7 +578,7 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
   __syncthreads();
 
   // 5. right-hand side on the 7^3 interior (stage type R); stage, next stage input
-  //    and RK update (FP64)
+  //    and RK update (stage_epilogue)
   if (tid < kNV) {
     const int i = tid % 7, j = (tid / 7) % 7, k = tid / 49;
     const int c0 = (i + 3) + 13 * (j + 3) + 169 * (k + 3);
@@ -540,23 +602,17 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
     }
     const long long node = (long long)b * kNV + tid;
     R* Uout = static_cast<R*>(A.Uout);
+    const int nx = ((A.cur_mask >> lb) & 1) ^ 1;
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       const long long o = f * A.fstride + node;
       K[(long long)s * kstride + o] = kv[f];
-      const double kd = static_cast<double>(kv[f]);
+      const EpilogueOut e = stage_epilogue<R>(A, K, kstride, o, kv[f], u0, us0, lc.dt, s, p);
       if (s < p - 1) {
-        // stage input of the next stage: u + dt sum_j a[s+1][j] k_j
-        double acc = 0.0;
-        for (int q = 0; q < A.next.n; ++q)
-          acc = fma(A.next.w[q], A.next.j[q] == s ? kd : static_cast<double>(K[(long long)A.next.j[q] * kstride + o]),
-                    acc);
-        Uout[o] = static_cast<R>(fma(lc.dt, acc, u0[o]));
+        Uout[o] = sizeof(R) == sizeof(double) ? R(e.uin_d) : R(e.uin_f);
       } else if (A.write_update) {
-        double acc = 0.0;
-        for (int q = 0; q < p - 1; ++q) acc = fma(A.w[q], static_cast<double>(K[(long long)q * kstride + o]), acc);
-        acc = fma(A.w[p - 1], kd, acc);
-        A.u[((A.cur_mask >> lb) & 1) ^ 1][o] = fma(lc.dt, acc, u0[o]);
+        A.u[nx][o] = e.unew;
+        if (sizeof(R) != sizeof(double)) A.us[nx][o] = e.unew_s;
       }
     }
   }
@@ -679,6 +735,7 @@ __global__ void __launch_bounds__(kBlockThreads, (sizeof(R) == 8 ? 2 : 3))
   const unsigned short* __restrict__ gc = A.gcode + (long long)g * kBT;
   const R* Uin = static_cast<const R*>(A.Uin);
   const double* u0 = A.u[(A.cur_mask >> lb) & 1];
+  const float* us0 = A.us[(A.cur_mask >> lb) & 1];
   const R* up_all = static_cast<const R*>(A.up);
   constexpr int kB = 4;
   for (int q0 = 0; q0 < kBT; q0 += kB * kBlockThreads) {
@@ -702,7 +759,7 @@ __global__ void __launch_bounds__(kBlockThreads, (sizeof(R) == 8 ? 2 : 3))
             const long long off = (long long)src * kNV + (rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1);
             if (s == 0) {
 #pragma unroll
-              for (int f = 0; f < NF; ++f) v[it][f] = static_cast<R>(__ldg(u0 + f * A.fstride + off));
+              for (int f = 0; f < NF; ++f) v[it][f] = state_in<R>(u0, us0, f * A.fstride + off);
             } else {
 #pragma unroll
               for (int f = 0; f < NF; ++f) v[it][f] = __ldg(Uin + f * A.fstride + off);
@@ -782,35 +839,24 @@ __global__ void __launch_bounds__(kBlockThreads, (sizeof(R) == 8 ? 2 : 3))
     const int cx0 = i > 6, cx1 = i >= 6, cy0 = j > 6, cy1 = j >= 6, cz0 = k > 6, cz1 = k >= 6;
     const long long own = (long long)(b0 + cx0 + 2 * cy0 + 4 * cz0) * kNV + (i - 6 * cx0) + 7 * (j - 6 * cy0) +
                           49 * (k - 6 * cz0);
+    const int nx = ((A.cur_mask >> lb) & 1) ^ 1;
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       const long long fo = f * A.fstride;
-      const double kd = static_cast<double>(kv[f]);
-      R uout = 0;
-      double unew = 0.0;
-      if (s < p - 1) {
-        double acc = 0.0;
-        for (int q = 0; q < A.next.n; ++q)
-          acc = fma(A.next.w[q],
-                    A.next.j[q] == s ? kd : static_cast<double>(K[(long long)A.next.j[q] * kstride + fo + own]), acc);
-        uout = static_cast<R>(fma(lc.dt, acc, u0[fo + own]));
-      } else if (A.write_update) {
-        double acc = 0.0;
-        for (int q = 0; q < p - 1; ++q) acc = fma(A.w[q], static_cast<double>(K[(long long)q * kstride + fo + own]), acc);
-        acc = fma(A.w[p - 1], kd, acc);
-        unew = fma(lc.dt, acc, u0[fo + own]);
-      }
-      double* unext = A.u[((A.cur_mask >> lb) & 1) ^ 1];
+      const EpilogueOut e = stage_epilogue<R>(A, K, kstride, fo + own, kv[f], u0, us0, lc.dt, s, p);
+      const R uout = sizeof(R) == sizeof(double) ? R(e.uin_d) : R(e.uin_f);
       for (int cz = cz0; cz <= cz1; ++cz)
         for (int cy = cy0; cy <= cy1; ++cy)
           for (int cx = cx0; cx <= cx1; ++cx) {
             const long long o = fo + (long long)(b0 + cx + 2 * cy + 4 * cz) * kNV + (i - 6 * cx) + 7 * (j - 6 * cy) +
                                 49 * (k - 6 * cz);
             K[(long long)s * kstride + o] = kv[f];
-            if (s < p - 1)
+            if (s < p - 1) {
               Uout[o] = uout;
-            else if (A.write_update)
-              unext[o] = unew;
+            } else if (A.write_update) {
+              A.u[nx][o] = e.unew;
+              if (sizeof(R) != sizeof(double)) A.us[nx][o] = e.unew_s;
+            }
           }
     }
   }
@@ -1059,10 +1105,20 @@ __global__ void update_kernel(UpdateArgs A) {
     const long long inf = e % A.fstride;
     const int b = int(inf / kNV);
     const int cur = (A.cur_mask >> A.oct[b].w) & 1;
-    double acc = 0.0;
-    for (int q = 0; q < A.p - 1; ++q) acc = fma(tab.w[q], static_cast<double>(K[q * kstride + e]), acc);
-    acc = fma(tab.w[A.p - 1], static_cast<double>(K[(A.p - 1) * kstride + e]), acc);
-    A.u[cur ^ 1][e] = fma(A.dt_f, acc, A.u[cur][e]);
+    if constexpr (sizeof(R) == sizeof(double)) {
+      double acc = 0.0;
+      for (int q = 0; q < A.p - 1; ++q) acc = fma(tab.w[q], static_cast<double>(K[q * kstride + e]), acc);
+      acc = fma(tab.w[A.p - 1], static_cast<double>(K[(A.p - 1) * kstride + e]), acc);
+      A.u[cur ^ 1][e] = fma(A.dt_f, acc, A.u[cur][e]);
+    } else {
+      // as the mixed-precision stage epilogue: FP32 increment accumulated into FP64 u
+      float acc = 0.0f;
+      for (int q = 0; q < A.p - 1; ++q) acc = fmaf(float(tab.w[q]), float(K[q * kstride + e]), acc);
+      acc = fmaf(float(tab.w[A.p - 1]), float(K[(A.p - 1) * kstride + e]), acc);
+      const double un = A.u[cur][e] + static_cast<double>(float(A.dt_f) * acc);
+      A.u[cur ^ 1][e] = un;
+      A.us[cur ^ 1][e] = static_cast<float>(un);
+    }
   }
 }
 
@@ -1112,9 +1168,12 @@ __device__ void sync_zip_octant(SyncSmem& S, const SyncArgs& A, const int b) {
     if ((rx | ry | rz) & 1) continue;
     const T* vs = static_cast<const T*>(A.vb[(A.sel_mask >> so.w) & 1]);
     T* vd = static_cast<T*>(A.vb[(A.sel_mask >> me.w) & 1]);
-    for (int f = 0; f < A.nf; ++f)
-      vd[f * A.fstride + (long long)b * kNV + n] =
-          vs[f * A.fstride + (long long)src * kNV + (rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1)];
+    float* sd = A.shadow[(A.sel_mask >> me.w) & 1];
+    for (int f = 0; f < A.nf; ++f) {
+      const T v = vs[f * A.fstride + (long long)src * kNV + (rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1)];
+      vd[f * A.fstride + (long long)b * kNV + n] = v;
+      if (sd) sd[f * A.fstride + (long long)b * kNV + n] = static_cast<float>(v);
+    }
   }
 }
 
@@ -1142,9 +1201,12 @@ __device__ void sync_hanging_octant(SyncSmem& S, const SyncArgs& A, const int b)
     if (!((rx | ry | rz) & 1)) continue;
     const T* vs = static_cast<const T*>(A.vb[(A.sel_mask >> so.w) & 1]);
     T* vd = static_cast<T*>(A.vb[(A.sel_mask >> me.w) & 1]);
-    for (int f = 0; f < A.nf; ++f)
-      vd[f * A.fstride + (long long)b * kNV + n] =
-          interp_tensor<T>(vs + f * A.fstride + (long long)src * kNV, c_W, rx, ry, rz);
+    float* sd = A.shadow[(A.sel_mask >> me.w) & 1];
+    for (int f = 0; f < A.nf; ++f) {
+      const T v = interp_tensor<T>(vs + f * A.fstride + (long long)src * kNV, c_W, rx, ry, rz);
+      vd[f * A.fstride + (long long)b * kNV + n] = v;
+      if (sd) sd[f * A.fstride + (long long)b * kNV + n] = static_cast<float>(v);
+    }
   }
 }
 
@@ -1545,6 +1607,19 @@ __global__ void maps_kernel(MapArgs A) {
 __global__ void widen_kernel(const float* __restrict__ in, double* __restrict__ out, long long n) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
     out[e] = static_cast<double>(in[e]);
+}
+
+__global__ void narrow_kernel(const double* __restrict__ in, float* __restrict__ out, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    out[e] = static_cast<float>(in[e]);
+}
+
+cudaError_t launch_narrow(const double* in, float* out, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  narrow_kernel<<<(int)blocks, 256, 0, s>>>(in, out, n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_widen(const float* in, double* out, long long n, cudaStream_t s) {

@@ -63,6 +63,7 @@ struct StageArgs {
   int* err;              // device error word: bit 0 source coordinate out of range
   const void* up;        // prolonged stage inputs of coarser sources, [slot][nf][2197], stage type
   int mixed;             // 1: FP32 stages, tile and right-hand side; FP64 state and corrections
+  float* us[2];          // mixed: FP32 copies of u[2], kept equal to float(u) (stage inputs read them)
   const int* up_slot;    // slot of an octant in `up` (-1: not a coarser source)
   const unsigned* padmap;  // [N][2197]: source slot | half-node code << 8 per padded point
   const int* list;         // stage_kernel: CTA x steps list[first + x] (nullptr: octant first + x)
@@ -115,10 +116,12 @@ struct SyncArgs {
   const int* list;       // octants to process (hanging pass), or nullptr = [0, n)
   int count;
   int* err;
+  float* shadow[2];      // FP64 state in mixed precision: its FP32 copies, written with it (or nullptr)
 };
 
 struct UpdateArgs {
   double* u[2];
+  float* us[2];          // mixed: FP32 copies of u
   const void* K;         // stage type
   int mixed;
   long long fstride;
@@ -205,6 +208,7 @@ cudaError_t launch_init(const InitArgs& a, cudaStream_t s);
 cudaError_t launch_maps(const MapArgs& a, cudaStream_t s);
 cudaError_t launch_padmap(const DevTree& t, unsigned* out, int* err, cudaStream_t s);
 cudaError_t launch_widen(const float* in, double* out, long long n, cudaStream_t s);
+cudaError_t launch_narrow(const double* in, float* out, long long n, cudaStream_t s);
 
 // allocation-free padding-map export: largest octant list one call accepts
 constexpr int kStaticMapOctants = 32;

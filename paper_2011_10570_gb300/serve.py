@@ -149,6 +149,9 @@ class Server:
                 continue
             steps = [0] * self.nslots
             k = min(self.chunk, min(a[2] for a in active.values()))
+            if len(active) == 1 and load >= self.saturation:
+                # nothing can join a solve that fills the GPU: run it to its end in one go
+                k = next(iter(active.values()))[2]
             for s, a in active.items():
                 steps[s] = min(k, a[2])
             if len(active) == 1:
