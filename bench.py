@@ -29,9 +29,10 @@ sys.path.insert(0, ROOT)
 METRIC = "LTS octant-node updates/s"
 UNIT = "node-updates/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x flops/FMA x max clock
-# DRAM bytes (read + write) per node-stage of stage_kernel<2>, from the ncu capture of
-# profiles/stage_kernel_wave_l4-8.md; set to None whenever the kernel changes after it
-STAGE_DRAM_BYTES_PER_NODE_STAGE = None
+# DRAM bytes (read + write) per node-stage of stage_kernel<2, double> / <2, float>, from the
+# ncu captures of profiles/stage_kernel_wave_l4-8.md; set to None whenever the kernel changes
+STAGE_DRAM_BYTES_PER_NODE_STAGE = 114.0
+STAGE_DRAM_BYTES_PER_NODE_STAGE_MIXED = 73.7
 
 
 def measured_peaks():
@@ -143,7 +144,7 @@ def host_threads():
 def run_reference(args, w, world, rank, pg):
     if rank != 0:
         return
-    threads = host_threads()
+    threads = args.oracle_threads or host_threads()
     sample = OracleSample(w, threads)
     n = sample.n
     vals, times = [], []
@@ -279,6 +280,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lts", choices=["lts", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-threads", type=int, default=0,
+                    help="host threads of the oracle in the reference arm (default: all cores)")
     ap.add_argument("--gts", action="store_true", help="also time GTS over the same physical time")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--batch", type=int, default=0, help="batched mode: number of instances (64 for the C4 workload)")
@@ -431,17 +434,21 @@ def main():
         "clocks": clk.summary(),
         "lts_model_speedup": st["model_speedup"],
     }
+    if nsub == 2 ** L:
+        # useful work at GTS's count (every octant at dt_f) per LTS wall second
+        line["gts_equivalent_rate"] = world * args.steps * st["gts_work_per_macro"] * 343 / (ms / 1e3)
     if ks["launches"]:
         avg_ms = ks["ms"] / ks["launches"]
         flops_per_launch = ks["flops"] / ks["launches"]
         achieved = flops_per_launch / (avg_ms / 1e3) / 1e12
-        traffic = (STAGE_DRAM_BYTES_PER_NODE_STAGE * ks["node_stages"] / ks["launches"]
-                   if STAGE_DRAM_BYTES_PER_NODE_STAGE and args.precision == "fp64" else None)
+        per_ns = STAGE_DRAM_BYTES_PER_NODE_STAGE if args.precision == "fp64" else STAGE_DRAM_BYTES_PER_NODE_STAGE_MIXED
+        traffic = per_ns * ks["node_stages"] / ks["launches"] if per_ns else None
         hbm_peak = measured_peaks().get("hbm_gbs")
         if args.precision == "mixed":
             gbs = ks["bytes"] / (ks["ms"] / 1e3) / 1e9
             line["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
-                                "frac": gbs / hbm_peak if hbm_peak else None, "traffic": None,
+                                "frac": gbs / hbm_peak if hbm_peak else None, "traffic": traffic,
+                                "traffic_source": "ncu dram bytes per node-stage (levels 4..8 capture) x node-stages per launch",
                                 "kernel": "stage_kernel<2, float>", "peak_source": "measured (MEASURED_PEAKS.json)",
                                 "fp64_tflops_algorithmic": achieved, "stage_share_of_step": ks["ms"] / ms}
         else:
