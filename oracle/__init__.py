@@ -50,7 +50,7 @@ def build(force: bool = False) -> str:
 class Refine(C.Structure):
     _fields_ = [("lo", C.c_double), ("hi", C.c_double), ("l_min", C.c_int), ("l_max", C.c_int),
                 ("kind", C.c_int), ("n_centers", C.c_int), ("centers", (C.c_double * 3) * 8),
-                ("radius", C.c_double), ("band", C.c_double)]
+                ("radius", C.c_double), ("band", C.c_double), ("eps", C.c_double)]
 
 
 class Problem(C.Structure):
@@ -81,6 +81,8 @@ def lib():
             L.orc_tree_export.argtypes = [vp, i32p, i32p]
             L.orc_refine_pred.restype = C.c_int
             L.orc_refine_pred.argtypes = [C.POINTER(Refine), C.c_int32, C.c_int32, C.c_int32, C.c_int]
+            L.orc_wavelet_coeff.restype = C.c_double
+            L.orc_wavelet_coeff.argtypes = [C.POINTER(Refine), C.c_int32, C.c_int32, C.c_int32, C.c_int]
             L.orc_find_leaf.restype = i64
             L.orc_find_leaf.argtypes = [vp, i64, i64, i64]
             L.orc_o2o.argtypes = [vp, i32p]
@@ -145,6 +147,7 @@ def make_refine(spec: dict) -> Refine:
             r.centers[i][d] = c[d]
     r.radius = spec.get("radius", 0.0)
     r.band = spec.get("band", 0.0)
+    r.eps = spec.get("eps", 0.0)
     return r
 
 
@@ -378,3 +381,7 @@ def set_threads(n):
 
 def refine_pred(spec, x, y, z, level):
     return lib().orc_refine_pred(C.byref(make_refine(spec)), x, y, z, level)
+
+
+def wavelet_coeff(spec, x, y, z, level):
+    return lib().orc_wavelet_coeff(C.byref(make_refine(spec)), x, y, z, level)

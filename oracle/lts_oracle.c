@@ -118,10 +118,85 @@ static int circle_pred(const orc_refine* s, const int64_t a[3], int64_t e) {
   return dr * dr + dzd * dzd <= b * b;
 }
 
+/* kind 3, the wavelet criterion of Sec. 3.2.2: a box is split while its field fails to be
+ * interpolated from its own nodes at the nodes of its children by more than eps.  The
+ * field is a sum of Gaussian shells f(x) = sum_c exp(-(|x - c| - R)^2 / w) (R = radius,
+ * w = band; R = 0 gives Gaussian bumps).  The degree-6 Lagrange weights at the half-node
+ * positions k/2 are the exact rationals prod_{m != j} (k - 2m) / prod_{m != j} (2j - 2m),
+ * each rounded once, and every sum runs in a fixed order, so the decision is reproducible. */
+static double wavelet_field(const orc_refine* s, const double x[3]) {
+  double f = 0.0;
+  for (int c = 0; c < s->n_centers; ++c) {
+    double d2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      double t = x[a] - s->centers[c][a];
+      d2 += t * t;
+    }
+    double r = sqrt(d2) - s->radius;
+    f += exp(-(r * r) / s->band);
+  }
+  return f;
+}
+
+static void half_weights(double w[13][7]) {
+  for (int k = 0; k < 13; ++k)
+    for (int j = 0; j < 7; ++j) {
+      int64_t num = 1, den = 1;
+      for (int m = 0; m < 7; ++m) {
+        if (m == j) continue;
+        num *= (int64_t)(k - 2 * m);
+        den *= (int64_t)(2 * j - 2 * m);
+      }
+      w[k][j] = (double)num / (double)den;
+    }
+}
+
+double orc_wavelet_coeff(const orc_refine* s, int32_t x, int32_t y, int32_t z, int level) {
+  int64_t e = edge_of(level);
+  int64_t a[3] = {x, y, z};
+  double w[13][7];
+  half_weights(w);
+  /* the field at the 13^3 half-node points: lattice6 coordinate 6 a + k e / 2 */
+  double* F = (double*)malloc(13 * 13 * 13 * sizeof(double));
+  for (int kz = 0; kz < 13; ++kz)
+    for (int ky = 0; ky < 13; ++ky)
+      for (int kx = 0; kx < 13; ++kx) {
+        int64_t k3[3] = {kx, ky, kz};
+        double p[3];
+        for (int d = 0; d < 3; ++d) {
+          int64_t P = 6 * a[d] + k3[d] * (e / 2);
+          p[d] = s->lo + (s->hi - s->lo) * ((double)P / (6.0 * (double)ROOT_EDGE));
+        }
+        F[kx + 13 * ky + 169 * kz] = wavelet_field(s, p);
+      }
+  double cmax = 0.0;
+  for (int kz = 0; kz < 13; ++kz)
+    for (int ky = 0; ky < 13; ++ky)
+      for (int kx = 0; kx < 13; ++kx) {
+        if (!((kx | ky | kz) & 1)) continue;
+        /* interpolate from the nodes (even half-node indices): x, then y, then z */
+        double sz = 0.0;
+        for (int c = 0; c < 7; ++c) {
+          double sy = 0.0;
+          for (int b = 0; b < 7; ++b) {
+            double sx = 0.0;
+            for (int q = 0; q < 7; ++q) sx = sx + w[kx][q] * F[2 * q + 13 * 2 * b + 169 * 2 * c];
+            sy = sy + w[ky][b] * sx;
+          }
+          sz = sz + w[kz][c] * sy;
+        }
+        double d = fabs(F[kx + 13 * ky + 169 * kz] - sz);
+        if (d > cmax) cmax = d;
+      }
+  free(F);
+  return cmax;
+}
+
 int orc_refine_pred(const orc_refine* s, int32_t x, int32_t y, int32_t z, int level) {
   int64_t e = edge_of(level);
   int64_t a[3] = {x, y, z};
   if (s->kind == 2) return circle_pred(s, a, e);
+  if (s->kind == 3) return orc_wavelet_coeff(s, x, y, z, level) > s->eps;
   int ncent = s->kind == 1 ? 1 : s->n_centers;
   for (int c = 0; c < ncent; ++c) {
     int64_t cc[3];

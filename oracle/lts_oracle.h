@@ -31,10 +31,13 @@ typedef struct {
   double lo, hi;          /* cube domain [lo,hi]^3 */
   int l_min, l_max;       /* refinement levels */
   int kind;               /* 0: balls of `radius` around centers; 1: shell |x-c0| in [radius-band, radius+band];
-                             2: within `band` of the circle of `radius` around c0 in the plane z = c0.z */
+                             2: within `band` of the circle of `radius` around c0 in the plane z = c0.z;
+                             3: wavelet criterion (Sec. 3.2.2) on the field
+                                f(x) = sum_c exp(-(|x - c| - radius)^2 / band), tolerance eps */
   int n_centers;
   double centers[8][3];
   double radius, band;
+  double eps;
 } orc_refine;
 
 enum { ORC_PDE_ADVECTION = 0, ORC_PDE_WAVE = 1 };
@@ -58,7 +61,7 @@ typedef struct {
   int ic;
   double ic_params[160];
   double nl_c;             /* wave: phi_t += -nl_c sin(2 chi) / r^2 (eq. phi), 0 at r = 0 */
-  int orbit;               /* wave: 1 adds two Gaussian sources on a circular orbit (reading R14) */
+  int orbit;               /* wave: 1 adds two Gaussian sources on a circular orbit (reading R18) */
   double orbit_params[4];  /* orbit radius, angular speed, width w, amplitude A:
                               phi_t += A sum_{i=1,2} exp(-|x - x_i(t)|^2 / w),
                               x_1 = radius (cos wt, sin wt, 0), x_2 = -x_1 */
@@ -76,6 +79,9 @@ void orc_tree_free(orc_tree* t);
 int64_t orc_tree_size(const orc_tree* t);
 void orc_tree_export(const orc_tree* t, int32_t* xyz, int32_t* level);     /* level order */
 int orc_refine_pred(const orc_refine* spec, int32_t x, int32_t y, int32_t z, int level);
+/* kind 3: the largest wavelet coefficient of the box (max over its 13^3 half-node points
+ * with an odd coordinate of |f - I f|, I the degree-6 Lagrange interpolant from its 7^3 nodes) */
+double orc_wavelet_coeff(const orc_refine* spec, int32_t x, int32_t y, int32_t z, int level);
 
 /* ---- maps (Sec. 3.2.4 meshing, Sec. 3.3 unzip) ---- */
 /* leaf index (level order) containing lattice cell (x,y,z), -1 if outside */

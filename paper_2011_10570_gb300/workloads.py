@@ -22,7 +22,7 @@ import numpy as np
 PDE_ADVECTION, PDE_WAVE = 0, 1
 BC_EXACT, BC_RADIATIVE = 0, 1
 IC_ADV_GAUSS, IC_ADV_POLY, IC_WAVE_SHELL, IC_WAVE_PLANAR, IC_WAVE_POLY, IC_WAVE_REST = 0, 1, 2, 3, 4, 5
-REFINE_BALLS, REFINE_SHELL, REFINE_CIRCLE = 0, 1, 2
+REFINE_BALLS, REFINE_SHELL, REFINE_CIRCLE, REFINE_WAVELET = 0, 1, 2, 3
 
 
 def advection_gauss(l_min=3, l_max=5, radius=0.3, t_end=0.25, cfl=0.25, ko_sigma=0.1, rk=4, width=0.05):
@@ -85,6 +85,21 @@ def wave_orbit(l_min=3, l_max=12, band=0.042, half=10.0, radius=1.0, omega=0.5, 
                 ic=IC_WAVE_REST, ic_params=[], orbit=1, orbit_params=[radius, omega, width, amp],
                 precision=precision)
     return dict(name="wave_orbit_l%d-%d" % (l_min, l_max), spec=spec, prob=prob, t_end=t_end)
+
+
+def wavelet_spec(w, eps=1e-5):
+    """The refinement of workload `w` replaced by the wavelet criterion of Sec. 3.2.2 on its
+    initial pulse: a Gaussian bump (advection) or shell (wave) of the same centre, radius and
+    width, refined while a box's largest wavelet coefficient exceeds eps."""
+    prob, spec = w["prob"], dict(w["spec"])
+    p = prob["ic_params"]
+    if prob["ic"] == IC_ADV_GAUSS:
+        spec.update(kind=REFINE_WAVELET, centers=[(p[0], p[1], p[2])], radius=0.0, band=p[3], eps=eps)
+    elif prob["ic"] == IC_WAVE_SHELL:
+        spec.update(kind=REFINE_WAVELET, centers=[spec["centers"][0]], radius=p[0], band=p[1], eps=eps)
+    else:
+        raise ValueError("wavelet refinement is defined for Gaussian bump or shell data")
+    return dict(w, spec=spec, name=w["name"] + "_wavelet")
 
 
 def random_cubic(seed, scale=1.0):
