@@ -255,14 +255,15 @@ def run_serve(args):
     out = {"metric": "served LTS solves: p50/p99 latency and throughput", "n_gpus": 1, "dtype": "f64",
            "data": "synthetic", "rates": []}
     for rate in args.serve_rates:
-        raw = workloads.serving_requests(seed=4, n=args.serve_n, rate=rate)
+        raw = workloads.serving_requests(seed=4, n=args.serve_n, rate=rate, lmax_choices=tuple(args.serve_lmax))
         reqs = [serve.Request(r["rid"], r["arrival"], r["work"], r["t_end"]) for r in raw]
         row = {"rate_per_s": rate}
         for sat in args.serve_saturation:
             server = serve.Server(slots=args.serve_slots, chunk=args.serve_chunk, keep_results=False,
                                   saturation=sat)
             res_b, wall_b = server.serve(reqs, realtime=True)
-            row["continuous_batching_sat%g" % sat] = serve.summary(res_b, wall_b)
+            row["continuous_batching_sat%g" % sat] = dict(serve.summary(res_b, wall_b),
+                                                           phases_s={k: round(v, 4) for k, v in server.phases.items()})
             del server
         res_1, wall_1 = serve.serve_one_at_a_time(reqs, realtime=True, keep_results=False)
         octs = sorted(r.octants for r in res_1)
@@ -291,6 +292,8 @@ def main():
     ap.add_argument("--serve", action="store_true", help="serving mode: Poisson stream, continuous batching")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[0.5, 2.0])
     ap.add_argument("--serve-n", type=int, default=16)
+    ap.add_argument("--serve-lmax", type=int, nargs="+", default=[5, 6],
+                    help="finest levels the request trees draw from (5 6: about 4k to 180k octants)")
     ap.add_argument("--serve-saturation", type=float, nargs="+", default=[8192.0],
                     help="admission limit on the resident solves' mean active octants per substep")
     ap.add_argument("--serve-slots", type=int, default=16)

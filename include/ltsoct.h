@@ -58,7 +58,12 @@ typedef struct lts_plan lts_plan;
  *   kind 1: its closed box meets the shell radius-band <= |x - centers[0]| <= radius+band;
  *   kind 2: its closed box comes within `band` of the circle of `radius` around
  *           centers[0] in the plane z = centers[0].z (distance evaluated in IEEE
- *           doubles from the box's exact lattice extents, no contraction).
+ *           doubles from the box's exact lattice extents, no contraction);
+ *   kind 3: the wavelet criterion the paper uses: the largest wavelet coefficient of the
+ *           field f(x) = sum_c exp(-(|x - centers[c]| - radius)^2 / band) on the box exceeds
+ *           eps, the coefficient being the largest |f - I f| over the 13^3 half-node points
+ *           of the box that are not its nodes, I the degree-6 tensor Lagrange interpolant
+ *           from its 7^3 nodes (exact rational weights rounded once, fixed summation order).
  * Octants of level < l_min are always split.  Centers and radii are mapped to
  * lattice units as llround((c - lo)/(hi - lo) * 2^20) and floor/ceil of
  * (r/(hi - lo) * 2^20)^2; the tests are exact int64 comparisons. */
@@ -69,6 +74,7 @@ typedef struct {
   int n_centers;    /* 1..8 */
   double centers[8][3];
   double radius, band;
+  double eps;       /* kind 3 only */
 } lts_refine_spec;
 
 enum { LTS_PDE_ADVECTION = 0, LTS_PDE_WAVE = 1 };

@@ -52,12 +52,14 @@ struct Predicate {
   int64_t r2_out = 0;  // squared outer radius (floor)
   int64_t r2_in = 0;   // squared inner radius (ceil), shell only
   double ring_r = 0, ring_b = 0;  // circle: radius and band in lattice units
+  lts_refine_spec spec;           // wavelet criterion: the field and tolerance
 };
 
 Predicate make_predicate(const lts_refine_spec& s) {
   Predicate p;
   p.kind = s.kind;
-  p.n = s.kind == 0 ? s.n_centers : 1;
+  p.spec = s;
+  p.n = s.kind == 0 || s.kind == 3 ? s.n_centers : 1;
   const double scale = static_cast<double>(int64_t(1) << kDepth);
   const double ext = s.hi - s.lo;
   for (int i = 0; i < p.n; ++i)
@@ -116,10 +118,69 @@ bool ring_holds(const Predicate& p, const int64_t lo[3], int64_t edge) {
   return drho * drho + z * z <= p.ring_b * p.ring_b;
 }
 
+// Wavelet criterion (Sec. 3.2.2): the largest failure, over the half-node points of the
+// box that are not its nodes, of the degree-6 Lagrange interpolant from the box's 7^3
+// nodes to reproduce the field sum_c exp(-(|x - c| - radius)^2 / band).  Weights are the
+// exact rationals prod_{m != j} (k - 2m) / prod_{m != j} (2j - 2m), each rounded once;
+// sums run in a fixed order without contraction, so every host decides alike.
+double wavelet_coefficient(const lts_refine_spec& s, const int64_t anchor[3], int64_t edge) {
+  double w[13][7];
+  for (int k = 0; k < 13; ++k)
+    for (int j = 0; j < 7; ++j) {
+      int64_t num = 1, den = 1;
+      for (int m = 0; m < 7; ++m)
+        if (m != j) {
+          num *= int64_t(k - 2 * m);
+          den *= int64_t(2 * j - 2 * m);
+        }
+      w[k][j] = double(num) / double(den);
+    }
+  std::vector<double> F(13 * 13 * 13);
+  const double lattice6 = 6.0 * double(int64_t(1) << kDepth);
+  for (int kz = 0; kz < 13; ++kz)
+    for (int ky = 0; ky < 13; ++ky)
+      for (int kx = 0; kx < 13; ++kx) {
+        const int64_t kk[3] = {kx, ky, kz};
+        double x[3];
+        for (int d = 0; d < 3; ++d) x[d] = s.lo + (s.hi - s.lo) * (double(6 * anchor[d] + kk[d] * (edge / 2)) / lattice6);
+        double f = 0.0;
+        for (int c = 0; c < s.n_centers; ++c) {
+          double d2 = 0.0;
+          for (int d = 0; d < 3; ++d) {
+            const double t = x[d] - s.centers[c][d];
+            d2 += t * t;
+          }
+          const double r = std::sqrt(d2) - s.radius;
+          f += std::exp(-(r * r) / s.band);
+        }
+        F[kx + 13 * ky + 169 * kz] = f;
+      }
+  double worst = 0.0;
+  for (int kz = 0; kz < 13; ++kz)
+    for (int ky = 0; ky < 13; ++ky)
+      for (int kx = 0; kx < 13; ++kx) {
+        if (!((kx | ky | kz) & 1)) continue;
+        double vz = 0.0;
+        for (int c = 0; c < 7; ++c) {
+          double vy = 0.0;
+          for (int b = 0; b < 7; ++b) {
+            double vx = 0.0;
+            for (int a = 0; a < 7; ++a) vx = vx + w[kx][a] * F[2 * a + 26 * b + 338 * c];
+            vy = vy + w[ky][b] * vx;
+          }
+          vz = vz + w[kz][c] * vy;
+        }
+        const double gap = std::fabs(F[kx + 13 * ky + 169 * kz] - vz);
+        if (gap > worst) worst = gap;
+      }
+  return worst;
+}
+
 bool predicate_holds(const Predicate& p, const Oct& o) {
   const int64_t lo[3] = {o.x, o.y, o.z};
   const int64_t edge = int64_t(1) << (kDepth - o.l);
   if (p.kind == 2) return ring_holds(p, lo, edge);
+  if (p.kind == 3) return wavelet_coefficient(p.spec, lo, edge) > p.spec.eps;
   for (int i = 0; i < p.n; ++i) {
     int64_t dmin2, dmax2;
     box_distances(lo, edge, p.c[i], &dmin2, &dmax2);
@@ -148,8 +209,11 @@ inline Oct child_of(const Oct& o, int c) {
 // refinement of the refined tree.
 bool build_octree(const lts_refine_spec& spec, std::vector<Oct>* leaves, std::string* err) {
   if (!(spec.hi > spec.lo) || spec.l_min < 0 || spec.l_max < spec.l_min || spec.l_max > kMaxLevel ||
-      spec.kind < 0 || spec.kind > 2 || (spec.kind == 0 && (spec.n_centers < 1 || spec.n_centers > 8))) {
-    *err = "octree_build: invalid refinement spec (need lo < hi, 0 <= l_min <= l_max <= 18, kind 0/1/2, 1..8 centers)";
+      spec.kind < 0 || spec.kind > 3 ||
+      ((spec.kind == 0 || spec.kind == 3) && (spec.n_centers < 1 || spec.n_centers > 8)) ||
+      (spec.kind == 3 && !(spec.band > 0.0 && spec.eps > 0.0))) {
+    *err = "octree_build: invalid refinement spec (need lo < hi, 0 <= l_min <= l_max <= 18, kind 0..3, 1..8 centers; "
+           "kind 3: band > 0, eps > 0)";
     return false;
   }
   const Predicate pred = make_predicate(spec);

@@ -27,7 +27,7 @@ class LtsError(RuntimeError):
 class RefineSpec(C.Structure):
     _fields_ = [("lo", C.c_double), ("hi", C.c_double), ("l_min", C.c_int), ("l_max", C.c_int),
                 ("kind", C.c_int), ("n_centers", C.c_int), ("centers", (C.c_double * 3) * 8),
-                ("radius", C.c_double), ("band", C.c_double)]
+                ("radius", C.c_double), ("band", C.c_double), ("eps", C.c_double)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -137,6 +137,7 @@ def make_refine(spec: dict) -> RefineSpec:
             r.centers[i][d] = c[d]
     r.radius = spec.get("radius", 0.0)
     r.band = spec.get("band", 0.0)
+    r.eps = spec.get("eps", 0.0)
     return r
 
 

@@ -116,6 +116,14 @@ class Server:
         trees = {}                       # rid -> (octree, device bytes, load), built once per request
         t0 = time.perf_counter()
         now = lambda: time.perf_counter() - t0
+        # wall time of the server's phases (seconds), for the bench report
+        self.phases = collections.Counter()
+        clock = [time.perf_counter()]
+
+        def mark(phase):
+            t = time.perf_counter()
+            self.phases[phase] += t - clock[0]
+            clock[0] = t
 
         def prepare(req):
             if req.rid not in trees:
@@ -126,6 +134,7 @@ class Server:
             return trees[req.rid]
 
         while pending or active:
+            mark("idle_or_host")
             # admit while a slot is free and the budget holds
             while pending and (not realtime or pending[0].arrival <= now()) and len(active) < self.nslots:
                 req = pending[0]
@@ -143,6 +152,7 @@ class Server:
                 active[slot] = [req, plan, n, now(), est, node_updates(plan.stats(), 0, n), ld]
                 used += est
                 load += ld
+                mark("admit")
             if not active:
                 if pending:
                     time.sleep(max(0.0, min(0.01, pending[0].arrival - now())))
@@ -159,12 +169,15 @@ class Server:
                 a0[1].run_substeps(steps[s0])
             else:
                 self.batch.run(steps, graph=True)
+            mark("launch")
             # host work while the GPU runs the chunk: octrees of requests that have arrived
             for req in list(pending)[:self.nslots]:
                 if realtime and req.arrival > now():
                     break
                 prepare(req)
+            mark("prepare")
             torch.cuda.current_stream().synchronize()
+            mark("gpu_wait")
             for s in list(active):
                 a = active[s]
                 a[2] -= steps[s]

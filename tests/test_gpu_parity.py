@@ -1,6 +1,7 @@
 """GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
 
-* maps (o2o, padding sources, shared-node owners) bit-exact;
+* octrees (geometric predicates and the wavelet criterion) and maps (o2o, padding
+  sources, shared-node owners) bit-exact;
 * FP64 fields within a relative L-infinity error of 1e-12 of the oracle, for LTS
   (Alg. 2) and GTS (Alg. 1), advection and wave, exact and radiative boundaries;
 * LTS == GTS bitwise on a one-level tree (Alg. 2 reduces to Alg. 1);
@@ -56,6 +57,8 @@ SMALL = [
     ("wave_planar_l2-4", lambda: W.wave_planar(l_min=2, l_max=4)),
     ("wave_shell_l3-6", lambda: W.wave_shell(l_min=3, l_max=6, half=4.0, radius=1.5, width=0.2)),
     ("wave_shell_l2-5_rk3", lambda: W.wave_shell(l_min=2, l_max=5, half=4.0, radius=1.5, width=0.2, rk=3)),
+    # wavelet refinement (Sec. 3.2.2) of the advected pulse
+    ("adv_wavelet_l2-5", lambda: W.wavelet_spec(W.advection_gauss(l_min=2, l_max=5), eps=1e-7)),
 ]
 
 
