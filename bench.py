@@ -163,7 +163,8 @@ def run_reference(args, w, world, rank, pg):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w["name"], "octants": n, "levels": "%d..%d" % (w["spec"]["l_min"], w["spec"]["l_max"]),
                    "fields": 2, "rk": 4,
-                   "parallelism": "replicas", "l2": "state arrays (847 MB each) larger than L2"},
+                   "parallelism": "replicas",
+                   "l2": "state arrays (%d MB each) larger than L2" % round(2 * n * 343 * 8 / 1e6)},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -430,7 +431,7 @@ def main():
         "config": {"workload": w["name"], "octants": n, "levels": "%d..%d" % (st["l_min"], st["l_max"]),
                    "fields": st["nf"], "rk": 4, "substeps_per_step": nsub, "substeps_per_macro_step": 2 ** L,
                    "parallelism": "replicas",
-                   "l2": "inputs larger than L2 (state arrays %d MB each)" % (st["nf"] * n * 343 * 8 // 2 ** 20)},
+                   "l2": "inputs larger than L2 (state arrays %d MB each)" % round(st["nf"] * n * 343 * 8 / 1e6)},
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                 "d2h_bytes_per_step": state_bytes},

@@ -212,6 +212,7 @@ def serve_one_at_a_time(requests, precision=0, realtime=True, keep_results=True)
         plan.set_initial(0.0)
         n = substeps_to(plan, req.t_end)
         plan.run_substeps(n)
+        stream.synchronize()             # a request is finished when its solve has run
         state = plan.get_state() if keep_results else None
         st = plan.stats()
         results.append(Result(req.rid, req.arrival, admitted, now(), st["n_octants"], n,
