@@ -618,8 +618,9 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
   }
 }
 
+// FP64: 4 CTAs per SM (registers and the 49.5 KB tile); mixed: 5 (1,760 of 2,048 threads)
 template <int NF, typename R>
-__global__ void __launch_bounds__(kThreads, 4) stage_kernel(const __grid_constant__ StageArgs A) {
+__global__ void __launch_bounds__(kThreads, (sizeof(R) == 8 ? 4 : 5)) stage_kernel(const __grid_constant__ StageArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StageSmem<NF, R>& S = *reinterpret_cast<StageSmem<NF, R>*>(smem_raw);
   stage_octant<NF, R>(S, A, A.list ? A.list[A.first + blockIdx.x] : A.first + blockIdx.x);
@@ -635,7 +636,7 @@ __global__ void __launch_bounds__(kThreads, 4) stage_kernel(const __grid_constan
 // octant copies: the results equal those of stage_kernel bit for bit, with 2.5
 // instead of 6.4 gathered points and 0.8 instead of 1 right-hand side per node.
 // ---------------------------------------------------------------------------
-constexpr int kBlockThreads = 448;  // 14 warps: the 2197 block nodes in five passes
+constexpr int kBlockThreads = 448;  // 14 warps: the 2197 block nodes in five passes; 2 CTAs/SM in FP64, 4 in mixed
 
 template <int NF, typename R>
 struct BlockSmem {
@@ -708,7 +709,7 @@ __device__ __noinline__ void block_fill_extrapolated(BlockSmem<NF, R>& S, int4 m
 }
 
 template <int NF, typename R>
-__global__ void __launch_bounds__(kBlockThreads, (sizeof(R) == 8 ? 2 : 3))
+__global__ void __launch_bounds__(kBlockThreads, (sizeof(R) == 8 ? 2 : 4))
     block_kernel(const __grid_constant__ StageArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BlockSmem<NF, R>& S = *reinterpret_cast<BlockSmem<NF, R>*>(smem_raw);
