@@ -954,6 +954,14 @@ struct ProlongSmem {
   R W[13][7];
 };
 
+// Division by a divisor fixed per CTA: q = floor(t / d) = umulhi(t, ceil(2^32 / d)), exact
+// while t * d < 2^32 (here t < 2 * 2197 and d <= 2 * 2197).
+struct FastDiv {
+  unsigned d, m;
+  __device__ explicit FastDiv(unsigned dv) : d(dv), m(dv > 1u ? 0xffffffffu / dv + 1u : 0u) {}
+  __device__ __forceinline__ unsigned div(unsigned t) const { return d > 1u ? __umulhi(t, m) : t; }
+};
+
 // class of a half-node coordinate: 0 for [0,3], 1 for [4,8], 2 for [9,12]
 __device__ __forceinline__ int half_class(int r) { return r <= 3 ? 0 : (r >= 9 ? 2 : 1); }
 
@@ -1016,8 +1024,9 @@ __device__ void prolong_octant(ProlongSmem<NF, R>& S, const ProlongArgs& A, cons
   }
   __syncthreads();
   // pass 1 (axis a): X1[ra][jb + 7 jc]
+  const FastDiv by_a49{unsigned(na * 49)};
   for (int t = tid; t < NF * na * 49; t += blockDim.x) {
-    const int f = t / (na * 49), rem = t - f * na * 49;
+    const int f = int(by_a49.div(unsigned(t))), rem = t - f * na * 49;
     const int ri = rem / 49, bc = rem - ri * 49;
     const int ra = a0 + ri;
     if (!(ma >> half_class(ra) & 1u)) continue;
@@ -1034,9 +1043,11 @@ __device__ void prolong_octant(ProlongSmem<NF, R>& S, const ProlongArgs& A, cons
   }
   __syncthreads();
   // pass 2 (axis b): X2[ra][rb][jc]
+  const FastDiv by_ab7{unsigned(na * nb * 7)}, by_b{unsigned(nb)};
   for (int t = tid; t < NF * na * nb * 7; t += blockDim.x) {
-    const int f = t / (na * nb * 7), rem = t - f * na * nb * 7;
-    const int jc = rem % 7, rbi = (rem / 7) % nb, rai = rem / (7 * nb);
+    const int f = int(by_ab7.div(unsigned(t))), rem = t - f * na * nb * 7;
+    const int jc = rem % 7, r7 = rem / 7;
+    const int rai = int(by_b.div(unsigned(r7))), rbi = r7 - rai * nb;
     const int ra = a0 + rai, rb = b0 + rbi;
     if (!(mab >> (half_class(ra) + 3 * half_class(rb)) & 1u)) continue;
     const R* x1 = S.X1[f] + ra * 49 + 7 * jc;  // [jb]
@@ -1055,9 +1066,11 @@ __device__ void prolong_octant(ProlongSmem<NF, R>& S, const ProlongArgs& A, cons
   R* out = static_cast<R*>(A.up) + (long long)slot * NF * kNT;
   const int soa = pa == 0 ? 1 : (pa == 1 ? 13 : 169), sob = pb == 0 ? 1 : (pb == 1 ? 13 : 169);
   const int soc = pc == 0 ? 1 : (pc == 1 ? 13 : 169);
+  const FastDiv by_abc{unsigned(na * nb * nc)}, by_a{unsigned(na)}, by_ab{unsigned(na * nb)};
   for (int t = tid; t < NF * na * nb * nc; t += blockDim.x) {
-    const int f = t / (na * nb * nc), rem = t - f * na * nb * nc;
-    const int rai = rem % na, rbi = (rem / na) % nb, rci = rem / (na * nb);
+    const int f = int(by_abc.div(unsigned(t))), rem = t - f * na * nb * nc;
+    const int rci = int(by_ab.div(unsigned(rem))), rab = rem - rci * na * nb;
+    const int rbi = int(by_a.div(unsigned(rab))), rai = rab - rbi * na;
     const int ra = a0 + rai, rb = b0 + rbi, rc = c0 + rci;
     if (!(m >> (half_class(ra) + 3 * half_class(rb) + 9 * half_class(rc)) & 1u)) continue;
     const R* x2 = S.X2[f] + (ra * 13 + rb) * 7;  // [jc]
