@@ -302,6 +302,8 @@ def main():
     ap.add_argument("--workload", default="shell", choices=["shell", "nonlinear", "orbit"],
                     help="shell: linear wave, levels 4..9 (the benchmark configuration); nonlinear: the same "
                          "with the -sin(2 chi)/r^2 source; orbit: two orbiting sources, levels 3..12")
+    ap.add_argument("--orbit-lmax", type=int, default=12,
+                    help="finest level of the orbit workload (12: the configuration; smaller for profiling)")
     ap.add_argument("--substeps", type=int, default=0,
                     help="substeps per step (default: a macro step; 64 for the orbit workload)")
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
@@ -316,7 +318,7 @@ def main():
         return run_serve(args)
     from paper_2011_10570_gb300 import workloads
     if args.workload == "orbit":
-        w = workloads.wave_orbit()
+        w = workloads.wave_orbit(l_max=args.orbit_lmax)
     elif args.workload == "nonlinear":
         w = workloads.wave_nonlinear(l_max=args.lmax)
     else:
