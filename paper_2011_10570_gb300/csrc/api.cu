@@ -75,8 +75,8 @@ struct lts_plan {
   int64_t grp_off[34] = {}, single_off[34] = {};
   int* d_grp = nullptr;
   int* d_single = nullptr;
-  int* d_gsrc = nullptr;                // [G][19^3]
-  unsigned short* d_gcode = nullptr;    // [G][19^3]
+  int* d_gsrc = nullptr;                // [G][kBG]: ghost points of the block tiles
+  unsigned short* d_gcode = nullptr;    // [G][kBG]
   int64_t launches = 0;               // every kernel launched by the plan
   size_t bytes = 0;
   cudaStream_t stream = nullptr;
@@ -284,6 +284,23 @@ ltsoct::StageArgs stage_args(const lts_plan* P, int stage, int first, int lstar,
   a.orbit = P->prob.orbit;
   for (int i = 0; i < 4; ++i) a.orb[i] = P->prob.orbit_params[i];
   a.c_s = P->tab.c[stage];
+  // FP32 copies of the constants for the mixed-precision kernels
+  for (int l = 0; l < 32; ++l) {
+    a.cf.lc[l][0] = float(a.lc[l].kos);
+    a.cf.lc[l][1] = float(a.lc[l].inv12h);
+    a.cf.lc[l][2] = float(a.lc[l].inv12h2);
+    a.cf.dt[l] = float(a.lc[l].dt);
+  }
+  for (int q = 0; q < 4; ++q) {
+    a.cf.next_w[q] = float(a.next.w[q]);
+    a.cf.w[q] = float(a.w[q]);
+    a.cf.orb[q] = float(a.orb[q]);
+  }
+  for (int d = 0; d < 3; ++d) a.cf.adv[d] = float(a.adv[d]);
+  a.cf.nl_c = float(a.nl_c);
+  a.cf.lo = float(a.lo);
+  a.cf.xscale = float(a.ext / (6.0 * double(int64_t(1) << ltsoct::kDepth)));
+  a.cf.sources = (a.nl_c != 0.0 || a.orbit) ? 1 : 0;
   return a;
 }
 
@@ -415,6 +432,8 @@ lts_status gts_step(lts_plan* P) {
   ua.oct = P->d_oct;
   ua.cur_mask = P->cur_mask;
   ua.dt_f = P->dt_f;
+  ua.dt_ff = float(P->dt_f);
+  for (int q = 0; q < 4; ++q) ua.wf[q] = float(P->tab.w[q]);
   CK(ltsoct::launch_update(ua, P->stream), "update kernel launch");
   P->launches++;
   for (int l = P->lmin; l <= P->lmax; ++l) P->cur_mask ^= 1u << l;
@@ -675,8 +694,8 @@ lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_
   const size_t ng = std::max<size_t>(P->grp.size(), 1);
   P->d_grp = static_cast<int*>(dev_alloc(P, sizeof(int) * ng));
   P->d_single = static_cast<int*>(dev_alloc(P, sizeof(int) * std::max<size_t>(P->single.size(), 1)));
-  P->d_gsrc = static_cast<int*>(dev_alloc(P, sizeof(int) * ng * ltsoct::kBT));
-  P->d_gcode = static_cast<unsigned short*>(dev_alloc(P, sizeof(unsigned short) * ng * ltsoct::kBT));
+  P->d_gsrc = static_cast<int*>(dev_alloc(P, sizeof(int) * ng * ltsoct::kBG));
+  P->d_gcode = static_cast<unsigned short*>(dev_alloc(P, sizeof(unsigned short) * ng * ltsoct::kBG));
   if (!P->d_oct || !P->d_nbr || !P->d_fine || !P->d_hang || !P->d_u[0] || !P->d_u[1] || !P->d_K || !P->d_err ||
       !P->d_U[0] || !P->d_U[1] || !P->d_up_list || !P->d_up_box || !P->d_up_slot || !P->d_up || !P->d_padmap ||
       !P->d_grp || !P->d_single || !P->d_gsrc || !P->d_gcode ||

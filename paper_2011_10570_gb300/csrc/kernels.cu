@@ -41,7 +41,21 @@ __constant__ double c_E[4][4];    // cubic extrapolation weights, rows m = 1..3
 constexpr int kThreads = 352;     // 11 warps: the 343 interior nodes in one pass
 constexpr int kLatt6 = 6 << kDepth;
 
+// padded points of a sibling-group block tile (19^3) outside its 13^3 nodes, in tile order
+__device__ unsigned short g_block_ghost[kBG];
+
 cudaError_t upload_tables(const Tables* rk4, const Tables* rk3, const double W[13][7], const double E[4][4]) {
+  {
+    unsigned short ghost[kBG];
+    int n = 0;
+    for (int q = 0; q < kBT; ++q) {
+      const int i = q % kBW - 3, j = (q / kBW) % kBW - 3, k = q / (kBW * kBW) - 3;
+      if (i < 0 || i > 12 || j < 0 || j > 12 || k < 0 || k > 12) ghost[n++] = static_cast<unsigned short>(q);
+    }
+    if (n != kBG) return cudaErrorInvalidValue;
+    const cudaError_t e = cudaMemcpyToSymbol(g_block_ghost, ghost, sizeof(ghost));
+    if (e != cudaSuccess) return e;
+  }
   DevTables h[2];
   const Tables* src[2] = {rk4, rk3};
   for (int i = 0; i < 2; ++i) {
@@ -253,7 +267,7 @@ struct StageSmem {
   int src[kNT];
   unsigned short code[kNT];  // rx | ry << 4 | rz << 8 | (level diff + 1) << 12 | exterior << 15
   NbrView nv;
-  double orb[2];             // orbit centre x_1 at this octant's stage time
+  R orb[2];                  // orbit centre x_1 at this octant's stage time
 };
 
 constexpr unsigned kExterior = 1u << 15;
@@ -352,9 +366,12 @@ __device__ __forceinline__ void rhs_node(const R* const* Tt, int c0, const Stage
     const R P1 = (T[c0 - 1] + T[c0 + 1]) + (T[c0 - SY] + T[c0 + SY]) + (T[c0 - SZ] + T[c0 + SZ]);
     const R P2 = (T[c0 - 2] + T[c0 + 2]) + (T[c0 - 2 * SY] + T[c0 + 2 * SY]) + (T[c0 - 2 * SZ] + T[c0 + 2 * SZ]);
     const R P3 = (T[c0 - 3] + T[c0 + 3]) + (T[c0 - 3 * SY] + T[c0 + 3 * SY]) + (T[c0 - 3 * SZ] + T[c0 + 3 * SZ]);
-    R d1s = R(A.adv[0]) * fma(R(8), T[c0 + 1] - T[c0 - 1], T[c0 - 2] - T[c0 + 2]);
-    d1s = fma(R(A.adv[1]), fma(R(8), T[c0 + SY] - T[c0 - SY], T[c0 - 2 * SY] - T[c0 + 2 * SY]), d1s);
-    d1s = fma(R(A.adv[2]), fma(R(8), T[c0 + SZ] - T[c0 - SZ], T[c0 - 2 * SZ] - T[c0 + 2 * SZ]), d1s);
+    R av[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) av[d] = sizeof(R) == sizeof(double) ? R(A.adv[d]) : R(A.cf.adv[d]);
+    R d1s = av[0] * fma(R(8), T[c0 + 1] - T[c0 - 1], T[c0 - 2] - T[c0 + 2]);
+    d1s = fma(av[1], fma(R(8), T[c0 + SY] - T[c0 - SY], T[c0 - 2 * SY] - T[c0 + 2 * SY]), d1s);
+    d1s = fma(av[2], fma(R(8), T[c0 + SZ] - T[c0 - SZ], T[c0 - 2 * SZ] - T[c0 + 2 * SZ]), d1s);
     const R ko = fma(R(-60), uc, fma(R(15), P1, fma(R(-6), P2, P3)));
     kv[0] = fma(kos, ko, -inv12h * d1s);
   } else {
@@ -399,8 +416,8 @@ struct EpilogueOut {
 
 template <typename R>
 __device__ __forceinline__ EpilogueOut stage_epilogue(const StageArgs& A, const R* K, long long kstride, long long o,
-                                                      R kvf, const double* u0, const float* us0, double dt, int s,
-                                                      int p) {
+                                                      R kvf, const double* u0, const float* us0, double dt, float dtf,
+                                                      int s, int p) {
   EpilogueOut out{0.0, 0.0, 0.0f, 0.0f};
   if constexpr (sizeof(R) == sizeof(double)) {
     const double kd = kvf;
@@ -420,45 +437,46 @@ __device__ __forceinline__ EpilogueOut stage_epilogue(const StageArgs& A, const 
     if (s < p - 1) {
       float acc = 0.0f;
       for (int q = 0; q < A.next.n; ++q)
-        acc = fmaf(float(A.next.w[q]), A.next.j[q] == s ? float(kvf) : float(K[(long long)A.next.j[q] * kstride + o]),
+        acc = fmaf(A.cf.next_w[q], A.next.j[q] == s ? float(kvf) : float(K[(long long)A.next.j[q] * kstride + o]),
                    acc);
-      out.uin_f = fmaf(float(dt), acc, us0[o]);
+      out.uin_f = fmaf(dtf, acc, us0[o]);
     } else if (A.write_update) {
       float acc = 0.0f;
-      for (int q = 0; q < p - 1; ++q) acc = fmaf(float(A.w[q]), float(K[(long long)q * kstride + o]), acc);
-      acc = fmaf(float(A.w[p - 1]), float(kvf), acc);
-      out.unew = u0[o] + static_cast<double>(float(dt) * acc);
+      for (int q = 0; q < p - 1; ++q) acc = fmaf(A.cf.w[q], float(K[(long long)q * kstride + o]), acc);
+      acc = fmaf(A.cf.w[p - 1], float(kvf), acc);
+      out.unew = u0[o] + static_cast<double>(dtf * acc);
       out.unew_s = static_cast<float>(out.unew);
     }
   }
   return out;
 }
 
-// node position in the stage type (FP32 positions suffice for FP32 source terms)
-template <typename R>
-__device__ __forceinline__ R node_x(double lo, double ext, int P6) {
-  if constexpr (sizeof(R) == sizeof(double)) {
-    return lattice_to_x(lo, ext, P6);
-  } else {
-    return fmaf(float(ext) * (1.0f / (6.0f * float(1 << kDepth))), float(P6), float(lo));
-  }
-}
-
 // source terms of phi_t at one node: -c sin(2 chi)/r^2 (eq. phi, 0 at r = 0) and the
 // two orbiting Gaussians centred at +-(cx, cy, 0), cx + i cy = R e^{i W t_s}
 template <typename R>
-__device__ __noinline__ R wave_source(const StageArgs& A, const int P6[3], R chi, double cx, double cy) {
-  const R x = node_x<R>(A.lo, A.ext, P6[0]), y = node_x<R>(A.lo, A.ext, P6[1]), z = node_x<R>(A.lo, A.ext, P6[2]);
+__device__ __noinline__ R wave_source(const StageArgs& A, const int P6[3], R chi, R ax, R ay) {
+  constexpr bool f64 = sizeof(R) == sizeof(double);
+  R x, y, z;
+  if constexpr (f64) {
+    x = lattice_to_x(A.lo, A.ext, P6[0]);
+    y = lattice_to_x(A.lo, A.ext, P6[1]);
+    z = lattice_to_x(A.lo, A.ext, P6[2]);
+  } else {
+    x = fmaf(A.cf.xscale, float(P6[0]), A.cf.lo);
+    y = fmaf(A.cf.xscale, float(P6[1]), A.cf.lo);
+    z = fmaf(A.cf.xscale, float(P6[2]), A.cf.lo);
+  }
+  const R nl_c = f64 ? R(A.nl_c) : R(A.cf.nl_c);
   R src = 0;
-  if (A.nl_c != 0.0) {
+  if (nl_c != R(0)) {
     const R r2 = x * x + y * y + z * z;
-    if (r2 > R(0)) src = -R(A.nl_c) * sin(R(2) * chi) / r2;
+    if (r2 > R(0)) src = -nl_c * sin(R(2) * chi) / r2;
   }
   if (A.orbit) {
-    const R ax = R(cx), ay = R(cy), inv_w = R(1) / R(A.orb[2]);
+    const R inv_w = R(1) / (f64 ? R(A.orb[2]) : R(A.cf.orb[2]));
     const R d1 = (x - ax) * (x - ax) + (y - ay) * (y - ay) + z * z;
     const R d2 = (x + ax) * (x + ax) + (y + ay) * (y + ay) + z * z;
-    src += R(A.orb[3]) * (exp(-d1 * inv_w) + exp(-d2 * inv_w));
+    src += (f64 ? R(A.orb[3]) : R(A.cf.orb[3])) * (exp(-d1 * inv_w) + exp(-d2 * inv_w));
   }
   return src;
 }
@@ -482,8 +500,8 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
     // x_1 = R (cos W t_s, sin W t_s, 0) at the stage time t_s = t_b + c_s dt of this level
     double c, sn;
     sincos(A.orb[1] * fma(A.c_s, A.lc[lb].dt, A.t_b), &sn, &c);
-    S.orb[0] = A.orb[0] * c;
-    S.orb[1] = A.orb[0] * sn;
+    S.orb[0] = R(A.orb[0] * c);
+    S.orb[1] = R(A.orb[0] * sn);
   }
   __syncthreads();
 
@@ -582,14 +600,16 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
   if (tid < kNV) {
     const int i = tid % 7, j = (tid / 7) % 7, k = tid / 49;
     const int c0 = (i + 3) + 13 * (j + 3) + 169 * (k + 3);
-    const R kos = R(lc.kos), inv12h = R(lc.inv12h), inv12h2 = R(lc.inv12h2);
+    const R kos = sizeof(R) == sizeof(double) ? R(lc.kos) : R(A.cf.lc[lb][0]);
+    const R inv12h = sizeof(R) == sizeof(double) ? R(lc.inv12h) : R(A.cf.lc[lb][1]);
+    const R inv12h2 = sizeof(R) == sizeof(double) ? R(lc.inv12h2) : R(A.cf.lc[lb][2]);
     R kv[NF];
     const R* Tt[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) Tt[f] = S.T[f];
     rhs_node<NF, R, 13, 169>(Tt, c0, A, kos, inv12h, inv12h2, kv);
     if (A.pde != LTS_PDE_ADVECTION) {
-      if (A.nl_c != 0.0 || A.orbit) {
+      if (A.cf.sources) {
         const int P6[3] = {6 * me.x + i * eb, 6 * me.y + j * eb, 6 * me.z + k * eb};
         kv[NF - 1] += wave_source<R>(A, P6, Tt[0][c0], S.orb[0], S.orb[1]);
       }
@@ -607,7 +627,7 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
     for (int f = 0; f < NF; ++f) {
       const long long o = f * A.fstride + node;
       K[(long long)s * kstride + o] = kv[f];
-      const EpilogueOut e = stage_epilogue<R>(A, K, kstride, o, kv[f], u0, us0, lc.dt, s, p);
+      const EpilogueOut e = stage_epilogue<R>(A, K, kstride, o, kv[f], u0, us0, lc.dt, A.cf.dt[lb], s, p);
       if (s < p - 1) {
         Uout[o] = sizeof(R) == sizeof(double) ? R(e.uin_d) : R(e.uin_f);
       } else if (A.write_update) {
@@ -642,7 +662,7 @@ template <int NF, typename R>
 struct BlockSmem {
   R T[NF][kBT];
   StageTerms om[4];
-  double orb[2];
+  R orb[2];
 };
 
 // exact boundary data at the exterior points of the block tile (as fill_exact)
@@ -727,31 +747,66 @@ __global__ void __launch_bounds__(kBlockThreads, (sizeof(R) == 8 ? 2 : 4))
   if (tid == 0 && A.orbit) {
     double c, sn;
     sincos(A.orb[1] * fma(A.c_s, A.lc[lb].dt, A.t_b), &sn, &c);
-    S.orb[0] = A.orb[0] * c;
-    S.orb[1] = A.orb[0] * sn;
+    S.orb[0] = R(A.orb[0] * c);
+    S.orb[1] = R(A.orb[0] * sn);
   }
 
-  // 1. gathers (as stage_kernel step 2), batched for memory parallelism
-  const int* __restrict__ gs = A.gsrc + (long long)g * kBT;
-  const unsigned short* __restrict__ gc = A.gcode + (long long)g * kBT;
+  // 1a. the block's own 13^3 nodes: the stage inputs of the 8 children (a node shared by
+  //     siblings is read from the lowest of them; their copies are equal)
+  const int* __restrict__ gs = A.gsrc + (long long)g * kBG;
+  const unsigned short* __restrict__ gc = A.gcode + (long long)g * kBG;
   const R* Uin = static_cast<const R*>(A.Uin);
   const double* u0 = A.u[(A.cur_mask >> lb) & 1];
   const float* us0 = A.us[(A.cur_mask >> lb) & 1];
   const R* up_all = static_cast<const R*>(A.up);
+  {
+    constexpr int kA = (13 * 13 * 13 + kBlockThreads - 1) / kBlockThreads;
+    R v[kA][NF];
+#pragma unroll
+    for (int it = 0; it < kA; ++it) {
+      const int n = tid + it * kBlockThreads;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) v[it][f] = 0;
+      if (n < 13 * 13 * 13) {
+        const int i = n % 13, j = (n / 13) % 13, k = n / 169;
+        const int cx = i > 6, cy = j > 6, cz = k > 6;
+        const long long off = (long long)(b0 + cx + 2 * cy + 4 * cz) * kNV + (i - 6 * cx) + 7 * (j - 6 * cy) +
+                              49 * (k - 6 * cz);
+        if (s == 0) {
+#pragma unroll
+          for (int f = 0; f < NF; ++f) v[it][f] = state_in<R>(u0, us0, f * A.fstride + off);
+        } else {
+#pragma unroll
+          for (int f = 0; f < NF; ++f) v[it][f] = __ldg(Uin + f * A.fstride + off);
+        }
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < kA; ++it) {
+      const int n = tid + it * kBlockThreads;
+      if (n < 13 * 13 * 13) {
+        const int i = n % 13, j = (n / 13) % 13, k = n / 169;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) S.T[f][(i + 3) + kBW * (j + 3) + kBW * kBW * (k + 3)] = v[it][f];
+      }
+    }
+  }
+
+  // 1b. ghost points (as stage_kernel step 2), batched for memory parallelism
   constexpr int kB = 4;
-  for (int q0 = 0; q0 < kBT; q0 += kB * kBlockThreads) {
+  for (int q0 = 0; q0 < kBG; q0 += kB * kBlockThreads) {
     R v[kB][NF];
 #pragma unroll
     for (int it = 0; it < kB; ++it) {
-      const int q = q0 + tid + it * kBlockThreads;
+      const int gi = q0 + tid + it * kBlockThreads;
 #pragma unroll
       for (int f = 0; f < NF; ++f) v[it][f] = 0;
-      if (q < kBT) {
-        const unsigned code = __ldg(gc + q);
+      if (gi < kBG) {
+        const unsigned code = __ldg(gc + gi);
         if (!(code & kExterior)) {
           const int rx = code & 15, ry = (code >> 4) & 15, rz = (code >> 8) & 15;
           const int rel_code = (code >> 12) & 3;  // 0 coarser, 1 same, 2 finer
-          const int src = __ldg(gs + q);
+          const int src = __ldg(gs + gi);
           if (rel_code == 0) {
             const R* up = up_all + (long long)__ldg(A.up_slot + src) * NF * kNT + rx + 13 * ry + 169 * rz;
 #pragma unroll
@@ -771,8 +826,9 @@ __global__ void __launch_bounds__(kBlockThreads, (sizeof(R) == 8 ? 2 : 4))
     }
 #pragma unroll
     for (int it = 0; it < kB; ++it) {
-      const int q = q0 + tid + it * kBlockThreads;
-      if (q < kBT) {
+      const int gi = q0 + tid + it * kBlockThreads;
+      if (gi < kBG) {
+        const int q = g_block_ghost[gi];
 #pragma unroll
         for (int f = 0; f < NF; ++f) S.T[f][q] = v[it][f];
       }
@@ -782,13 +838,14 @@ __global__ void __launch_bounds__(kBlockThreads, (sizeof(R) == 8 ? 2 : 4))
 
   // 2. finer sources with the coarse<-fine correction of eq. fc_1 (FP64)
   if (!A.gts) {
-    for (int q = tid; q < kBT; q += blockDim.x) {
-      const unsigned code = __ldg(gc + q);
+    for (int gi = tid; gi < kBG; gi += blockDim.x) {
+      const unsigned code = __ldg(gc + gi);
       if ((code & kExterior) || ((code >> 12) & 3) != 2) continue;
       const int rx = code & 15, ry = (code >> 4) & 15, rz = (code >> 8) & 15;
       const int ls = lb + 1;
       const double* ub = A.u[(A.cur_mask >> ls) & 1];
-      const long long off = (long long)__ldg(gs + q) * kNV + (rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1);
+      const long long off = (long long)__ldg(gs + gi) * kNV + (rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1);
+      const int q = g_block_ghost[gi];
 #pragma unroll
       for (int f = 0; f < NF; ++f)
         S.T[f][q] = static_cast<R>(corrected_value<R>(ub + f * A.fstride + off, K + f * A.fstride + off, kstride,
@@ -813,7 +870,9 @@ __global__ void __launch_bounds__(kBlockThreads, (sizeof(R) == 8 ? 2 : 4))
 
   // 4. right-hand side at the 13^3 block nodes; stage, next stage input and RK update
   //    (FP64) written to every octant copy of the node
-  const R kos = R(lc.kos), inv12h = R(lc.inv12h), inv12h2 = R(lc.inv12h2);
+  const R kos = sizeof(R) == sizeof(double) ? R(lc.kos) : R(A.cf.lc[lb][0]);
+  const R inv12h = sizeof(R) == sizeof(double) ? R(lc.inv12h) : R(A.cf.lc[lb][1]);
+  const R inv12h2 = sizeof(R) == sizeof(double) ? R(lc.inv12h2) : R(A.cf.lc[lb][2]);
   const R* Tt[NF];
 #pragma unroll
   for (int f = 0; f < NF; ++f) Tt[f] = S.T[f];
@@ -824,7 +883,7 @@ __global__ void __launch_bounds__(kBlockThreads, (sizeof(R) == 8 ? 2 : 4))
     R kv[NF];
     rhs_node<NF, R, kBW, kBW * kBW>(Tt, c0, A, kos, inv12h, inv12h2, kv);
     if (A.pde != LTS_PDE_ADVECTION) {
-      if (A.nl_c != 0.0 || A.orbit) {
+      if (A.cf.sources) {
         const int P6[3] = {6 * me.x + i * eb, 6 * me.y + j * eb, 6 * me.z + k * eb};
         kv[NF - 1] += wave_source<R>(A, P6, Tt[0][c0], S.orb[0], S.orb[1]);
       }
@@ -844,7 +903,7 @@ __global__ void __launch_bounds__(kBlockThreads, (sizeof(R) == 8 ? 2 : 4))
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       const long long fo = f * A.fstride;
-      const EpilogueOut e = stage_epilogue<R>(A, K, kstride, fo + own, kv[f], u0, us0, lc.dt, s, p);
+      const EpilogueOut e = stage_epilogue<R>(A, K, kstride, fo + own, kv[f], u0, us0, lc.dt, A.cf.dt[lb], s, p);
       const R uout = sizeof(R) == sizeof(double) ? R(e.uin_d) : R(e.uin_f);
       for (int cz = cz0; cz <= cz1; ++cz)
         for (int cy = cy0; cy <= cy1; ++cy)
@@ -882,16 +941,16 @@ cudaError_t launch_block(const StageArgs& a, int count, cudaStream_t s) {
   return a.mixed ? launch_block_t<2, float>(a, count, s) : launch_block_t<2, double>(a, count, s);
 }
 
-// Padding of every sibling group's block tile: the point p in [-3, 15]^3 (child node
+// Padding of the ghost points of every sibling group's block tile: a point p in [-3, 15]^3 (child node
 // units from the parent's anchor) lies in the padded tile of child c (c_a = 1 iff
 // p_a > 6) at local coordinate p - 6 c in [-3, 9]; its source and code are that
 // child's padding-map entry, with the slot resolved to the leaf.
 __global__ void __launch_bounds__(256) groupmap_kernel(const DevTree T, const int* __restrict__ grp, int count,
                                                        const unsigned* __restrict__ padmap, int* __restrict__ gsrc,
                                                        unsigned short* __restrict__ gcode) {
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)count * kBT;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)count * kBG;
        e += (long long)gridDim.x * blockDim.x) {
-    const int g = int(e / kBT), q = int(e - (long long)g * kBT);
+    const int g = int(e / kBG), q = g_block_ghost[e - (long long)g * kBG];
     const int px = q % kBW - 3, py = (q / kBW) % kBW - 3, pz = q / (kBW * kBW) - 3;
     const int cx = px > 6, cy = py > 6, cz = pz > 6;
     const int c = grp[g] + cx + 2 * cy + 4 * cz;
@@ -1127,9 +1186,9 @@ __global__ void update_kernel(UpdateArgs A) {
     } else {
       // as the mixed-precision stage epilogue: FP32 increment accumulated into FP64 u
       float acc = 0.0f;
-      for (int q = 0; q < A.p - 1; ++q) acc = fmaf(float(tab.w[q]), float(K[q * kstride + e]), acc);
-      acc = fmaf(float(tab.w[A.p - 1]), float(K[(A.p - 1) * kstride + e]), acc);
-      const double un = A.u[cur][e] + static_cast<double>(float(A.dt_f) * acc);
+      for (int q = 0; q < A.p - 1; ++q) acc = fmaf(A.wf[q], float(K[q * kstride + e]), acc);
+      acc = fmaf(A.wf[A.p - 1], float(K[(A.p - 1) * kstride + e]), acc);
+      const double un = A.u[cur][e] + static_cast<double>(A.dt_ff * acc);
       A.u[cur ^ 1][e] = un;
       A.us[cur ^ 1][e] = static_cast<float>(un);
     }

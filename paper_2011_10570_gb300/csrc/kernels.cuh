@@ -37,6 +37,20 @@ struct StageTerms {
   double w[4];
 };
 
+// FP32 copies of the per-stage constants, used by the mixed-precision kernels so that
+// no node converts an FP64 constant (conversions share GB300's small FP64 pipe)
+struct StageConstF {
+  float lc[32][3];       // per level: kos, inv12h, inv12h2
+  float dt[32];          // per level: dt
+  float next_w[4];       // weights of the next stage input (StageArgs::next)
+  float w[4];            // RK weights
+  float adv[3];
+  float nl_c;
+  float orb[4];          // orbit radius, angular speed, width, amplitude
+  float lo, xscale;      // x = lo + xscale * (lattice6 coordinate)
+  int sources;           // 1: the wave equation has source terms
+};
+
 struct StageArgs {
   DevTree tree;
   double* u[2];          // double-buffered state [nf][N][343]; level l uses u[(cur_mask >> l) & 1]
@@ -70,13 +84,14 @@ struct StageArgs {
   // block kernel (Sec. 3.2.5 octree-to-block decomposition): CTA x steps the complete
   // sibling group grp[first + x] (8 consecutive octants) as one 13^3-node block
   const int* grp;
-  const int* gsrc;               // [G][19^3] source octant of every padded block point (-1: exterior)
-  const unsigned short* gcode;   // [G][19^3] its half-node code (as in the padding map)
+  const int* gsrc;               // [G][kBG] source octant of every ghost point of a block tile (-1: exterior)
+  const unsigned short* gcode;   // [G][kBG] its half-node code (as in the padding map)
   // wave source terms (eq. phi and the orbiting Gaussians); c_s is this stage's node
   double nl_c;
   int orbit;
   double orb[4];         // radius, angular speed, width, amplitude
   double c_s;
+  StageConstF cf;
 };
 
 // Prolongation of the stage inputs of coarser sources (Fig. unzip, coarse -> fine)
@@ -130,6 +145,8 @@ struct UpdateArgs {
   const int4* oct;
   unsigned cur_mask;
   double dt_f;
+  float dt_ff;           // dt_f and the RK weights in FP32 (mixed precision)
+  float wf[4];
 };
 
 struct InitArgs {
@@ -200,6 +217,7 @@ cudaError_t launch_groupmap(const DevTree& t, const int* grp, int count, const u
                             unsigned short* gcode, cudaStream_t s);
 constexpr int kBW = 19;               // padded block width of a sibling group: 13 nodes + 2 x 3
 constexpr int kBT = kBW * kBW * kBW;  // 6859 padded points
+constexpr int kBG = kBT - 13 * 13 * 13;  // 4662 of them outside the block's 13^3 nodes
 cudaError_t launch_prolong(const ProlongArgs& a, cudaStream_t s);
 cudaError_t launch_sync_zip(const SyncArgs& a, cudaStream_t s);
 cudaError_t launch_sync_hanging(const SyncArgs& a, cudaStream_t s);
