@@ -6,7 +6,7 @@
  * benchmark's CPU-baseline leg; never by the library.  Plain loops in FP64,
  * compiled with -ffp-contract=off.  Every function names the passage of the
  * paper it restates; where the paper is silent or garbled the reading taken
- * is stated beside the code (readings R1..R16 of the design notes).
+ * is stated beside the code as a reading.
  *
  * Parity status: every function here is pinned by a CPU test against
  * brute force, closed forms, exact polynomial reproduction or values the
@@ -70,9 +70,10 @@ uint64_t orc_morton(uint32_t x, uint32_t y, uint32_t z) {
 
 static int64_t edge_of(int l) { return ROOT_EDGE >> l; }
 
-/* Refinement predicate (reading R1: the paper's wavelet criterion, Sec. 3.2.2,
- * is replaced by an integer geometric predicate).  Centers and radii are
- * mapped to lattice units; squared distances are compared in int64. */
+/* Refinement predicates.  Kinds 0-2 are integer geometric predicates (a reading: they
+ * reproduce the configurations' trees exactly; centers and radii are mapped to lattice
+ * units and squared distances compared in int64); kind 3 is the paper's wavelet
+ * criterion of Sec. 3.2.2. */
 static int64_t to_lattice(double v, double lo, double hi) {
   return llround((v - lo) / (hi - lo) * (double)ROOT_EDGE);
 }
@@ -491,7 +492,7 @@ static int64_t floor_div(int64_t a, int64_t b) {
   return q;
 }
 
-/* Reading R5/R6: the value at a lattice point P comes from the coarsest leaf
+/* Reading of Sec. 3.3 / Fig. dg_to_cg: the value at a lattice point P comes from the coarsest leaf
  * whose closed box contains P, ties to the smallest Morton key; with octants in
  * (level, Morton) order this is the smallest level-order index.  The leaves
  * containing P are the leaves covering the (up to 8) unit cells touching P. */
@@ -568,7 +569,7 @@ void orc_node_map(const orc_tree* t, int64_t b, int32_t* src, int32_t* r) {
 
 /* ------------------------------------------------------------------------ */
 /* Operators: Lagrange interpolation (coarse -> fine padding, Sec. 3.3) and   */
-/* centred finite differences with Kreiss-Oliger dissipation (reading R3).     */
+/* centred finite differences with Kreiss-Oliger dissipation (a reading of the paper).     */
 /* ------------------------------------------------------------------------ */
 
 /* 1-D Lagrange basis of degree 6 on nodes 0..6 evaluated at r/2, r = 0..12 */
@@ -656,7 +657,7 @@ void orc_tile_ops(const double* T, double h, double* d1, double* d2, double* ko6
 
 /* ------------------------------------------------------------------------ */
 /* Runge-Kutta tableaus (eq. rk_schemes) and the LTS stage corrections       */
-/* (eqs. rk_crrection, fc_1, fc_2; reading R9)                                */
+/* (eqs. rk_crrection, fc_1, fc_2; a reading of the paper)                                */
 /* ------------------------------------------------------------------------ */
 
 int orc_tableau(int rk, double a[4][4], double w[4], double c[4]) {
@@ -721,7 +722,7 @@ static double factorial(int n) {
   return f;
 }
 
-/* Stage correction in units dt_N = 1 (reading R9):
+/* Stage correction in units dt_N = 1 (a reading of the paper):
  *   Y = P_N^-1 C^-1 K_N                       (eq. rk_crrection inverted)
  *   u_N(t_N + theta) = u_N + sum_m theta^(m+1)/(m+1)! Y_m
  *   K~ = C P_rho B_theta Y                    (eqs. fc_1 / fc_2)
@@ -986,7 +987,7 @@ orc_solver* orc_solver_create(const orc_tree* t, const orc_refine* spec, const o
   orc_omega(pr->rk, 0.0, 0.5, s->omega[2]);
   orc_omega(pr->rk, 0.5, 0.5, s->omega[3]);
   orc_stage_taylor(pr->rk, s->gamma);
-  /* reading R12: dt_f = CFL * h at the finest level, h = node spacing */
+  /* reading: dt_f = CFL * h at the finest level, h = node spacing */
   double h_f = (spec->hi - spec->lo) / (6.0 * (double)((int64_t)1 << lmax));
   s->dt_f = pr->cfl * h_f;
   s->N = t->n;
@@ -1114,7 +1115,7 @@ static void extrap_weights(int m, double E[4]) {
   }
 }
 
-/* Radiative boundary (reading R11): exterior ghosts by cubic extrapolation
+/* Radiative boundary (a reading of the paper): exterior ghosts by cubic extrapolation
  * along the outward normal, axis by axis (x, then y, then z). */
 static void fill_extrapolated(const orc_solver* s, const oct_t* o, double* T) {
   int64_t e = edge_of(o->l);
@@ -1296,7 +1297,7 @@ static void compute_stage(orc_solver* s, int64_t b, int st, int gts, int lstar, 
           kout[n] = phi + kos * koc;
           kout[NV + n] = lap + kos * kop;
           if (s->pr.nl_c != 0.0 || s->pr.orbit) {
-            /* eq. phi: -c sin(2 chi)/r^2 (taken as 0 at r = 0); reading R14: orbiting
+            /* eq. phi: -c sin(2 chi)/r^2 (taken as 0 at r = 0); reading: orbiting
              * Gaussian sources at the stage time t_b + c_s dt_b */
             int64_t P[3] = {6 * (int64_t)o->x + ii * e, 6 * (int64_t)o->y + jj * e, 6 * (int64_t)o->z + kk * e};
             double x[3];
@@ -1322,7 +1323,7 @@ static void compute_stage(orc_solver* s, int64_t b, int st, int gts, int lstar, 
             for (int a = 0; a < 3; ++a)
               if (P[a] == 0 || P[a] == L6) on_bnd = 1;
             if (on_bnd) {
-              /* reading R11: df/dt = -(x^i/r) d_i f - k_f (f - f0)/r, f0 = 0, k = 1 (chi), 2 (phi) */
+              /* reading: df/dt = -(x^i/r) d_i f - k_f (f - f0)/r, f0 = 0, k = 1 (chi), 2 (phi) */
               double x[3];
               pos6_to_x(s, P, x);
               double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
@@ -1348,7 +1349,7 @@ static void compute_stage(orc_solver* s, int64_t b, int st, int gts, int lstar, 
 /* Time stepping (Alg. 1, Alg. 2, Fig. blk_loop)                              */
 /* ------------------------------------------------------------------------ */
 
-/* Fig. blk_loop / reading R8: in substep n of a macro step, level l steps iff
+/* Fig. blk_loop / reading: in substep n of a macro step, level l steps iff
  * n is a multiple of 2^(l_max - l); the active levels are l >= l*(n). */
 int orc_active_level(int l_min, int l_max, int64_t n) {
   for (int l = l_min; l <= l_max; ++l)
@@ -1370,7 +1371,7 @@ void orc_set_initial(orc_solver* s, double t0) {
       orc_exact_derivs(&s->pr, x, t0, d);
       double v0 = d[0][0], v1 = d[1][0];
       if (s->pr.ic == ORC_IC_WAVE_SHELL) {
-        /* reading R13: chi_0 = F(r) (1 + amp sum eps sin(kscale k.x + theta)), phi_0 = 0
+        /* reading: chi_0 = F(r) (1 + amp sum eps sin(kscale k.x + theta)), phi_0 = 0
          * (the shell data at rest, not the time derivative of the closed form) */
         const double* p = s->pr.ic_params;
         double amp = p[2], ks = p[4], pert = 0.0;
@@ -1428,7 +1429,7 @@ void orc_exact_state(const orc_solver* s, double t, double* u) {
 }
 
 /* DG -> shared nodes -> DG (zip then unzip, Sec. 3.3 / Fig. dg_to_cg; readings
- * R5-R7), in place.  Zip: every non-hanging node takes the value of its owner,
+ * the padding and ownership readings), in place.  Zip: every non-hanging node takes the value of its owner,
  * the coarsest leaf having it as a node (ties to the smallest Morton key).
  * Unzip: a hanging node is interpolated from the shared-node representation of
  * the coarser leaf containing it, whose own nodes are final once the coarser
@@ -1559,7 +1560,7 @@ void orc_gts_steps(orc_solver* s, int64_t nsteps) {
   }
 }
 
-/* eqs. w_nuts, w_uts, invS (reading R15: alpha_l counts octants at level l_max - l) */
+/* eqs. w_nuts, w_uts, invS (reading: alpha_l counts octants at level l_max - l) */
 double orc_work_model(const orc_tree* t, double* w_lts, double* w_gts) {
   int lmin = 99, lmax = -1;
   for (int l = 0; l <= ORC_D; ++l)

@@ -61,7 +61,7 @@ typedef struct {
   int ic;
   double ic_params[160];
   double nl_c;             /* wave: phi_t += -nl_c sin(2 chi) / r^2 (eq. phi), 0 at r = 0 */
-  int orbit;               /* wave: 1 adds two Gaussian sources on a circular orbit (reading R18) */
+  int orbit;               /* wave: 1 adds two Gaussian sources on a circular orbit (a reading of the paper) */
   double orbit_params[4];  /* orbit radius, angular speed, width w, amplitude A:
                               phi_t += A sum_{i=1,2} exp(-|x - x_i(t)|^2 / w),
                               x_1 = radius (cos wt, sin wt, 0), x_2 = -x_1 */

@@ -273,7 +273,7 @@ struct StageSmem {
 constexpr unsigned kExterior = 1u << 15;
 constexpr int kPer = (kNT + kThreads - 1) / kThreads;  // padded points per thread
 
-// exact boundary data (reading R10): RK stage values of the closed-form solution
+// exact boundary data (a reading of the paper): RK stage values of the closed-form solution
 template <int NF, typename R>
 __device__ __noinline__ void fill_exact(StageSmem<NF, R>& S, const StageArgs& A, int4 me, int eb, double dtb) {
   for (int q = threadIdx.x; q < kNT; q += blockDim.x) {
@@ -295,7 +295,7 @@ __device__ __noinline__ void fill_exact(StageSmem<NF, R>& S, const StageArgs& A,
   }
 }
 
-// radiative boundary (reading R11): cubic extrapolation along the outward normal, x then y then z
+// radiative boundary (a reading of the paper): cubic extrapolation along the outward normal, x then y then z
 template <int NF, typename R>
 __device__ __noinline__ void fill_extrapolated(StageSmem<NF, R>& S, int4 me, int eb) {
   const int anchor[3] = {me.x, me.y, me.z};

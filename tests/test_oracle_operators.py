@@ -1,7 +1,7 @@
 """Pins for the oracle's spatial operators, RK tableaus, LTS stage corrections and
 closed forms.
 
-* finite differences: exact on polynomials up to the stencil order (Sec. 3.3, reading R3);
+* finite differences: exact on polynomials up to the stencil order (Sec. 3.3, a reading of the paper);
 * Kreiss-Oliger: the 6th difference annihilates degree <= 5 and gives 6! h^6 on x^6;
 * Lagrange 7 -> 13 interpolation (coarse-to-fine padding, Fig. unzip) reproduces degree <= 6;
 * omega tables (eqs. rk_crrection, fc_1, fc_2): a ghost built from a source's RK
