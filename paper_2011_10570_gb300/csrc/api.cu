@@ -68,6 +68,14 @@ struct lts_plan {
   void* d_up = nullptr;                 // prolonged stage inputs [slot][nf][2197], stage type
   int* d_err = nullptr;
   unsigned* d_padmap = nullptr;  // [N][2197] padding map, built once by padmap_kernel
+  // compact shared-node maps (zip: copied nodes; hanging: interpolated nodes, per level)
+  int* d_zl_dst = nullptr;
+  int* d_zl_src = nullptr;
+  int64_t n_zip = 0;
+  int* d_hl_dst = nullptr;
+  int* d_hl_src = nullptr;
+  unsigned short* d_hl_code = nullptr;
+  int64_t hl_off[34] = {};
   // octree-to-block decomposition (Sec. 3.2.5): complete sibling groups are stepped as
   // one 13^3-node block by block_kernel, the other octants one by one by stage_kernel
   bool blocking = true;
@@ -145,6 +153,96 @@ ltsoct::DevTree dev_tree(const lts_plan* P) {
 int cur_of(const lts_plan* P, int l) { return (P->cur_mask >> l) & 1; }
 
 // in-place shared-node sync of the arrays vb (level l uses vb[(sel >> l) & 1])
+// Compact shared-node maps: nodemap_kernel resolves the owner of every boundary node of
+// every octant once (dense, temporary); the copies and the hanging nodes are gathered
+// into lists on the host, the hanging ones per level and within a level ordered by the
+// number of odd half-node coordinates (uniform work across a warp).
+lts_status build_node_maps(lts_plan* P) {
+  const size_t nb = size_t(P->N) * ltsoct::kBN, nh = std::max<size_t>(P->hang.size(), 1) * ltsoct::kBN;
+  std::vector<int32_t> hang_pos(P->N, -1);
+  for (size_t h = 0; h < P->hang.size(); ++h) hang_pos[P->hang[h]] = int32_t(h);
+  int *t_pos = nullptr, *t_zip = nullptr, *t_hsrc = nullptr;
+  unsigned short* t_hcode = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(t_pos);
+    cudaFree(t_zip);
+    cudaFree(t_hsrc);
+    cudaFree(t_hcode);
+  };
+  cudaError_t e = cudaMalloc(&t_pos, sizeof(int) * P->N);
+  if (e == cudaSuccess) e = cudaMalloc(&t_zip, sizeof(int) * nb);
+  if (e == cudaSuccess) e = cudaMalloc(&t_hsrc, sizeof(int) * nh);
+  if (e == cudaSuccess) e = cudaMalloc(&t_hcode, sizeof(unsigned short) * nh);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(t_pos, hang_pos.data(), sizeof(int) * P->N, cudaMemcpyHostToDevice, P->stream);
+  if (e == cudaSuccess) e = ltsoct::launch_nodemap(dev_tree(P), t_pos, t_zip, t_hsrc, t_hcode, P->d_err, P->stream);
+  std::vector<int32_t> zip(nb), hsrc(nh);
+  std::vector<uint16_t> hcode(nh);
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(zip.data(), t_zip, sizeof(int) * nb, cudaMemcpyDeviceToHost, P->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hsrc.data(), t_hsrc, sizeof(int) * nh, cudaMemcpyDeviceToHost, P->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hcode.data(), t_hcode, sizeof(uint16_t) * nh, cudaMemcpyDeviceToHost, P->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, P->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(e, "lts_plan_create: node maps");
+  if (herr) return fail(LTS_EINTERNAL, "lts_plan_create: node maps: a shared node without a valid owner");
+  P->launches++;
+  // boundary nodes in node order (the table of the kernels)
+  int bnode[ltsoct::kBN], nbn = 0;
+  for (int q = 0; q < kNV; ++q) {
+    const int i = q % 7, j = (q / 7) % 7, k = q / 49;
+    if (i == 0 || i == 6 || j == 0 || j == 6 || k == 0 || k == 6) bnode[nbn++] = q;
+  }
+  std::vector<int32_t> zl_dst, zl_src;
+  for (int64_t b = 0; b < P->N; ++b)
+    for (int k = 0; k < ltsoct::kBN; ++k) {
+      const int32_t src = zip[size_t(b) * ltsoct::kBN + k];
+      if (src < 0) continue;
+      zl_dst.push_back(int32_t(b * kNV + bnode[k]));
+      zl_src.push_back(src);
+    }
+  // hanging nodes: per level, then by the number of odd coordinates
+  std::vector<int32_t> hl_dst, hl_src;
+  std::vector<uint16_t> hl_code;
+  for (int l = 0; l <= 32; ++l) {
+    P->hl_off[l] = int64_t(hl_dst.size());
+    for (int odd = 1; odd <= 3; ++odd)
+      for (int64_t h = P->hang_off[l]; h < P->hang_off[l + 1]; ++h)
+        for (int k = 0; k < ltsoct::kBN; ++k) {
+          const size_t x = size_t(h) * ltsoct::kBN + k;
+          if (hsrc[x] < 0) continue;
+          const unsigned c = hcode[x];
+          const int n_odd = int(c & 1u) + int((c >> 4) & 1u) + int((c >> 8) & 1u);
+          if (n_odd != odd) continue;
+          hl_dst.push_back(int32_t(int64_t(P->hang[h]) * kNV + bnode[k]));
+          hl_src.push_back(hsrc[x]);
+          hl_code.push_back(uint16_t(c));
+        }
+  }
+  P->hl_off[33] = int64_t(hl_dst.size());
+  P->n_zip = int64_t(zl_dst.size());
+  P->d_zl_dst = static_cast<int*>(dev_alloc(P, sizeof(int) * std::max<size_t>(zl_dst.size(), 1)));
+  P->d_zl_src = static_cast<int*>(dev_alloc(P, sizeof(int) * std::max<size_t>(zl_src.size(), 1)));
+  P->d_hl_dst = static_cast<int*>(dev_alloc(P, sizeof(int) * std::max<size_t>(hl_dst.size(), 1)));
+  P->d_hl_src = static_cast<int*>(dev_alloc(P, sizeof(int) * std::max<size_t>(hl_src.size(), 1)));
+  P->d_hl_code = static_cast<unsigned short*>(dev_alloc(P, sizeof(uint16_t) * std::max<size_t>(hl_code.size(), 1)));
+  if (!P->d_zl_dst || !P->d_zl_src || !P->d_hl_dst || !P->d_hl_src || !P->d_hl_code)
+    return fail(LTS_ENOMEM, "lts_plan_create: node map allocation failed");
+  if (!zl_dst.empty()) {
+    CK(cudaMemcpyAsync(P->d_zl_dst, zl_dst.data(), sizeof(int) * zl_dst.size(), cudaMemcpyHostToDevice, P->stream), "copy");
+    CK(cudaMemcpyAsync(P->d_zl_src, zl_src.data(), sizeof(int) * zl_src.size(), cudaMemcpyHostToDevice, P->stream), "copy");
+  }
+  if (!hl_dst.empty()) {
+    CK(cudaMemcpyAsync(P->d_hl_dst, hl_dst.data(), sizeof(int) * hl_dst.size(), cudaMemcpyHostToDevice, P->stream), "copy");
+    CK(cudaMemcpyAsync(P->d_hl_src, hl_src.data(), sizeof(int) * hl_src.size(), cudaMemcpyHostToDevice, P->stream), "copy");
+    CK(cudaMemcpyAsync(P->d_hl_code, hl_code.data(), sizeof(uint16_t) * hl_code.size(), cudaMemcpyHostToDevice,
+                       P->stream), "copy");
+  }
+  CK(cudaStreamSynchronize(P->stream), "cudaStreamSynchronize");
+  return LTS_OK;
+}
+
 lts_status sync_fields(lts_plan* P, void* vb0, void* vb1, unsigned sel, int elem) {
   ltsoct::SyncArgs a{};
   a.tree = dev_tree(P);
@@ -161,6 +259,10 @@ lts_status sync_fields(lts_plan* P, void* vb0, void* vb1, unsigned sel, int elem
   a.list = nullptr;
   a.count = int(P->N);
   a.err = P->d_err;
+  a.map_dst = P->d_zl_dst;
+  a.map_src = P->d_zl_src;
+  a.map_first = 0;
+  a.map_count = P->n_zip;
   CK(ltsoct::launch_sync_zip(a, P->stream), "sync (zip)");
   P->launches++;
   for (int l = P->lmin + 1; l <= P->lmax; ++l) {
@@ -168,6 +270,11 @@ lts_status sync_fields(lts_plan* P, void* vb0, void* vb1, unsigned sel, int elem
     if (!n) continue;
     a.list = P->d_hang + P->hang_off[l];
     a.count = int(n);
+    a.map_dst = P->d_hl_dst;
+    a.map_src = P->d_hl_src;
+    a.map_code = P->d_hl_code;
+    a.map_first = P->hl_off[l];
+    a.map_count = P->hl_off[l + 1] - P->hl_off[l];
     CK(ltsoct::launch_sync_hanging(a, P->stream), "sync (hanging nodes)");
     P->launches++;
   }
@@ -740,6 +847,7 @@ lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_
                                                   P->d_gcode, P->stream)
                         : cudaErrorInvalidValue;
   if (e17 == cudaSuccess && !P->grp.empty()) P->launches++;
+
   int herr = 0;
   cudaError_t e14 = cudaMemcpyAsync(&herr, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, P->stream);
   cudaError_t e8 = cudaStreamSynchronize(P->stream);
@@ -753,6 +861,12 @@ lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_
     release(P);
     delete P;
     return fail(LTS_EINTERNAL, "lts_plan_create: padding map: a source lay outside its octant (unbalanced tree)");
+  }
+  st = build_node_maps(P);
+  if (st != LTS_OK) {
+    release(P);
+    delete P;
+    return st;
   }
   *out = P;
   return LTS_OK;

@@ -44,7 +44,21 @@ constexpr int kLatt6 = 6 << kDepth;
 // padded points of a sibling-group block tile (19^3) outside its 13^3 nodes, in tile order
 __device__ unsigned short g_block_ghost[kBG];
 
+// boundary nodes of an octant (a coordinate 0 or 6), in node order
+__device__ unsigned short g_bnode[kBN];
+
 cudaError_t upload_tables(const Tables* rk4, const Tables* rk3, const double W[13][7], const double E[4][4]) {
+  {
+    unsigned short bn[kBN];
+    int n = 0;
+    for (int q = 0; q < kNV; ++q) {
+      const int i = q % 7, j = (q / 7) % 7, k = q / 49;
+      if (i == 0 || i == 6 || j == 0 || j == 6 || k == 0 || k == 6) bn[n++] = static_cast<unsigned short>(q);
+    }
+    if (n != kBN) return cudaErrorInvalidValue;
+    const cudaError_t e = cudaMemcpyToSymbol(g_bnode, bn, sizeof(bn));
+    if (e != cudaSuccess) return e;
+  }
   {
     unsigned short ghost[kBG];
     int n = 0;
@@ -1212,6 +1226,7 @@ cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 struct SyncSmem {
   NbrView nv;
+  double W[13][7];  // interpolation weights (divergent row indices: shared, not constant memory)
 };
 
 __device__ __forceinline__ bool is_boundary_node(int i, int j, int k) {
@@ -1255,6 +1270,7 @@ __device__ void sync_zip_octant(SyncSmem& S, const SyncArgs& A, const int b) {
 template <typename T>
 __device__ void sync_hanging_octant(SyncSmem& S, const SyncArgs& A, const int b) {
   load_neighbours(A.tree, b, S.nv);
+  for (int q = threadIdx.x; q < 91; q += blockDim.x) S.W[q / 7][q % 7] = c_W[q / 7][q % 7];
   __syncthreads();
   const int4 me = A.tree.oct[b];
   const int eb = 1 << (kDepth - me.w);
@@ -1276,7 +1292,7 @@ __device__ void sync_hanging_octant(SyncSmem& S, const SyncArgs& A, const int b)
     T* vd = static_cast<T*>(A.vb[(A.sel_mask >> me.w) & 1]);
     float* sd = A.shadow[(A.sel_mask >> me.w) & 1];
     for (int f = 0; f < A.nf; ++f) {
-      const T v = interp_tensor<T>(vs + f * A.fstride + (long long)src * kNV, c_W, rx, ry, rz);
+      const T v = interp_tensor<T>(vs + f * A.fstride + (long long)src * kNV, S.W, rx, ry, rz);
       vd[f * A.fstride + (long long)b * kNV + n] = v;
       if (sd) sd[f * A.fstride + (long long)b * kNV + n] = static_cast<float>(v);
     }
@@ -1295,21 +1311,137 @@ __global__ void __launch_bounds__(128) sync_hanging_kernel(const __grid_constant
   sync_hanging_octant<T>(S, A, A.list[blockIdx.x]);
 }
 
+// The same two passes from the plan's compact node maps (built once from nodemap_kernel's
+// output): one thread per copied or hanging node, so every lane of a warp does work.
+template <typename T>
+__global__ void __launch_bounds__(256) zipmap_kernel(const __grid_constant__ SyncArgs A) {
+  for (long long e = A.map_first + blockIdx.x * (long long)blockDim.x + threadIdx.x; e < A.map_first + A.map_count;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int dst = __ldg(A.map_dst + e), src = __ldg(A.map_src + e);
+    const int ld = A.tree.oct[dst / kNV].w, ls = A.tree.oct[src / kNV].w;
+    const T* vs = static_cast<const T*>(A.vb[(A.sel_mask >> ls) & 1]);
+    T* vd = static_cast<T*>(A.vb[(A.sel_mask >> ld) & 1]);
+    float* sd = A.shadow[(A.sel_mask >> ld) & 1];
+    for (int f = 0; f < A.nf; ++f) {
+      const T v = vs[f * A.fstride + src];
+      vd[f * A.fstride + dst] = v;
+      if (sd) sd[f * A.fstride + dst] = static_cast<float>(v);
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) hangmap_kernel(const __grid_constant__ SyncArgs A) {
+  // the interpolation weights in shared memory: threads of a warp index different rows,
+  // which the constant cache would serialise
+  __shared__ double W[13][7];
+  for (int q = threadIdx.x; q < 91; q += blockDim.x) W[q / 7][q % 7] = c_W[q / 7][q % 7];
+  __syncthreads();
+  for (long long e = A.map_first + blockIdx.x * (long long)blockDim.x + threadIdx.x; e < A.map_first + A.map_count;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int dst = __ldg(A.map_dst + e), src = __ldg(A.map_src + e);
+    const unsigned code = __ldg(A.map_code + e);
+    const int ld = A.tree.oct[dst / kNV].w, ls = A.tree.oct[src].w;
+    const T* vs = static_cast<const T*>(A.vb[(A.sel_mask >> ls) & 1]);
+    T* vd = static_cast<T*>(A.vb[(A.sel_mask >> ld) & 1]);
+    float* sd = A.shadow[(A.sel_mask >> ld) & 1];
+    const int rx = code & 15, ry = (code >> 4) & 15, rz = (code >> 8) & 15;
+    for (int f = 0; f < A.nf; ++f) {
+      const T v = interp_tensor<T>(vs + f * A.fstride + (long long)src * kNV, W, rx, ry, rz);
+      vd[f * A.fstride + dst] = v;
+      if (sd) sd[f * A.fstride + dst] = static_cast<float>(v);
+    }
+  }
+}
+
+static int map_blocks(long long work) {
+  long long b = (work + 255) / 256;
+  return int(b < 152 * 16 ? (b > 0 ? b : 1) : 152 * 16);
+}
+
 cudaError_t launch_sync_zip(const SyncArgs& a, cudaStream_t s) {
   if (a.count <= 0) return cudaSuccess;
-  if (a.elem == 4)
+  if (a.map_dst) {
+    if (a.map_count <= 0) return cudaSuccess;
+    const int nb = map_blocks(a.map_count);
+    if (a.elem == 4)
+      zipmap_kernel<float><<<nb, 256, 0, s>>>(a);
+    else
+      zipmap_kernel<double><<<nb, 256, 0, s>>>(a);
+  } else if (a.elem == 4) {
     sync_zip_kernel<float><<<a.count, 128, 0, s>>>(a);
-  else
+  } else {
     sync_zip_kernel<double><<<a.count, 128, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_sync_hanging(const SyncArgs& a, cudaStream_t s) {
   if (a.count <= 0) return cudaSuccess;
-  if (a.elem == 4)
+  if (a.map_dst) {
+    if (a.map_count <= 0) return cudaSuccess;
+    const int nb = map_blocks(a.map_count);
+    if (a.elem == 4)
+      hangmap_kernel<float><<<nb, 256, 0, s>>>(a);
+    else
+      hangmap_kernel<double><<<nb, 256, 0, s>>>(a);
+  } else if (a.elem == 4) {
     sync_hanging_kernel<float><<<a.count, 128, 0, s>>>(a);
-  else
+  } else {
     sync_hanging_kernel<double><<<a.count, 128, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+// Node maps of a plan: for every boundary node of every octant, its owner (R6 rule, the
+// octant itself included) and whether it is a copy (all half-node coordinates even) or
+// a hanging node to interpolate.
+__global__ void __launch_bounds__(128) nodemap_kernel(const DevTree T, const int* __restrict__ hang_pos,
+                                                       int* __restrict__ zipmap, int* __restrict__ hang_src,
+                                                       unsigned short* __restrict__ hang_code, int* err) {
+  __shared__ NbrView nv;
+  for (int b = blockIdx.x; b < T.n; b += gridDim.x) {
+    __syncthreads();
+    load_neighbours(T, b, nv);
+    __syncthreads();
+    const int4 me = T.oct[b];
+    const int eb = 1 << (kDepth - me.w);
+    const int hp = hang_pos[b];
+    for (int k = threadIdx.x; k < kBN; k += blockDim.x) {
+      const int n = g_bnode[k];
+      const int i = n % 7, j = (n / 7) % 7, kk = n / 49;
+      int zsrc = -1, hsrc = -1;
+      unsigned code = 0;
+      const int src = resolve_source(nv, i, j, kk, b, true);
+      if (src != b && src >= 0) {
+        const int4 so = T.oct[src];
+        const int rx = half_node(6 * me.x + i * eb, so.x, so.w);
+        const int ry = half_node(6 * me.y + j * eb, so.y, so.w);
+        const int rz = half_node(6 * me.z + kk * eb, so.z, so.w);
+        if (unsigned(rx) > 12u || unsigned(ry) > 12u || unsigned(rz) > 12u) {
+          atomicOr(err, 1);
+        } else if (!((rx | ry | rz) & 1)) {
+          zsrc = src * kNV + (rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1);
+        } else if (hp >= 0) {
+          hsrc = src;
+          code = unsigned(rx) | unsigned(ry) << 4 | unsigned(rz) << 8;
+        } else {
+          atomicOr(err, 2);  // a hanging node outside the hanging list: never on a balanced tree
+        }
+      }
+      zipmap[(long long)b * kBN + k] = zsrc;
+      if (hp >= 0) {
+        hang_src[(long long)hp * kBN + k] = hsrc;
+        hang_code[(long long)hp * kBN + k] = static_cast<unsigned short>(code);
+      }
+    }
+  }
+}
+
+cudaError_t launch_nodemap(const DevTree& t, const int* hang_pos, int* zipmap, int* hang_src,
+                           unsigned short* hang_code, int* err, cudaStream_t s) {
+  if (t.n <= 0) return cudaSuccess;
+  nodemap_kernel<<<t.n < 152 * 8 ? t.n : 152 * 8, 128, 0, s>>>(t, hang_pos, zipmap, hang_src, hang_code, err);
   return cudaGetLastError();
 }
 

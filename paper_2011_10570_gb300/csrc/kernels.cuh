@@ -132,7 +132,15 @@ struct SyncArgs {
   int count;
   int* err;
   float* shadow[2];      // FP64 state in mixed precision: its FP32 copies, written with it (or nullptr)
+  // the plan's compact node maps (map_dst nullptr: sources resolved per node); a launch
+  // handles entries [map_first, map_first + map_count)
+  const int* map_dst;              // destination element (octant * 343 + node)
+  const int* map_src;              // zip: source element; hanging: source octant
+  const unsigned short* map_code;  // hanging: half-node code rx | ry << 4 | rz << 8
+  long long map_first, map_count;
 };
+
+constexpr int kBN = 343 - 125;     // boundary nodes of an octant (on its faces)
 
 struct UpdateArgs {
   double* u[2];
@@ -221,6 +229,8 @@ constexpr int kBG = kBT - 13 * 13 * 13;  // 4662 of them outside the block's 13^
 cudaError_t launch_prolong(const ProlongArgs& a, cudaStream_t s);
 cudaError_t launch_sync_zip(const SyncArgs& a, cudaStream_t s);
 cudaError_t launch_sync_hanging(const SyncArgs& a, cudaStream_t s);
+cudaError_t launch_nodemap(const DevTree& t, const int* hang_pos, int* zipmap, int* hang_src,
+                           unsigned short* hang_code, int* err, cudaStream_t s);
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
 cudaError_t launch_init(const InitArgs& a, cudaStream_t s);
 cudaError_t launch_maps(const MapArgs& a, cudaStream_t s);
