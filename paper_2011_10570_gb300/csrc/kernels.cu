@@ -416,6 +416,30 @@ __device__ __forceinline__ R state_in(const double* __restrict__ u, const float*
   }
 }
 
+// the state as stage input array: FP64 u, or in mixed precision its FP32 copy
+template <typename R>
+__device__ __forceinline__ const R* state_array(const double* u, const float* us) {
+  if constexpr (sizeof(R) == sizeof(double)) {
+    return u;
+  } else {
+    return us;
+  }
+}
+
+// asynchronous global -> shared copy of one element (cp.async, sm_80+): the gathers of a
+// tile go out without staging in registers, and the FP64 correction pass overlaps them
+template <typename R>
+__device__ __forceinline__ void async_copy(R* smem, const R* gmem) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  if constexpr (sizeof(R) == 8) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+  }
+}
+
+__device__ __forceinline__ void async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Stage epilogue of one node-field (o its index in the field arrays): the next stage's
 // input u + dt sum_j a[s+1][j] k_j, or after the last stage the new state
 // u + dt sum_j w_j k_j.  FP64: all in FP64.  Mixed: the stage input in FP32 from the
@@ -539,44 +563,27 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
   const double* u0 = A.u[(A.cur_mask >> lb) & 1];
   const float* us0 = A.us[(A.cur_mask >> lb) & 1];
   const R* up_all = static_cast<const R*>(A.up);
-  {
-    R v[kPer][NF];
+  const R* st_in = s == 0 ? state_array<R>(u0, us0) : Uin;
+  for (int q = tid; q < kNT; q += kThreads) {
+    const unsigned code = S.code[q];
+    if (code & kExterior) {
 #pragma unroll
-    for (int it = 0; it < kPer; ++it) {
-      const int q = tid + it * kThreads;
-#pragma unroll
-      for (int f = 0; f < NF; ++f) v[it][f] = 0;
-      if (q < kNT) {
-        const unsigned code = S.code[q];
-        if (!(code & kExterior)) {
-          const int rx = code & 15, ry = (code >> 4) & 15, rz = (code >> 8) & 15;
-          const int rel_code = (code >> 12) & 3;  // 0 coarser, 1 same, 2 finer
-          const int src = S.src[q];
-          if (rel_code == 0) {
-            const R* up = up_all + (long long)__ldg(A.up_slot + src) * NF * kNT + rx + 13 * ry + 169 * rz;
-#pragma unroll
-            for (int f = 0; f < NF; ++f) v[it][f] = __ldg(up + f * kNT);
-          } else if (rel_code == 1 || A.gts) {
-            const long long off = (long long)src * kNV + (rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1);
-            if (s == 0) {
-#pragma unroll
-              for (int f = 0; f < NF; ++f) v[it][f] = state_in<R>(u0, us0, f * A.fstride + off);
-            } else {
-#pragma unroll
-              for (int f = 0; f < NF; ++f) v[it][f] = __ldg(Uin + f * A.fstride + off);
-            }
-          }
-        }
-      }
+      for (int f = 0; f < NF; ++f) S.T[f][q] = 0;  // the boundary fill overwrites it
+      continue;
     }
+    const int rx = code & 15, ry = (code >> 4) & 15, rz = (code >> 8) & 15;
+    const int rel_code = (code >> 12) & 3;  // 0 coarser, 1 same, 2 finer
+    const int src = S.src[q];
+    if (rel_code == 0) {
+      const R* up = up_all + (long long)__ldg(A.up_slot + src) * NF * kNT + rx + 13 * ry + 169 * rz;
 #pragma unroll
-    for (int it = 0; it < kPer; ++it) {
-      const int q = tid + it * kThreads;
-      if (q < kNT) {
+      for (int f = 0; f < NF; ++f) async_copy(&S.T[f][q], up + f * kNT);
+    } else if (rel_code == 1 || A.gts) {
+      const long long off = (long long)src * kNV + (rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1);
 #pragma unroll
-        for (int f = 0; f < NF; ++f) S.T[f][q] = v[it][f];
-      }
+      for (int f = 0; f < NF; ++f) async_copy(&S.T[f][q], st_in + f * A.fstride + off);
     }
+    // finer sources under LTS: the correction pass below writes them
   }
 
   // 3. finer sources (injection) with the coarse<-fine correction of eq. fc_1 (FP64)
@@ -594,6 +601,7 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
                                                       S.om[1], A.lc[ls].dt));
     }
   }
+  async_wait_all();
   __syncthreads();
 
   // 4. physical boundary
@@ -764,6 +772,7 @@ __global__ void __launch_bounds__(kBlockThreads, (sizeof(R) == 8 ? 2 : 4))
     S.orb[0] = R(A.orb[0] * c);
     S.orb[1] = R(A.orb[0] * sn);
   }
+  __syncthreads();  // S.om is read by the correction pass
 
   // 1a. the block's own 13^3 nodes: the stage inputs of the 8 children (a node shared by
   //     siblings is read from the lowest of them; their copies are equal)
@@ -773,82 +782,39 @@ __global__ void __launch_bounds__(kBlockThreads, (sizeof(R) == 8 ? 2 : 4))
   const double* u0 = A.u[(A.cur_mask >> lb) & 1];
   const float* us0 = A.us[(A.cur_mask >> lb) & 1];
   const R* up_all = static_cast<const R*>(A.up);
-  {
-    constexpr int kA = (13 * 13 * 13 + kBlockThreads - 1) / kBlockThreads;
-    R v[kA][NF];
+  const R* st_in = s == 0 ? state_array<R>(u0, us0) : Uin;
+  for (int n = tid; n < 13 * 13 * 13; n += kBlockThreads) {
+    const int i = n % 13, j = (n / 13) % 13, k = n / 169;
+    const int cx = i > 6, cy = j > 6, cz = k > 6;
+    const long long off = (long long)(b0 + cx + 2 * cy + 4 * cz) * kNV + (i - 6 * cx) + 7 * (j - 6 * cy) +
+                          49 * (k - 6 * cz);
+    const int q = (i + 3) + kBW * (j + 3) + kBW * kBW * (k + 3);
 #pragma unroll
-    for (int it = 0; it < kA; ++it) {
-      const int n = tid + it * kBlockThreads;
-#pragma unroll
-      for (int f = 0; f < NF; ++f) v[it][f] = 0;
-      if (n < 13 * 13 * 13) {
-        const int i = n % 13, j = (n / 13) % 13, k = n / 169;
-        const int cx = i > 6, cy = j > 6, cz = k > 6;
-        const long long off = (long long)(b0 + cx + 2 * cy + 4 * cz) * kNV + (i - 6 * cx) + 7 * (j - 6 * cy) +
-                              49 * (k - 6 * cz);
-        if (s == 0) {
-#pragma unroll
-          for (int f = 0; f < NF; ++f) v[it][f] = state_in<R>(u0, us0, f * A.fstride + off);
-        } else {
-#pragma unroll
-          for (int f = 0; f < NF; ++f) v[it][f] = __ldg(Uin + f * A.fstride + off);
-        }
-      }
-    }
-#pragma unroll
-    for (int it = 0; it < kA; ++it) {
-      const int n = tid + it * kBlockThreads;
-      if (n < 13 * 13 * 13) {
-        const int i = n % 13, j = (n / 13) % 13, k = n / 169;
-#pragma unroll
-        for (int f = 0; f < NF; ++f) S.T[f][(i + 3) + kBW * (j + 3) + kBW * kBW * (k + 3)] = v[it][f];
-      }
-    }
+    for (int f = 0; f < NF; ++f) async_copy(&S.T[f][q], st_in + f * A.fstride + off);
   }
 
-  // 1b. ghost points (as stage_kernel step 2), batched for memory parallelism
-  constexpr int kB = 4;
-  for (int q0 = 0; q0 < kBG; q0 += kB * kBlockThreads) {
-    R v[kB][NF];
+  // 1b. ghost points (as stage_kernel step 2)
+  for (int gi = tid; gi < kBG; gi += kBlockThreads) {
+    const int q = g_block_ghost[gi];
+    const unsigned code = __ldg(gc + gi);
+    if (code & kExterior) {
 #pragma unroll
-    for (int it = 0; it < kB; ++it) {
-      const int gi = q0 + tid + it * kBlockThreads;
-#pragma unroll
-      for (int f = 0; f < NF; ++f) v[it][f] = 0;
-      if (gi < kBG) {
-        const unsigned code = __ldg(gc + gi);
-        if (!(code & kExterior)) {
-          const int rx = code & 15, ry = (code >> 4) & 15, rz = (code >> 8) & 15;
-          const int rel_code = (code >> 12) & 3;  // 0 coarser, 1 same, 2 finer
-          const int src = __ldg(gs + gi);
-          if (rel_code == 0) {
-            const R* up = up_all + (long long)__ldg(A.up_slot + src) * NF * kNT + rx + 13 * ry + 169 * rz;
-#pragma unroll
-            for (int f = 0; f < NF; ++f) v[it][f] = __ldg(up + f * kNT);
-          } else if (rel_code == 1 || A.gts) {
-            const long long off = (long long)src * kNV + (rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1);
-            if (s == 0) {
-#pragma unroll
-              for (int f = 0; f < NF; ++f) v[it][f] = state_in<R>(u0, us0, f * A.fstride + off);
-            } else {
-#pragma unroll
-              for (int f = 0; f < NF; ++f) v[it][f] = __ldg(Uin + f * A.fstride + off);
-            }
-          }
-        }
-      }
+      for (int f = 0; f < NF; ++f) S.T[f][q] = 0;  // the boundary fill overwrites it
+      continue;
     }
+    const int rx = code & 15, ry = (code >> 4) & 15, rz = (code >> 8) & 15;
+    const int rel_code = (code >> 12) & 3;  // 0 coarser, 1 same, 2 finer
+    const int src = __ldg(gs + gi);
+    if (rel_code == 0) {
+      const R* up = up_all + (long long)__ldg(A.up_slot + src) * NF * kNT + rx + 13 * ry + 169 * rz;
 #pragma unroll
-    for (int it = 0; it < kB; ++it) {
-      const int gi = q0 + tid + it * kBlockThreads;
-      if (gi < kBG) {
-        const int q = g_block_ghost[gi];
+      for (int f = 0; f < NF; ++f) async_copy(&S.T[f][q], up + f * kNT);
+    } else if (rel_code == 1 || A.gts) {
+      const long long off = (long long)src * kNV + (rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1);
 #pragma unroll
-        for (int f = 0; f < NF; ++f) S.T[f][q] = v[it][f];
-      }
+      for (int f = 0; f < NF; ++f) async_copy(&S.T[f][q], st_in + f * A.fstride + off);
     }
   }
-  __syncthreads();
 
   // 2. finer sources with the coarse<-fine correction of eq. fc_1 (FP64)
   if (!A.gts) {
@@ -866,6 +832,7 @@ __global__ void __launch_bounds__(kBlockThreads, (sizeof(R) == 8 ? 2 : 4))
                                                       S.om[1], A.lc[ls].dt));
     }
   }
+  async_wait_all();
   __syncthreads();
 
   // 3. physical boundary
