@@ -278,7 +278,7 @@ template <int NF, typename R>
 struct StageSmem {
   R T[NF][kNT];              // padded tiles
   StageTerms om[4];          // correction terms of this stage per relation
-  int src[kNT];
+  unsigned char slot[kNT];   // source slot in the neighbour view (kSlotNone: exterior)
   unsigned short code[kNT];  // rx | ry << 4 | rz << 8 | (level diff + 1) << 12 | exterior << 15
   NbrView nv;
   R orb[2];                  // orbit centre x_1 at this octant's stage time
@@ -549,7 +549,7 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
     const unsigned* __restrict__ pm = A.padmap + (long long)b * kNT;
     for (int q = tid; q < kNT; q += blockDim.x) {
       const unsigned e = __ldg(pm + q);
-      S.src[q] = slot_leaf(S.nv, e & 255u, b);
+      S.slot[q] = static_cast<unsigned char>(e & 255u);
       S.code[q] = static_cast<unsigned short>(e >> 8);
     }
   }
@@ -573,7 +573,7 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
     }
     const int rx = code & 15, ry = (code >> 4) & 15, rz = (code >> 8) & 15;
     const int rel_code = (code >> 12) & 3;  // 0 coarser, 1 same, 2 finer
-    const int src = S.src[q];
+    const int src = slot_leaf(S.nv, S.slot[q], b);
     if (rel_code == 0) {
       const R* up = up_all + (long long)__ldg(A.up_slot + src) * NF * kNT + rx + 13 * ry + 169 * rz;
 #pragma unroll
@@ -594,7 +594,7 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
       const int rx = code & 15, ry = (code >> 4) & 15, rz = (code >> 8) & 15;
       const int ls = lb + 1;
       const double* ub = A.u[(A.cur_mask >> ls) & 1];
-      const long long off = (long long)S.src[q] * kNV + (rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1);
+      const long long off = (long long)slot_leaf(S.nv, S.slot[q], b) * kNV + (rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1);
 #pragma unroll
       for (int f = 0; f < NF; ++f)
         S.T[f][q] = static_cast<R>(corrected_value<R>(ub + f * A.fstride + off, K + f * A.fstride + off, kstride,
@@ -660,9 +660,9 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
   }
 }
 
-// FP64: 4 CTAs per SM (registers and the 49.5 KB tile); mixed: 5 (1,760 of 2,048 threads)
+// 5 CTAs per SM (1,760 of 2,048 threads; 43 KB of shared memory each in FP64)
 template <int NF, typename R>
-__global__ void __launch_bounds__(kThreads, (sizeof(R) == 8 ? 4 : 5)) stage_kernel(const __grid_constant__ StageArgs A) {
+__global__ void __launch_bounds__(kThreads, 5) stage_kernel(const __grid_constant__ StageArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StageSmem<NF, R>& S = *reinterpret_cast<StageSmem<NF, R>*>(smem_raw);
   stage_octant<NF, R>(S, A, A.list ? A.list[A.first + blockIdx.x] : A.first + blockIdx.x);
