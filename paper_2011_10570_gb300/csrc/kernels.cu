@@ -274,24 +274,48 @@ __device__ __forceinline__ double lattice_to_x(double lo, double ext, int P6) {
 // ---------------------------------------------------------------------------
 // The stage kernel
 // ---------------------------------------------------------------------------
+// kinds of a slot of the neighbour view, as seen from the octant being stepped
+constexpr int kKindCoarser = 0, kKindSame = 1, kKindFiner = 2, kKindNone = 3;
+constexpr int kSlots = 256;  // slot values of a padding-map entry (kSlotNone = 255 included)
+
 template <int NF, typename R>
 struct StageSmem {
-  R T[NF][kNT];              // padded tiles
-  StageTerms om[4];          // correction terms of this stage per relation
-  unsigned char slot[kNT];   // source slot in the neighbour view (kSlotNone: exterior)
-  unsigned short code[kNT];  // rx | ry << 4 | rz << 8 | (level diff + 1) << 12 | exterior << 15
+  R T[NF][kNT];               // padded tiles
+  StageTerms om[4];           // correction terms of this stage per relation
+  long long base[kSlots];     // per slot: element offset of its source in the array it is read from
+  unsigned char kind[kSlots]; // per slot: kKindCoarser / kKindSame / kKindFiner / kKindNone
+  int any_finer;              // some slot holds a finer leaf
   NbrView nv;
-  R orb[2];                  // orbit centre x_1 at this octant's stage time
+  R orb[2];                   // orbit centre x_1 at this octant's stage time
 };
 
-constexpr unsigned kExterior = 1u << 15;
+constexpr unsigned kExterior = 1u << 15;  // exterior flag of the 16-bit codes of the block map
 constexpr int kPer = (kNT + kThreads - 1) / kThreads;  // padded points per thread
+
+// padding-map entry: slot | off << 8 | rx << 20 | ry << 24 | rz << 28, with (rx, ry, rz)
+// the point's half-node coordinates in its source and off its element offset there
+// (rx + 13 ry + 169 rz in a coarser source's prolonged block, the node index otherwise)
+__device__ __forceinline__ unsigned pad_entry(unsigned slot, int rx, int ry, int rz, bool coarser) {
+  const unsigned off = coarser ? unsigned(rx + 13 * ry + 169 * rz) : unsigned((rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1));
+  return slot | off << 8 | unsigned(rx) << 20 | unsigned(ry) << 24 | unsigned(rz) << 28;
+}
+__device__ __forceinline__ int pad_rx(unsigned e) { return int((e >> 20) & 15u); }
+__device__ __forceinline__ int pad_ry(unsigned e) { return int((e >> 24) & 15u); }
+__device__ __forceinline__ int pad_rz(unsigned e) { return int(e >> 28); }
+__device__ __forceinline__ unsigned pad_off(unsigned e) { return (e >> 8) & 4095u; }
+
+// exterior padded point of octant (anchor me, edge eb): outside the domain
+__device__ __forceinline__ bool exterior_point(int4 me, int eb, int q) {
+  const int i = q % 13 - 3, j = (q / 13) % 13 - 3, k = q / 169 - 3;
+  const int P[3] = {6 * me.x + i * eb, 6 * me.y + j * eb, 6 * me.z + k * eb};
+  return P[0] < 0 || P[1] < 0 || P[2] < 0 || P[0] > kLatt6 || P[1] > kLatt6 || P[2] > kLatt6;
+}
 
 // exact boundary data (a reading of the paper): RK stage values of the closed-form solution
 template <int NF, typename R>
 __device__ __noinline__ void fill_exact(StageSmem<NF, R>& S, const StageArgs& A, int4 me, int eb, double dtb) {
   for (int q = threadIdx.x; q < kNT; q += blockDim.x) {
-    if (!(S.code[q] & kExterior)) continue;
+    if (!exterior_point(me, eb, q)) continue;
     const int i = q % 13 - 3, j = (q / 13) % 13 - 3, k = q / 169 - 3;
     const double x[3] = {lattice_to_x(A.lo, A.ext, 6 * me.x + i * eb), lattice_to_x(A.lo, A.ext, 6 * me.y + j * eb),
                          lattice_to_x(A.lo, A.ext, 6 * me.z + k * eb)};
@@ -534,6 +558,7 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
 
   load_neighbours(A.tree, b, S.nv);
   if (tid < 4) S.om[tid] = A.om[tid];
+  if (tid == 4) S.any_finer = 0;
   if (tid == 0 && A.orbit) {
     // x_1 = R (cos W t_s, sin W t_s, 0) at the stage time t_s = t_b + c_s dt of this level
     double c, sn;
@@ -543,15 +568,28 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
   }
   __syncthreads();
 
-  // 1. source of every padded point (coarsest leaf containing it, then smallest Morton
-  //    key), from the plan's padding map: slot in the neighbour view and half-node code
-  {
-    const unsigned* __restrict__ pm = A.padmap + (long long)b * kNT;
-    for (int q = tid; q < kNT; q += blockDim.x) {
-      const unsigned e = __ldg(pm + q);
-      S.slot[q] = static_cast<unsigned char>(e & 255u);
-      S.code[q] = static_cast<unsigned short>(e >> 8);
+  // 1. sources: the padding map gives every padded point its source (coarsest leaf
+  //    containing it, then smallest Morton key) as a slot of the neighbour view and an
+  //    element offset in that source; each slot's kind and base offset are resolved
+  //    here once per octant
+  const R* Uin = static_cast<const R*>(A.Uin);
+  const double* u0 = A.u[(A.cur_mask >> lb) & 1];
+  const float* us0 = A.us[(A.cur_mask >> lb) & 1];
+  const R* up_all = static_cast<const R*>(A.up);
+  const R* st_in = s == 0 ? state_array<R>(u0, us0) : Uin;
+  for (int t = tid; t < kSlots; t += blockDim.x) {
+    const int leaf = t < 27 + 27 * 8 ? slot_leaf(S.nv, unsigned(t), b) : -1;  // slots 243..255 hold no leaf
+    int kind = kKindNone;
+    long long base = 0;
+    if (leaf >= 0) {
+      // the 26 direct neighbours are coarser or same-level leaves, the children slots finer
+      const int ls = t == 13 ? lb : (t < 27 ? A.tree.oct[leaf].w : lb + 1);
+      kind = (ls >= lb - 1 && ls <= lb + 1) ? ls - lb + 1 : kKindNone;  // 2:1 balance: always in range
+      base = kind == kKindCoarser ? (long long)__ldg(A.up_slot + leaf) * NF * kNT : (long long)leaf * kNV;
+      if (kind == kKindFiner) S.any_finer = 1;
     }
+    S.kind[t] = static_cast<unsigned char>(kind);
+    S.base[t] = base;
   }
   __syncthreads();
 
@@ -559,42 +597,46 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
   //    read the stage inputs; coarser sources read their prolonged stage inputs
   //    (prepared by prolong_kernel); under GTS every source is read directly.  At
   //    stage 0 the stage input is the state u itself.
-  const R* Uin = static_cast<const R*>(A.Uin);
-  const double* u0 = A.u[(A.cur_mask >> lb) & 1];
-  const float* us0 = A.us[(A.cur_mask >> lb) & 1];
-  const R* up_all = static_cast<const R*>(A.up);
-  const R* st_in = s == 0 ? state_array<R>(u0, us0) : Uin;
-  for (int q = tid; q < kNT; q += kThreads) {
-    const unsigned code = S.code[q];
-    if (code & kExterior) {
+  //    The map entries are loaded first, all at once: each copy's address depends on
+  //    its entry, and the copies are ordered memory operations.
+  const unsigned* __restrict__ pm = A.padmap + (long long)b * kNT;
+  unsigned ev[kPer];
 #pragma unroll
-      for (int f = 0; f < NF; ++f) S.T[f][q] = 0;  // the boundary fill overwrites it
-      continue;
-    }
-    const int rx = code & 15, ry = (code >> 4) & 15, rz = (code >> 8) & 15;
-    const int rel_code = (code >> 12) & 3;  // 0 coarser, 1 same, 2 finer
-    const int src = slot_leaf(S.nv, S.slot[q], b);
-    if (rel_code == 0) {
-      const R* up = up_all + (long long)__ldg(A.up_slot + src) * NF * kNT + rx + 13 * ry + 169 * rz;
+  for (int r = 0; r < kPer; ++r) ev[r] = tid + r * kThreads < kNT ? __ldg(pm + tid + r * kThreads) : kSlotNone;
+#pragma unroll
+  for (int r = 0; r < kPer; ++r) {
+    const int q = tid + r * kThreads;
+    if (q >= kNT) break;
+    const unsigned e = ev[r];
+    const unsigned slot = e & 255u;
+    const int kind = S.kind[slot];
+    if (kind == kKindCoarser) {
+      const R* up = up_all + S.base[slot] + pad_off(e);
 #pragma unroll
       for (int f = 0; f < NF; ++f) async_copy(&S.T[f][q], up + f * kNT);
-    } else if (rel_code == 1 || A.gts) {
-      const long long off = (long long)src * kNV + (rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1);
+    } else if (kind == kKindSame || (kind == kKindFiner && A.gts)) {
+      const R* src = st_in + S.base[slot] + pad_off(e);
 #pragma unroll
-      for (int f = 0; f < NF; ++f) async_copy(&S.T[f][q], st_in + f * A.fstride + off);
+      for (int f = 0; f < NF; ++f) async_copy(&S.T[f][q], src + f * A.fstride);
+    } else if (kind == kKindNone) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) S.T[f][q] = 0;  // the boundary fill overwrites it
     }
     // finer sources under LTS: the correction pass below writes them
   }
 
   // 3. finer sources (injection) with the coarse<-fine correction of eq. fc_1 (FP64)
-  if (!A.gts) {
-    for (int q = tid; q < kNT; q += blockDim.x) {
-      const unsigned code = S.code[q];
-      if ((code & kExterior) || ((code >> 12) & 3) != 2) continue;
-      const int rx = code & 15, ry = (code >> 4) & 15, rz = (code >> 8) & 15;
-      const int ls = lb + 1;
-      const double* ub = A.u[(A.cur_mask >> ls) & 1];
-      const long long off = (long long)slot_leaf(S.nv, S.slot[q], b) * kNV + (rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1);
+  if (!A.gts && S.any_finer) {
+    const int ls = lb + 1;
+    const double* ub = A.u[(A.cur_mask >> ls) & 1];
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+      const int q = tid + r * kThreads;
+      if (q >= kNT) break;
+      const unsigned e = ev[r];
+      const unsigned slot = e & 255u;
+      if (S.kind[slot] != kKindFiner) continue;
+      const long long off = S.base[slot] + pad_off(e);
 #pragma unroll
       for (int f = 0; f < NF; ++f)
         S.T[f][q] = static_cast<R>(corrected_value<R>(ub + f * A.fstride + off, K + f * A.fstride + off, kstride,
@@ -685,7 +727,11 @@ struct BlockSmem {
   R T[NF][kBT];
   StageTerms om[4];
   R orb[2];
+  int any_finer;  // some ghost point has a finer source
 };
+
+constexpr int kBPer = (kBG + kBlockThreads - 1) / kBlockThreads;  // ghost points per thread
+constexpr int kBChunk = 4;  // ghost-map entries loaded together before their copies are issued
 
 // exact boundary data at the exterior points of the block tile (as fill_exact)
 template <int NF, typename R>
@@ -766,6 +812,7 @@ __global__ void __launch_bounds__(kBlockThreads, (sizeof(R) == 8 ? 2 : 4))
   const long long kstride = (long long)A.nf * A.fstride;
   R* __restrict__ K = static_cast<R*>(A.K);
   if (tid < 4) S.om[tid] = A.om[tid];
+  if (tid == 4) S.any_finer = 0;
   if (tid == 0 && A.orbit) {
     double c, sn;
     sincos(A.orb[1] * fma(A.c_s, A.lc[lb].dt, A.t_b), &sn, &c);
@@ -793,31 +840,49 @@ __global__ void __launch_bounds__(kBlockThreads, (sizeof(R) == 8 ? 2 : 4))
     for (int f = 0; f < NF; ++f) async_copy(&S.T[f][q], st_in + f * A.fstride + off);
   }
 
-  // 1b. ghost points (as stage_kernel step 2)
-  for (int gi = tid; gi < kBG; gi += kBlockThreads) {
-    const int q = g_block_ghost[gi];
-    const unsigned code = __ldg(gc + gi);
-    if (code & kExterior) {
+  // 1b. ghost points (as stage_kernel step 2), their map entries loaded kBChunk at a
+  //     time ahead of the copies that depend on them
+  for (int r0 = 0; r0 < kBPer; r0 += kBChunk) {
+    unsigned cv[kBChunk];
+    int sv[kBChunk];
 #pragma unroll
-      for (int f = 0; f < NF; ++f) S.T[f][q] = 0;  // the boundary fill overwrites it
-      continue;
+    for (int r = 0; r < kBChunk; ++r) {
+      const int gi = tid + (r0 + r) * kBlockThreads;
+      const bool ok = r0 + r < kBPer && gi < kBG;
+      cv[r] = ok ? __ldg(gc + gi) : 0xffffu;
+      sv[r] = ok ? __ldg(gs + gi) : -1;
     }
-    const int rx = code & 15, ry = (code >> 4) & 15, rz = (code >> 8) & 15;
-    const int rel_code = (code >> 12) & 3;  // 0 coarser, 1 same, 2 finer
-    const int src = __ldg(gs + gi);
-    if (rel_code == 0) {
-      const R* up = up_all + (long long)__ldg(A.up_slot + src) * NF * kNT + rx + 13 * ry + 169 * rz;
 #pragma unroll
-      for (int f = 0; f < NF; ++f) async_copy(&S.T[f][q], up + f * kNT);
-    } else if (rel_code == 1 || A.gts) {
-      const long long off = (long long)src * kNV + (rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1);
+    for (int r = 0; r < kBChunk; ++r) {
+      const int gi = tid + (r0 + r) * kBlockThreads;
+      const unsigned code = cv[r];
+      if (code == 0xffffu) continue;  // past the end
+      const int q = g_block_ghost[gi];
+      if (code & kExterior) {
 #pragma unroll
-      for (int f = 0; f < NF; ++f) async_copy(&S.T[f][q], st_in + f * A.fstride + off);
+        for (int f = 0; f < NF; ++f) S.T[f][q] = 0;  // the boundary fill overwrites it
+        continue;
+      }
+      const int rx = code & 15, ry = (code >> 4) & 15, rz = (code >> 8) & 15;
+      const int rel_code = (code >> 12) & 3;  // 0 coarser, 1 same, 2 finer
+      const int src = sv[r];
+      if (rel_code == 0) {
+        const R* up = up_all + (long long)__ldg(A.up_slot + src) * NF * kNT + rx + 13 * ry + 169 * rz;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) async_copy(&S.T[f][q], up + f * kNT);
+      } else if (rel_code == 1 || A.gts) {
+        const long long off = (long long)src * kNV + (rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) async_copy(&S.T[f][q], st_in + f * A.fstride + off);
+      } else {
+        S.any_finer = 1;
+      }
     }
   }
+  __syncthreads();  // S.any_finer
 
   // 2. finer sources with the coarse<-fine correction of eq. fc_1 (FP64)
-  if (!A.gts) {
+  if (!A.gts && S.any_finer) {
     for (int gi = tid; gi < kBG; gi += blockDim.x) {
       const unsigned code = __ldg(gc + gi);
       if ((code & kExterior) || ((code >> 12) & 3) != 2) continue;
@@ -948,8 +1013,13 @@ __global__ void __launch_bounds__(256) groupmap_kernel(const DevTree T, const in
       const int box = T.nbr[(long long)c * 27 + d];
       src = box <= -2 ? T.fine[(long long)(-box - 2) * 8 + ch] : -1;
     }
+    unsigned code = kExterior;
+    if (src >= 0) {
+      const int rel = T.oct[src].w - T.oct[c].w + 1;
+      code = unsigned(pad_rx(w)) | unsigned(pad_ry(w)) << 4 | unsigned(pad_rz(w)) << 8 | unsigned(rel) << 12;
+    }
     gsrc[e] = src;
-    gcode[e] = static_cast<unsigned short>(w >> 8);
+    gcode[e] = static_cast<unsigned short>(code);
   }
 }
 
@@ -1676,8 +1746,9 @@ cudaError_t launch_init(const InitArgs& a, cudaStream_t s) {
 
 // ---------------------------------------------------------------------------
 // Padding map (Fig. unzip): for every octant and padded point, the source's slot in
-// the octant's neighbour view and the point's half-node code in the source.  The
-// tree is static, so this is resolved once per plan instead of at every stage.
+// the octant's neighbour view, the point's element offset in the source and its
+// half-node coordinates there (pad_entry).  The tree is static, so this is resolved
+// once per plan instead of at every stage.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) padmap_kernel(const DevTree T, unsigned* __restrict__ out, int* err) {
   __shared__ NbrView nv;
@@ -1690,30 +1761,31 @@ __global__ void __launch_bounds__(256) padmap_kernel(const DevTree T, unsigned* 
     const int eb = 1 << (kDepth - lb);
     for (int q = threadIdx.x; q < kNT; q += blockDim.x) {
       const int i = q % 13 - 3, j = (q / 13) % 13 - 3, k = q / 169 - 3;
-      unsigned slot, code;
+      unsigned entry;
       if (i >= 0 && i <= 6 && j >= 0 && j <= 6 && k >= 0 && k <= 6) {
-        slot = 13u;
-        code = unsigned(2 * i) | unsigned(2 * j) << 4 | unsigned(2 * k) << 8 | 1u << 12;
+        entry = pad_entry(13u, 2 * i, 2 * j, 2 * k, false);
       } else {
+        unsigned slot;
         const int src = resolve_source(nv, i, j, k, b, false, &slot);
         if (src < 0) {
-          slot = kSlotNone;
-          code = kExterior;
+          entry = kSlotNone;
         } else {
           const int4 so = T.oct[src];
           const int rx = half_node(6 * me.x + i * eb, so.x, so.w);
           const int ry = half_node(6 * me.y + j * eb, so.y, so.w);
           const int rz = half_node(6 * me.z + k * eb, so.z, so.w);
-          if (unsigned(rx) > 12u || unsigned(ry) > 12u || unsigned(rz) > 12u || unsigned(so.w - lb + 1) > 2u) {
+          const bool coarser = so.w < lb;
+          // same-level and finer sources hold the point as a node (even coordinates)
+          const bool odd = !coarser && ((rx | ry | rz) & 1);
+          if (unsigned(rx) > 12u || unsigned(ry) > 12u || unsigned(rz) > 12u || unsigned(so.w - lb + 1) > 2u || odd) {
             atomicOr(err, 1);  // never on a balanced tree: reported, and the point becomes a zero ghost
-            slot = kSlotNone;
-            code = kExterior;
+            entry = kSlotNone;
           } else {
-            code = unsigned(rx) | unsigned(ry) << 4 | unsigned(rz) << 8 | unsigned(so.w - lb + 1) << 12;
+            entry = pad_entry(slot, rx, ry, rz, coarser);
           }
         }
       }
-      out[(long long)b * kNT + q] = slot | code << 8;
+      out[(long long)b * kNT + q] = entry;
     }
   }
 }
@@ -1741,12 +1813,11 @@ __global__ void maps_kernel(MapArgs A) {
     for (int q = threadIdx.x; q < kNT; q += blockDim.x) {
       const unsigned e = A.padmap[(long long)b * kNT + q];
       const int src = slot_leaf(S.nv, e & 255u, b);
-      const unsigned code = e >> 8;
       const long long o = (long long)blockIdx.x * kNT + q;
       A.src[o] = src;
-      A.r[o * 3 + 0] = src >= 0 ? int(code & 15u) : -1;
-      A.r[o * 3 + 1] = src >= 0 ? int((code >> 4) & 15u) : -1;
-      A.r[o * 3 + 2] = src >= 0 ? int((code >> 8) & 15u) : -1;
+      A.r[o * 3 + 0] = src >= 0 ? pad_rx(e) : -1;
+      A.r[o * 3 + 1] = src >= 0 ? pad_ry(e) : -1;
+      A.r[o * 3 + 2] = src >= 0 ? pad_rz(e) : -1;
     }
     return;
   }

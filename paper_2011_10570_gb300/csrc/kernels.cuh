@@ -79,13 +79,13 @@ struct StageArgs {
   int mixed;             // 1: FP32 stages, tile and right-hand side; FP64 state and corrections
   float* us[2];          // mixed: FP32 copies of u[2], kept equal to float(u) (stage inputs read them)
   const int* up_slot;    // slot of an octant in `up` (-1: not a coarser source)
-  const unsigned* padmap;  // [N][2197]: source slot | half-node code << 8 per padded point
+  const unsigned* padmap;  // [N][2197]: slot | offset << 8 | rx << 20 | ry << 24 | rz << 28 per padded point
   const int* list;         // stage_kernel: CTA x steps list[first + x] (nullptr: octant first + x)
   // block kernel (Sec. 3.2.5 octree-to-block decomposition): CTA x steps the complete
   // sibling group grp[first + x] (8 consecutive octants) as one 13^3-node block
   const int* grp;
   const int* gsrc;               // [G][kBG] source octant of every ghost point of a block tile (-1: exterior)
-  const unsigned short* gcode;   // [G][kBG] its half-node code (as in the padding map)
+  const unsigned short* gcode;   // [G][kBG] rx | ry << 4 | rz << 8 | (level diff + 1) << 12 | exterior << 15
   // wave source terms (eq. phi and the orbiting Gaussians); c_s is this stage's node
   double nl_c;
   int orbit;
