@@ -290,7 +290,6 @@ struct StageSmem {
 };
 
 constexpr unsigned kExterior = 1u << 15;  // exterior flag of the 16-bit codes of the block map
-constexpr int kPer = (kNT + kThreads - 1) / kThreads;  // padded points per thread
 
 // padding-map entry: slot | off << 8 | rx << 20 | ry << 24 | rz << 28, with (rx, ry, rz)
 // the point's half-node coordinates in its source and off its element offset there
@@ -544,9 +543,10 @@ __device__ __noinline__ R wave_source(const StageArgs& A, const int P6[3], R chi
 }
 
 // One RK stage of octant b (Alg. 2 compute_stage, or Alg. 1 when A.gts): called by
-// every thread of a CTA of kThreads threads, with S in shared memory.
-template <int NF, typename R>
+// every thread of a CTA of TPB threads, with S in shared memory.
+template <int NF, typename R, int TPB>
 __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int b) {
+  constexpr int kPer = (kNT + TPB - 1) / TPB;  // padded points per thread
   const int tid = threadIdx.x;
   const int p = A.p;
   const int s = A.stage;
@@ -602,10 +602,10 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
   const unsigned* __restrict__ pm = A.padmap + (long long)b * kNT;
   unsigned ev[kPer];
 #pragma unroll
-  for (int r = 0; r < kPer; ++r) ev[r] = tid + r * kThreads < kNT ? __ldg(pm + tid + r * kThreads) : kSlotNone;
+  for (int r = 0; r < kPer; ++r) ev[r] = tid + r * TPB < kNT ? __ldg(pm + tid + r * TPB) : kSlotNone;
 #pragma unroll
   for (int r = 0; r < kPer; ++r) {
-    const int q = tid + r * kThreads;
+    const int q = tid + r * TPB;
     if (q >= kNT) break;
     const unsigned e = ev[r];
     const unsigned slot = e & 255u;
@@ -631,7 +631,7 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
     const double* ub = A.u[(A.cur_mask >> ls) & 1];
 #pragma unroll
     for (int r = 0; r < kPer; ++r) {
-      const int q = tid + r * kThreads;
+      const int q = tid + r * TPB;
       if (q >= kNT) break;
       const unsigned e = ev[r];
       const unsigned slot = e & 255u;
@@ -661,8 +661,8 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
 
   // 5. right-hand side on the 7^3 interior (stage type R); stage, next stage input
   //    and RK update (stage_epilogue)
-  if (tid < kNV) {
-    const int i = tid % 7, j = (tid / 7) % 7, k = tid / 49;
+  for (int n = tid; n < kNV; n += TPB) {
+    const int i = n % 7, j = (n / 7) % 7, k = n / 49;
     const int c0 = (i + 3) + 13 * (j + 3) + 169 * (k + 3);
     const R kos = sizeof(R) == sizeof(double) ? R(lc.kos) : R(A.cf.lc[lb][0]);
     const R inv12h = sizeof(R) == sizeof(double) ? R(lc.inv12h) : R(A.cf.lc[lb][1]);
@@ -684,7 +684,7 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
         if (on_bnd) radiative_rhs<NF, R, 13, 169>(Tt, A, c0, P6, inv12h, kv);
       }
     }
-    const long long node = (long long)b * kNV + tid;
+    const long long node = (long long)b * kNV + n;
     R* Uout = static_cast<R*>(A.Uout);
     const int nx = ((A.cur_mask >> lb) & 1) ^ 1;
 #pragma unroll
@@ -702,12 +702,21 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
   }
 }
 
-// 5 CTAs per SM (1,760 of 2,048 threads; 43 KB of shared memory each in FP64)
+// Threads per CTA and CTAs per SM of the stage kernel: 352 threads (the 343 interior
+// nodes in one pass) and 5 CTAs per SM (1,760 of 2,048 threads; 39 KB of shared memory
+// each in FP64, 21 KB in mixed precision).  Mixed precision with 128 threads and 10
+// CTAs per SM (more octants in flight, no register spills) measured 13% slower.
+template <typename R> struct StageShape {
+  static constexpr int kTPB = kThreads;
+  static constexpr int kMinBlocks = 5;
+};
+
 template <int NF, typename R>
-__global__ void __launch_bounds__(kThreads, 5) stage_kernel(const __grid_constant__ StageArgs A) {
+__global__ void __launch_bounds__(StageShape<R>::kTPB, StageShape<R>::kMinBlocks)
+    stage_kernel(const __grid_constant__ StageArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StageSmem<NF, R>& S = *reinterpret_cast<StageSmem<NF, R>*>(smem_raw);
-  stage_octant<NF, R>(S, A, A.list ? A.list[A.first + blockIdx.x] : A.first + blockIdx.x);
+  stage_octant<NF, R, StageShape<R>::kTPB>(S, A, A.list ? A.list[A.first + blockIdx.x] : A.first + blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1037,9 +1046,12 @@ static cudaError_t launch_stage_t(const StageArgs& a, int count, cudaStream_t s)
     cudaError_t e = cudaFuncSetAttribute(stage_kernel<NF, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sizeof(StageSmem<NF, R>));
     if (e != cudaSuccess) return e;
+    // all of the unified L1 / shared memory as shared memory: the occupancy above needs it
+    e = cudaFuncSetAttribute(stage_kernel<NF, R>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
     configured = true;
   }
-  stage_kernel<NF, R><<<count, kThreads, sizeof(StageSmem<NF, R>), s>>>(a);
+  stage_kernel<NF, R><<<count, StageShape<R>::kTPB, sizeof(StageSmem<NF, R>), s>>>(a);
   return cudaGetLastError();
 }
 
@@ -1617,9 +1629,9 @@ __global__ void __launch_bounds__(kThreads, 4) batch_stage_kernel(const __grid_c
     }
     const int b = args.first + (item - pre[i]);
     if (args.nf == 1)
-      stage_octant<1, R>(*reinterpret_cast<StageSmem<1, R>*>(smem_raw), args, b);
+      stage_octant<1, R, kThreads>(*reinterpret_cast<StageSmem<1, R>*>(smem_raw), args, b);
     else
-      stage_octant<2, R>(*reinterpret_cast<StageSmem<2, R>*>(smem_raw), args, b);
+      stage_octant<2, R, kThreads>(*reinterpret_cast<StageSmem<2, R>*>(smem_raw), args, b);
   }
 }
 
