@@ -181,13 +181,14 @@ __device__ __forceinline__ int slot_leaf(const NbrView& nv, unsigned slot, int s
 // half-node coordinate of lattice6 coordinate P in a source with anchor a, level l
 __device__ __forceinline__ int half_node(int P, int a, int l) { return ((P - 6 * a) * 2) >> (kDepth - l); }
 
+// No barrier inside: the children entries read their box's entry from global memory,
+// and every caller synchronises before it reads nv.
 __device__ void load_neighbours(const DevTree& t, int b, NbrView& nv) {
-  for (int d = threadIdx.x; d < 27; d += blockDim.x) nv.nbr[d] = t.nbr[b * 27 + d];
-  __syncthreads();
+  for (int d = threadIdx.x; d < 27; d += blockDim.x) nv.nbr[d] = __ldg(t.nbr + b * 27 + d);
   for (int q = threadIdx.x; q < 27 * 8; q += blockDim.x) {
     const int d = q >> 3, c = q & 7;
-    const int e = nv.nbr[d];
-    nv.kids[d][c] = e <= -2 ? t.fine[(-e - 2) * 8 + c] : -1;
+    const int e = __ldg(t.nbr + b * 27 + d);
+    nv.kids[d][c] = e <= -2 ? __ldg(t.fine + (-e - 2) * 8 + c) : -1;
   }
 }
 
@@ -284,8 +285,6 @@ struct StageSmem {
   StageTerms om[4];           // correction terms of this stage per relation
   long long base[kSlots];     // per slot: element offset of its source in the array it is read from
   unsigned char kind[kSlots]; // per slot: kKindCoarser / kKindSame / kKindFiner / kKindNone
-  int any_finer;              // some slot holds a finer leaf
-  NbrView nv;
   R orb[2];                   // orbit centre x_1 at this octant's stage time
 };
 
@@ -556,9 +555,7 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
   const long long kstride = (long long)A.nf * A.fstride;
   R* __restrict__ K = static_cast<R*>(A.K);
 
-  load_neighbours(A.tree, b, S.nv);
   if (tid < 4) S.om[tid] = A.om[tid];
-  if (tid == 4) S.any_finer = 0;
   if (tid == 0 && A.orbit) {
     // x_1 = R (cos W t_s, sin W t_s, 0) at the stage time t_s = t_b + c_s dt of this level
     double c, sn;
@@ -566,7 +563,6 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
     S.orb[0] = R(A.orb[0] * c);
     S.orb[1] = R(A.orb[0] * sn);
   }
-  __syncthreads();
 
   // 1. sources: the padding map gives every padded point its source (coarsest leaf
   //    containing it, then smallest Morton key) as a slot of the neighbour view and an
@@ -577,8 +573,25 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
   const float* us0 = A.us[(A.cur_mask >> lb) & 1];
   const R* up_all = static_cast<const R*>(A.up);
   const R* st_in = s == 0 ? state_array<R>(u0, us0) : Uin;
+  // The map entries are loaded first, all at once (their latency overlaps the slot
+  // table's): each copy's address depends on its entry, and the copies are ordered
+  // memory operations.
+  const unsigned* __restrict__ pm = A.padmap + (long long)b * kNT;
+  unsigned ev[kPer];
+#pragma unroll
+  for (int r = 0; r < kPer; ++r) ev[r] = tid + r * TPB < kNT ? __ldg(pm + tid + r * TPB) : kSlotNone;
+  int my_finer = 0;
   for (int t = tid; t < kSlots; t += blockDim.x) {
-    const int leaf = t < 27 + 27 * 8 ? slot_leaf(S.nv, unsigned(t), b) : -1;  // slots 243..255 hold no leaf
+    // the leaf in slot t of the neighbour view (as slot_leaf), read from the tree directly
+    int leaf = -1;
+    if (t == 13) {
+      leaf = b;
+    } else if (t < 27) {
+      leaf = __ldg(A.tree.nbr + (long long)b * 27 + t);  // < 0: outside, or a box with children
+    } else if (t < 27 + 27 * 8) {  // slots 243..255 hold no leaf
+      const int e = __ldg(A.tree.nbr + (long long)b * 27 + ((t - 27) >> 3));
+      leaf = e <= -2 ? __ldg(A.tree.fine + (long long)(-e - 2) * 8 + ((t - 27) & 7)) : -1;
+    }
     int kind = kKindNone;
     long long base = 0;
     if (leaf >= 0) {
@@ -586,23 +599,17 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
       const int ls = t == 13 ? lb : (t < 27 ? A.tree.oct[leaf].w : lb + 1);
       kind = (ls >= lb - 1 && ls <= lb + 1) ? ls - lb + 1 : kKindNone;  // 2:1 balance: always in range
       base = kind == kKindCoarser ? (long long)__ldg(A.up_slot + leaf) * NF * kNT : (long long)leaf * kNV;
-      if (kind == kKindFiner) S.any_finer = 1;
+      my_finer |= kind == kKindFiner;
     }
     S.kind[t] = static_cast<unsigned char>(kind);
     S.base[t] = base;
   }
-  __syncthreads();
+  const bool any_finer = __syncthreads_or(my_finer) != 0;  // also publishes the table, om and orb
 
   // 2. gathers, batched for memory parallelism: own interior and same-level sources
   //    read the stage inputs; coarser sources read their prolonged stage inputs
   //    (prepared by prolong_kernel); under GTS every source is read directly.  At
   //    stage 0 the stage input is the state u itself.
-  //    The map entries are loaded first, all at once: each copy's address depends on
-  //    its entry, and the copies are ordered memory operations.
-  const unsigned* __restrict__ pm = A.padmap + (long long)b * kNT;
-  unsigned ev[kPer];
-#pragma unroll
-  for (int r = 0; r < kPer; ++r) ev[r] = tid + r * TPB < kNT ? __ldg(pm + tid + r * TPB) : kSlotNone;
 #pragma unroll
   for (int r = 0; r < kPer; ++r) {
     const int q = tid + r * TPB;
@@ -626,7 +633,7 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
   }
 
   // 3. finer sources (injection) with the coarse<-fine correction of eq. fc_1 (FP64)
-  if (!A.gts && S.any_finer) {
+  if (!A.gts && any_finer) {
     const int ls = lb + 1;
     const double* ub = A.u[(A.cur_mask >> ls) & 1];
 #pragma unroll
@@ -651,13 +658,13 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
   constexpr int kRoot = 1 << kDepth;
   const bool touches = me.x == 0 || me.y == 0 || me.z == 0 || me.x + eb == kRoot || me.y + eb == kRoot ||
                        me.z + eb == kRoot;
-  if (touches) {
+  if (touches) {  // uniform over the CTA
     if (A.bc == LTS_BC_EXACT)
       fill_exact<NF, R>(S, A, me, eb, lc.dt);
     else
       fill_extrapolated<NF, R>(S, me, eb);
+    __syncthreads();
   }
-  __syncthreads();
 
   // 5. right-hand side on the 7^3 interior (stage type R); stage, next stage input
   //    and RK update (stage_epilogue)
@@ -915,13 +922,13 @@ __global__ void __launch_bounds__(kBlockThreads, (sizeof(R) == 8 ? 2 : 4))
   const int eb2 = 2 * eb;
   const bool touches = me.x == 0 || me.y == 0 || me.z == 0 || me.x + eb2 == kRoot || me.y + eb2 == kRoot ||
                        me.z + eb2 == kRoot;
-  if (touches) {
+  if (touches) {  // uniform over the CTA
     if (A.bc == LTS_BC_EXACT)
       block_fill_exact<NF, R>(S, A, me, eb, lc.dt);
     else
       block_fill_extrapolated<NF, R>(S, me, eb2);
+    __syncthreads();
   }
-  __syncthreads();
 
   // 4. right-hand side at the 13^3 block nodes; stage, next stage input and RK update
   //    (FP64) written to every octant copy of the node
@@ -1073,8 +1080,10 @@ struct ProlongSmem {
   R V[NF][kNV];
   R X1[NF][13 * 49];      // [ra][jc][jb] in the frame of the pass axes a, b, c
   R X2[NF][13 * 13 * 7];  // [ra][rb][jc]
-  R W[13][7];
+  R E[3][4];              // symmetric-part weights of the mirrored pairs (1, 11), (3, 9), (5, 7)
+  R O[3][3];              // antisymmetric-part weights
 };
+
 
 // Division by a divisor fixed per CTA: q = floor(t / d) = umulhi(t, ceil(2^32 / d)), exact
 // while t * d < 2^32 (here t < 2 * 2197 and d <= 2 * 2197).
@@ -1090,6 +1099,33 @@ __device__ __forceinline__ int half_class(int r) { return r <= 3 ? 0 : (r >= 9 ?
 // lowest / highest coordinate of the classes in a 3-bit set
 __device__ __forceinline__ int class_lo(unsigned m) { return (m & 1u) ? 0 : ((m & 2u) ? 4 : 9); }
 __device__ __forceinline__ int class_hi(unsigned m) { return (m & 4u) ? 12 : ((m & 2u) ? 8 : 3); }
+
+// One line of the interpolation: the 7 node values v of a line to the half-node
+// positions r in [r0, r0 + n) whose class is in the 3-bit set cls; put(r, value).
+// Even positions are nodes (copies).  Odd positions come in mirrored pairs (k, 12 - k):
+// the Lagrange weights satisfy W[12 - k][j] = W[k][6 - j], so with s_j = v_j + v_{6-j}
+// and d_j = v_j - v_{6-j} the pair is E + O and E - O, E = sum_j E[p][j] s_j (s_3 = v_3)
+// and O = sum_j O[p][j] d_j: 33 operations for a whole line instead of 42.
+template <typename R, typename Put>
+__device__ __forceinline__ void interp_line(const R (&v)[7], int r0, int n, unsigned cls, const R (*E)[4],
+                                            const R (*O)[3], Put put) {
+  auto needed = [&](int r) { return r >= r0 && r < r0 + n && ((cls >> half_class(r)) & 1u); };
+#pragma unroll
+  for (int r = 0; r <= 12; r += 2)
+    if (needed(r)) put(r, v[r >> 1]);
+  const R s0 = v[0] + v[6], s1 = v[1] + v[5], s2 = v[2] + v[4];
+  const R d0 = v[0] - v[6], d1 = v[1] - v[5], d2 = v[2] - v[4];
+#pragma unroll
+  for (int pr = 0; pr < 3; ++pr) {
+    const int k = 2 * pr + 1;
+    const bool nk = needed(k), nm = needed(12 - k);
+    if (!(nk || nm)) continue;
+    const R e = fma(E[pr][0], s0, fma(E[pr][1], s1, fma(E[pr][2], s2, E[pr][3] * v[3])));
+    const R o = fma(O[pr][0], d0, fma(O[pr][1], d1, O[pr][2] * d2));
+    if (nk) put(k, e + o);
+    if (nm) put(12 - k, e - o);
+  }
+}
 
 // Prolongation of octant b for one stage; called by every thread of a CTA.  The
 // passes run along axes a, b, c (a permutation of x, y, z chosen per source on the
@@ -1126,7 +1162,15 @@ __device__ void prolong_octant(ProlongSmem<NF, R>& S, const ProlongArgs& A, cons
   const int c0 = class_lo(mc), nc = class_hi(mc) - c0 + 1;
   const long long kstride = (long long)A.nf * A.fstride;
   const R* K = static_cast<const R*>(A.K);
-  for (int q = tid; q < 91; q += blockDim.x) S.W[q / 7][q % 7] = R(c_W[q / 7][q % 7]);
+  if (tid < 21) {  // pair weights of the symmetric evaluation (interp_line), from the FP64 table
+    const int pr = tid / 7, q = tid % 7, k = 2 * pr + 1;
+    if (q < 4) {
+      S.E[pr][q] = R(q < 3 ? 0.5 * (c_W[k][q] + c_W[k][6 - q]) : c_W[k][3]);
+    } else {
+      const int j = q - 4;
+      S.O[pr][j] = R(0.5 * (c_W[k][j] - c_W[k][6 - j]));
+    }
+  }
   const int cur = (A.cur_mask >> lb) & 1;
   const R* Uin = static_cast<const R*>(A.Uin);
   const double* ub = A.u[cur ^ (rel == 3 ? 1 : 0)];
@@ -1145,66 +1189,51 @@ __device__ void prolong_octant(ProlongSmem<NF, R>& S, const ProlongArgs& A, cons
     S.V[f][n] = v;
   }
   __syncthreads();
-  // pass 1 (axis a): X1[ra][jb + 7 jc]
-  const FastDiv by_a49{unsigned(na * 49)};
-  for (int t = tid; t < NF * na * 49; t += blockDim.x) {
-    const int f = int(by_a49.div(unsigned(t))), rem = t - f * na * 49;
-    const int ri = rem / 49, bc = rem - ri * 49;
-    const int ra = a0 + ri;
-    if (!(ma >> half_class(ra) & 1u)) continue;
-    const R* v = S.V[f] + 7 * bc;
-    R acc;
-    if (ra & 1) {
-      acc = 0;
+  // pass 1 (axis a): one thread per line (f, jb, jc), X1[ra][jb + 7 jc]
+  for (int t = tid; t < NF * 49; t += blockDim.x) {
+    const int f = t / 49, bc = t - f * 49;
+    R v[7];
 #pragma unroll
-      for (int q = 0; q < 7; ++q) acc = fma(S.W[ra][q], v[q], acc);
-    } else {
-      acc = v[ra >> 1];
-    }
-    S.X1[f][ra * 49 + bc] = acc;
+    for (int q = 0; q < 7; ++q) v[q] = S.V[f][7 * bc + q];
+    R* x1 = S.X1[f] + bc;
+    interp_line<R>(v, a0, na, ma, S.E, S.O, [&](int r, R val) { x1[r * 49] = val; });
   }
   __syncthreads();
-  // pass 2 (axis b): X2[ra][rb][jc]
-  const FastDiv by_ab7{unsigned(na * nb * 7)}, by_b{unsigned(nb)};
-  for (int t = tid; t < NF * na * nb * 7; t += blockDim.x) {
-    const int f = int(by_ab7.div(unsigned(t))), rem = t - f * na * nb * 7;
-    const int jc = rem % 7, r7 = rem / 7;
-    const int rai = int(by_b.div(unsigned(r7))), rbi = r7 - rai * nb;
-    const int ra = a0 + rai, rb = b0 + rbi;
-    if (!(mab >> (half_class(ra) + 3 * half_class(rb)) & 1u)) continue;
+  // pass 2 (axis b): one thread per line (f, ra, jc), X2[ra][rb][jc]
+  const FastDiv by_a7{unsigned(na * 7)};
+  for (int t = tid; t < NF * na * 7; t += blockDim.x) {
+    const int f = int(by_a7.div(unsigned(t))), rem = t - f * na * 7;
+    const int rai = rem / 7, jc = rem - rai * 7;
+    const int ra = a0 + rai, ca = half_class(ra);
+    const unsigned cls = ((mab >> ca) & 1u) | ((mab >> (ca + 3)) & 1u) << 1 | ((mab >> (ca + 6)) & 1u) << 2;
+    if (!cls) continue;
+    R v[7];
     const R* x1 = S.X1[f] + ra * 49 + 7 * jc;  // [jb]
-    R acc;
-    if (rb & 1) {
-      acc = 0;
 #pragma unroll
-      for (int q = 0; q < 7; ++q) acc = fma(S.W[rb][q], x1[q], acc);
-    } else {
-      acc = x1[rb >> 1];
-    }
-    S.X2[f][(ra * 13 + rb) * 7 + jc] = acc;
+    for (int q = 0; q < 7; ++q) v[q] = x1[q];
+    R* x2 = S.X2[f] + ra * 13 * 7 + jc;
+    interp_line<R>(v, b0, nb, cls, S.E, S.O, [&](int r, R val) { x2[r * 7] = val; });
   }
   __syncthreads();
-  // pass 3 (axis c): every position of the set, written at rx + 13 ry + 169 rz
+  // pass 3 (axis c): one thread per line (f, ra, rb), every position of the set written
+  // at rx + 13 ry + 169 rz
   R* out = static_cast<R*>(A.up) + (long long)slot * NF * kNT;
   const int soa = pa == 0 ? 1 : (pa == 1 ? 13 : 169), sob = pb == 0 ? 1 : (pb == 1 ? 13 : 169);
   const int soc = pc == 0 ? 1 : (pc == 1 ? 13 : 169);
-  const FastDiv by_abc{unsigned(na * nb * nc)}, by_a{unsigned(na)}, by_ab{unsigned(na * nb)};
-  for (int t = tid; t < NF * na * nb * nc; t += blockDim.x) {
-    const int f = int(by_abc.div(unsigned(t))), rem = t - f * na * nb * nc;
-    const int rci = int(by_ab.div(unsigned(rem))), rab = rem - rci * na * nb;
+  const FastDiv by_ab{unsigned(na * nb)}, by_a{unsigned(na)};
+  for (int t = tid; t < NF * na * nb; t += blockDim.x) {
+    const int f = int(by_ab.div(unsigned(t))), rab = t - f * na * nb;
     const int rbi = int(by_a.div(unsigned(rab))), rai = rab - rbi * na;
-    const int ra = a0 + rai, rb = b0 + rbi, rc = c0 + rci;
-    if (!(m >> (half_class(ra) + 3 * half_class(rb) + 9 * half_class(rc)) & 1u)) continue;
+    const int ra = a0 + rai, rb = b0 + rbi;
+    const unsigned sh = unsigned(half_class(ra) + 3 * half_class(rb));
+    const unsigned cls = ((m >> sh) & 1u) | ((m >> (sh + 9)) & 1u) << 1 | ((m >> (sh + 18)) & 1u) << 2;
+    if (!cls) continue;
+    R v[7];
     const R* x2 = S.X2[f] + (ra * 13 + rb) * 7;  // [jc]
-    R acc;
-    if (rc & 1) {
-      acc = 0;
 #pragma unroll
-      for (int q = 0; q < 7; ++q) acc = fma(S.W[rc][q], x2[q], acc);
-    } else {
-      acc = x2[rc >> 1];
-    }
-    out[f * kNT + ra * soa + rb * sob + rc * soc] = acc;
+    for (int q = 0; q < 7; ++q) v[q] = x2[q];
+    R* o = out + f * kNT + ra * soa + rb * sob;
+    interp_line<R>(v, c0, nc, cls, S.E, S.O, [&](int r, R val) { o[r * soc] = val; });
   }
 }
 
