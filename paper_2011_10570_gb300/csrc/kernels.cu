@@ -6,9 +6,10 @@
 //   prolong_kernel: one CTA per octant with finer neighbours forms its stage
 //     inputs as those neighbours see them (eqs. fc_1, fc_2) and interpolates
 //     them to the half-node positions they read (Fig. unzip, coarse -> fine).
-//   stage_kernel: one CTA per active octant resolves the source of each of the
-//     2197 points of its padded block (Sec. 3.3: coarsest leaf containing the
-//     point, ties to the smallest Morton key = smallest level-order index),
+//   stage_kernel: one CTA per active octant reads the source of each of the
+//     2197 points of its padded block from the plan's padding map (Sec. 3.3:
+//     coarsest leaf containing the point, ties to the smallest Morton key =
+//     smallest level-order index; resolved once per plan by padmap_kernel),
 //     gathers the sources' stage inputs into shared memory, fills the physical
 //     boundary, evaluates the 4th-order FD right-hand side with Kreiss-Oliger
 //     dissipation on the 7^3 interior and writes the stage, the next stage's
