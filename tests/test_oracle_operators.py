@@ -80,6 +80,11 @@ def test_lagrange_interpolation(orc):
         vals = xs ** deg
         for r in range(13):
             assert abs(W[r] @ vals - (0.5 * r) ** deg) < 1e-9 * max(1.0, (0.5 * r) ** deg)
+    # reflection x -> 6 - x maps the nodes onto themselves and position r / 2 onto
+    # (12 - r) / 2: the weights of mirrored positions are reversed copies (the CUDA
+    # prolongation evaluates mirrored pairs from symmetric and antisymmetric sums)
+    for r in range(13):
+        assert np.allclose(W[12 - r], W[r][::-1], rtol=0, atol=1e-15)
     rng = np.random.default_rng(2)
     c = rng.uniform(-1, 1, (4, 4, 4))
     node = np.arange(7.0)
