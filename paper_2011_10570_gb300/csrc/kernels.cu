@@ -1472,9 +1472,10 @@ cudaError_t launch_sync_hanging(const SyncArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Node maps of a plan: for every boundary node of every octant, its owner (R6 rule, the
-// octant itself included) and whether it is a copy (all half-node coordinates even) or
-// a hanging node to interpolate.
+// Node maps of a plan: for every boundary node of every octant, its owner (the coarsest
+// octant having the node, ties to the smallest Morton key, the octant itself included)
+// and whether it is a copy (all half-node coordinates even) or a hanging node to
+// interpolate.
 __global__ void __launch_bounds__(128) nodemap_kernel(const DevTree T, const int* __restrict__ hang_pos,
                                                        int* __restrict__ zipmap, int* __restrict__ hang_src,
                                                        unsigned short* __restrict__ hang_code, int* err) {
