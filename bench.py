@@ -32,7 +32,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x flops/FM
 # DRAM bytes (read + write) per node-stage of stage_kernel<2, double> / <2, float>, from the
 # ncu captures of profiles/stage_kernel_wave_l4-8.md; set to None whenever the kernel changes
 STAGE_DRAM_BYTES_PER_NODE_STAGE = 117.5
-STAGE_DRAM_BYTES_PER_NODE_STAGE_MIXED = 74.1
+STAGE_DRAM_BYTES_PER_NODE_STAGE_MIXED = 74.3
 
 
 def measured_peaks():

@@ -48,6 +48,13 @@ __device__ unsigned short g_block_ghost[kBG];
 // boundary nodes of an octant (a coordinate 0 or 6), in node order
 __device__ unsigned short g_bnode[kBN];
 
+// node of the 13^3 stage tile whose FP32 right-hand side thread t evaluates (-1: none).
+// Lane l of every warp takes a node whose tile index c0 is l mod 32, so the 19 loads per
+// field of a node hit 32 different banks; in node order, rows of 7 nodes at a row stride
+// of 13 put two nodes of a warp on one bank.  (The order is also free of conflicts for
+// 8-byte loads, but the FP64 kernel, bound by its FP64 pipe, measured no gain from it.)
+__device__ short g_rhs_node[kThreads];
+
 cudaError_t upload_tables(const Tables* rk4, const Tables* rk3, const double W[13][7], const double E[4][4]) {
   {
     unsigned short bn[kBN];
@@ -58,6 +65,30 @@ cudaError_t upload_tables(const Tables* rk4, const Tables* rk3, const double W[1
     }
     if (n != kBN) return cudaErrorInvalidValue;
     const cudaError_t e = cudaMemcpyToSymbol(g_bnode, bn, sizeof(bn));
+    if (e != cudaSuccess) return e;
+  }
+  {
+    // tile nodes by bank (c0 mod 32); warp w takes the w-th node of every bank
+    short order[kThreads];
+    int taken[32] = {0};
+    for (int t = 0; t < kThreads; ++t) order[t] = -1;
+    for (int w = 0; w < kThreads / 32; ++w)
+      for (int l = 0; l < 32; ++l) {
+        int seen = 0;
+        for (int q = 0; q < kNV; ++q) {
+          const int c0 = (q % 7 + 3) + 13 * ((q / 7) % 7 + 3) + 169 * (q / 49 + 3);
+          if (c0 % 32 != l) continue;
+          if (seen++ == taken[l]) {
+            order[w * 32 + l] = static_cast<short>(q);
+            ++taken[l];
+            break;
+          }
+        }
+      }
+    int placed = 0;
+    for (int l = 0; l < 32; ++l) placed += taken[l];
+    if (placed != kNV) return cudaErrorInvalidValue;  // 343 nodes over 11 warps: 10 or 11 per bank
+    const cudaError_t e = cudaMemcpyToSymbol(g_rhs_node, order, sizeof(order));
     if (e != cudaSuccess) return e;
   }
   {
@@ -286,6 +317,7 @@ struct StageSmem {
   StageTerms om[4];           // correction terms of this stage per relation
   long long base[kSlots];     // per slot: element offset of its source in the array it is read from
   unsigned char kind[kSlots]; // per slot: kKindCoarser / kKindSame / kKindFiner / kKindNone
+  R KV[sizeof(R) == sizeof(float) ? NF : 1][sizeof(R) == sizeof(float) ? kNV : 1];  // FP32: staged right-hand sides
   R orb[2];                   // orbit centre x_1 at this octant's stage time
 };
 
@@ -667,15 +699,14 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
     __syncthreads();
   }
 
-  // 5. right-hand side on the 7^3 interior (stage type R); stage, next stage input
-  //    and RK update (stage_epilogue)
-  for (int n = tid; n < kNV; n += TPB) {
+  // 5. right-hand side on the 7^3 interior (stage type R) and 6. stage, next stage
+  //    input and RK update (stage_epilogue) of node n
+  auto rhs_at = [&](int n, R (&kv)[NF]) {
     const int i = n % 7, j = (n / 7) % 7, k = n / 49;
     const int c0 = (i + 3) + 13 * (j + 3) + 169 * (k + 3);
     const R kos = sizeof(R) == sizeof(double) ? R(lc.kos) : R(A.cf.lc[lb][0]);
     const R inv12h = sizeof(R) == sizeof(double) ? R(lc.inv12h) : R(A.cf.lc[lb][1]);
     const R inv12h2 = sizeof(R) == sizeof(double) ? R(lc.inv12h2) : R(A.cf.lc[lb][2]);
-    R kv[NF];
     const R* Tt[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) Tt[f] = S.T[f];
@@ -692,6 +723,8 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
         if (on_bnd) radiative_rhs<NF, R, 13, 169>(Tt, A, c0, P6, inv12h, kv);
       }
     }
+  };
+  auto finish = [&](int n, const R (&kv)[NF]) {
     const long long node = (long long)b * kNV + n;
     R* Uout = static_cast<R*>(A.Uout);
     const int nx = ((A.cur_mask >> lb) & 1) ^ 1;
@@ -706,6 +739,32 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
         A.u[nx][o] = e.unew;
         if (sizeof(R) != sizeof(double)) A.us[nx][o] = e.unew_s;
       }
+    }
+  };
+  if constexpr (sizeof(R) == sizeof(double)) {
+    // FP64: node order; the FP64 pipe, not shared memory, bounds this kernel
+    if (tid < kNV) {
+      R kv[NF];
+      rhs_at(tid, kv);
+      finish(tid, kv);
+    }
+  } else {
+    // FP32: right-hand sides in the bank-conflict-free order of g_rhs_node, staged in
+    // shared memory, then the epilogue in node order (coalesced stores)
+    static_assert(TPB == kThreads, "g_rhs_node is laid out for kThreads threads");
+    const int n = g_rhs_node[tid];
+    if (n >= 0) {
+      R kv[NF];
+      rhs_at(n, kv);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) S.KV[f][n] = kv[f];
+    }
+    __syncthreads();
+    for (int m = tid; m < kNV; m += TPB) {
+      R kv[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) kv[f] = S.KV[f][m];
+      finish(m, kv);
     }
   }
 }
