@@ -116,6 +116,7 @@ def lib():
             L.orc_set_state.argtypes = [vp, dp, C.c_double]
             L.orc_get_state.argtypes = [vp, dp]
             L.orc_get_stage.argtypes = [vp, C.c_int, dp]
+            L.orc_solver_tile.argtypes = [vp, i64, dp]
             L.orc_exact_state.argtypes = [vp, C.c_double, dp]
             L.orc_lts_substeps.argtypes = [vp, i64]
             L.orc_lts_substep_masked.argtypes = [vp, C.POINTER(C.c_uint8), C.POINTER(C.c_uint8)]
@@ -291,6 +292,12 @@ class Solver:
         k = np.zeros((self.nf, self.n, NV))
         lib().orc_get_stage(self.h, j, _p(k, C.c_double))
         return k
+
+    def tile(self, b):
+        """padded 13^3 block [nf][13][13][13] (k, j, i order) of octant b from the current state"""
+        T = np.zeros((self.nf, 13, 13, 13))
+        lib().orc_solver_tile(self.h, int(b), _p(T, C.c_double))
+        return T
 
     def exact(self, t):
         u = np.zeros((self.nf, self.n, NV))

@@ -1121,7 +1121,7 @@ static void fill_extrapolated(const orc_solver* s, const oct_t* o, double* T) {
   int64_t e = edge_of(o->l);
   int64_t A[3] = {o->x, o->y, o->z};
   double E[4][4];
-  for (int m = 1; m <= 3; ++m) extrap_weights(m, E[m]);
+  for (int m = 1; m <= 3; ++m) extrap_weights(g_mutation == 7 ? m % 3 + 1 : m, E[m]); /* mutation 7: wrong row */
   for (int a = 0; a < 3; ++a) {
     int lo_bnd = (6 * A[a] == 0);
     int hi_bnd = (6 * (A[a] + e) == L6);
@@ -1163,17 +1163,16 @@ static void fill_extrapolated(const orc_solver* s, const oct_t* o, double* T) {
   }
 }
 
-/* One RK stage of one octant (Alg. 2 compute_stage; Alg. 1 when gts != 0):
- * unzip into a padded 13^3 tile (Sec. 3.3, Fig. unzip) with time-corrected
- * neighbour stages (eqs. fc_1, fc_2), then the FD right-hand side. */
-static void compute_stage(orc_solver* s, int64_t b, int st, int gts, int lstar, double* kout /* [nf][343] */) {
+/* Unzip of one octant at one RK stage (Sec. 3.3, Fig. unzip): the padded 13^3
+ * tile T[nf][2197] of stage inputs, with time-corrected neighbour stages
+ * (eqs. fc_1, fc_2) and the physical boundary fill. */
+static void unzip_tile(orc_solver* s, int64_t b, int st, int gts, int lstar, double* T /* [nf][2197] */) {
   const oct_t* o = &s->t->oct[b];
   int lb = o->l;
   double dtb = gts ? s->dt_f : dt_level(s, lb);
   double tb = orc_solver_time(s);
   int nf = s->nf;
   padent* pe = get_pad(s, b);
-  double* T = (double*)malloc((size_t)nf * NT * sizeof(double));
   int64_t e = edge_of(lb);
 
   /* stage inputs of every source that needs interpolation, computed once per octant-stage */
@@ -1264,6 +1263,18 @@ static void compute_stage(orc_solver* s, int64_t b, int st, int gts, int lstar, 
   } else {
     for (int f = 0; f < nf; ++f) fill_extrapolated(s, o, T + (size_t)f * NT);
   }
+}
+
+/* One RK stage of one octant (Alg. 2 compute_stage; Alg. 1 when gts != 0):
+ * unzip into a padded 13^3 tile, then the FD right-hand side. */
+static void compute_stage(orc_solver* s, int64_t b, int st, int gts, int lstar, double* kout /* [nf][343] */) {
+  const oct_t* o = &s->t->oct[b];
+  int lb = o->l;
+  double dtb = gts ? s->dt_f : dt_level(s, lb);
+  double tb = orc_solver_time(s);
+  double* T = (double*)malloc((size_t)s->nf * NT * sizeof(double));
+  int64_t e = edge_of(lb);
+  unzip_tile(s, b, st, gts, lstar, T);
 
   /* right-hand side on the 7^3 interior */
   double h = (s->spec.hi - s->spec.lo) * (double)e / (6.0 * (double)ROOT_EDGE);
@@ -1336,7 +1347,10 @@ static void compute_stage(orc_solver* s, int64_t b, int st, int gts, int lstar, 
                   xd += x[a] * d1_of(v, h);
                 }
                 double fv = Tf[tix(ii, jj, kk)];
-                kout[(size_t)f * NV + n] = -xd / r - (f == 0 ? 1.0 : 2.0) * fv / r;
+                double kf = f == 0 ? 1.0 : 2.0;
+                if (g_mutation == 5) kf = 3.0 - kf; /* mutation 5: k of chi and phi swapped */
+                if (g_mutation == 6) xd = -xd;      /* mutation 6: sign of the x^i/r term */
+                kout[(size_t)f * NV + n] = -xd / r - kf * fv / r;
               }
             }
           }
@@ -1405,6 +1419,11 @@ void orc_set_state(orc_solver* s, const double* u, double t0) {
   s->t_macro = t0;
   s->n_sub = 0;
 }
+
+/* The padded 13^3 block of octant b unzipped from the current state (Sec. 3.3,
+ * Fig. unzip): the first RK stage's input with every neighbour at the same time
+ * (Alg. 1 relation), physical boundary fill included.  T is [nf][2197]. */
+void orc_solver_tile(orc_solver* s, int64_t b, double* T) { unzip_tile(s, b, 0, 1, s->l_min, T); }
 
 void orc_get_state(const orc_solver* s, double* u) { memcpy(u, s->u, s->fsz * (size_t)s->nf * sizeof(double)); }
 

@@ -121,6 +121,8 @@ void orc_set_initial(orc_solver* s, double t0);
 void orc_set_state(orc_solver* s, const double* u, double t0);
 void orc_get_state(const orc_solver* s, double* u);
 void orc_get_stage(const orc_solver* s, int stage, double* k);
+/* padded 13^3 block [nf][2197] of octant b from the current state (first-stage input) */
+void orc_solver_tile(orc_solver* s, int64_t b, double* T);
 void orc_exact_state(const orc_solver* s, double t, double* u);
 /* Alg. 2 with the substep schedule of Fig. blk_loop: n substeps of dt_f */
 void orc_lts_substeps(orc_solver* s, int64_t n);
@@ -138,7 +140,8 @@ double orc_work_model(const orc_tree* t, double* w_lts, double* w_gts);
 void orc_set_threads(int n);
 /* negative controls for the tests (0 = the method as stated): 1 no time correction,
  * 2 nearest node instead of interpolation, 3 wrong advection sign, 4 step-end
- * state for inactive coarser sources */
+ * state for inactive coarser sources, 5 radiative k of chi and phi swapped,
+ * 6 sign of the radiative x^i/r term flipped, 7 wrong cubic-extrapolation row */
 void orc_set_mutation(int m);
 
 #ifdef __cplusplus
