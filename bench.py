@@ -29,8 +29,8 @@ sys.path.insert(0, ROOT)
 METRIC = "LTS octant-node updates/s"
 UNIT = "node-updates/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x flops/FMA x max clock
-# DRAM bytes (read + write) per node-stage of stage_kernel<2, double> / <2, float>, from the
-# ncu captures of profiles/stage_kernel_wave_l4-8.md; set to None whenever the kernel changes
+# DRAM bytes (read + write) per node-stage of stage_kernel<2, double> / <2, float>, from ncu
+# captures of one stage launch on the levels 4..8 wave case; None whenever the kernel changes
 STAGE_DRAM_BYTES_PER_NODE_STAGE = 117.5
 STAGE_DRAM_BYTES_PER_NODE_STAGE_MIXED = 74.3
 
@@ -284,7 +284,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-threads", type=int, default=0,
                     help="host threads of the oracle in the reference arm (default: all cores)")
-    ap.add_argument("--gts", action="store_true", help="also time GTS over the same physical time")
+    ap.add_argument("--no-gts", action="store_true",
+                    help="skip the GTS comparison (GTS over the same physical time, and the LTS-GTS difference)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--batch", type=int, default=0, help="batched mode: number of instances (64 for the C4 workload)")
     ap.add_argument("--rounds", type=int, default=64, help="batched mode: timed rounds")
@@ -405,11 +406,14 @@ def main():
     e2e_value = world * e2e_steps * schedule_work(st, 0, nsub) / e2e_s if e2e_steps else None
     state_bytes = host.nbytes
 
-    # GTS over the same physical time (2^L global steps per macro step)
+    # GTS (Alg. 1) over the same physical time: 2^L global steps of dt_f per macro step,
+    # timed like the LTS steps; then the difference of the two solutions after one macro
+    # step from the same initial data (LTS's interface error against GTS at equal dt_f)
     gts = None
-    if args.gts:
+    if not args.no_gts:
         plan.set_initial(0.0)
         plan.gts_steps(2)
+        plan.set_initial(0.0)
         torch.cuda.synchronize()
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         g0.record(stream)
@@ -420,8 +424,18 @@ def main():
         # LTS: the timed steps; GTS: nsub global steps of dt_f (the same physical time
         # per step when a step is a macro step)
         gts = {"ms_per_step": gms, "lts_ms_per_step": ms / args.steps, "steps_of_dt_finest": nsub,
-               "lts_speedup_measured": gms / (ms / args.steps), "lts_speedup_model": st["model_speedup"]}
-        if nsub != 2 ** L:
+               "lts_speedup_measured": gms / (ms / args.steps), "lts_speedup_model": st["model_speedup"],
+               "gts_node_updates_per_s": world * st["gts_work_per_macro"] * 343 * (nsub / 2 ** L) / (gms / 1e3)}
+        if nsub == 2 ** L:
+            u_g = plan.get_state(out)
+            plan.set_initial(0.0)
+            plan.run_substeps(nsub)
+            u_l = plan.get_state(host)
+            gts["lts_minus_gts_rel_linf"] = max(float(np.abs(u_l[f] - u_g[f]).max() / np.abs(u_g[f]).max())
+                                                for f in range(st["nf"]))
+            gts["lts_minus_gts_note"] = ("after one macro step from the same initial data, per field relative "
+                                         "to the field's max, the larger of the two")
+        else:
             gts["note"] = ("a step is %d of the %d substeps of a macro step: the LTS window also holds the "
                            "coarse levels' steps of substep 0 when it starts a macro step" % (nsub, 2 ** L))
 

@@ -205,7 +205,9 @@ lts_status lts_export_node_map(lts_plan* plan, const int32_t* octs, int64_t n, i
  * call shares the array and overwrites what the last call left there; calls whose
  * GPU work overlaps (other threads, other plans, other streams) race on it.  The
  * octant list, src[n][2197] and r[n][2197][3] are host buffers as above; the call
- * synchronises the plan's stream. */
+ * synchronises the plan's stream.  The device current at the call must be the one
+ * that was current when the plan was created (else LTS_EINVAL), since the array's
+ * address differs per device. */
 lts_status lts_export_pad_map_static(lts_plan* plan, const int32_t* octs, int64_t n, int32_t* src, int32_t* r);
 
 /* Octree-to-block decomposition (Sec. 3.2.5).  With blocking on (the default), every
@@ -224,7 +226,11 @@ lts_status lts_set_blocking(lts_plan* plan, int on);
 /* When on, every stage-kernel launch is bracketed by CUDA events on the plan's
  * stream; lts_kernel_stats synchronises and reports, since the last reset, the
  * number of stage launches, their summed device time (ms), and the algorithmic
- * FP64 flops and HBM bytes of those launches (per-node figures of the design notes). */
+ * flops and HBM bytes of those launches.  Per node-stage: wave 59 flops (both fields,
+ * FMA = 2), advection 45; per node-stage and field 38 bytes in FP64 (own stage input,
+ * step-start state and stage, 8 each; the next stage input, 6 over the stages; the
+ * update's share, 8) and 24 in mixed precision (the same arrays with FP32 stages).
+ * Gathers of neighbours' values are not counted (they are expected to hit L2). */
 lts_status lts_set_profiling(lts_plan* plan, int on);
 lts_status lts_kernel_stats(lts_plan* plan, int64_t* launches, double* ms, double* flops, double* bytes,
                             int64_t* node_stages, int reset);

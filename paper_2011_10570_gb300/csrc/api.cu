@@ -88,6 +88,7 @@ struct lts_plan {
   int64_t launches = 0;               // every kernel launched by the plan
   size_t bytes = 0;
   cudaStream_t stream = nullptr;
+  int device = -1;                      // CUDA device current when the plan was created
   std::vector<void*> allocations;
   bool profiling = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
@@ -653,6 +654,10 @@ lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_
   P->prob = *prob;
   P->spec = tree->spec;
   P->stream = static_cast<cudaStream_t>(prob->stream);
+  if (cudaGetDevice(&P->device) != cudaSuccess) {
+    delete P;
+    return fail(LTS_ECUDA, "lts_plan_create: cudaGetDevice failed");
+  }
   P->scheme = prob->rk == 4 ? 0 : 1;
   ltsoct::Tables rk4, rk3;
   ltsoct::make_tables(4, &rk4);
@@ -1109,6 +1114,12 @@ lts_status lts_export_pad_map_static(lts_plan* P, const int32_t* octs, int64_t n
   for (int64_t i = 0; i < n; ++i)
     if (octs[i] < 0 || octs[i] >= P->N) return fail(LTS_EINVAL, "lts_export_pad_map_static: octant index out of range");
   if (!n) return LTS_OK;
+  // the staging array's address is per device: take it on the plan's device only
+  int cur = -1;
+  CK(cudaGetDevice(&cur), "cudaGetDevice");
+  if (cur != P->device)
+    return fail(LTS_EINVAL, "lts_export_pad_map_static: the current device (" + std::to_string(cur) +
+                                ") is not the plan's device (" + std::to_string(P->device) + ")");
   int* scratch = nullptr;
   CK(ltsoct::static_map_scratch(&scratch), "lts_export_pad_map_static: staging area address");
   const int K = ltsoct::kStaticMapOctants;
