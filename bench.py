@@ -201,6 +201,7 @@ def run_batch(args):
         p.set_initial(0.0)
     batch = ltsoct.Batch(plans)
     tune = batch.autotune(rounds=4)
+    batch.wait()
     rounds = args.rounds
     for p in plans:
         p.set_initial(0.0)
@@ -215,6 +216,7 @@ def run_batch(args):
         batch.run([rounds] * len(plans), graph=True)
         ev1.record(stream)
         torch.cuda.synchronize()
+    batch.wait()
     ms = ev0.elapsed_time(ev1)
     launches = batch.stats()["launches"] - l0
     # the same work one instance at a time (per-plan launches, no batching)
@@ -238,7 +240,9 @@ def run_batch(args):
                    "octants_min": min(n_oct),
                    "octants_median": int(np.median(n_oct)), "octants_max": max(n_oct),
                    "levels": "3..6-11", "step": "one round: one substep of every instance"},
-        "gpu_launches": launches, "graph": True, "autotuned_grid": tune["grid"],
+        "gpu_launches": launches, "graph": True,
+        "autotuned": {"mode": tune["mode"], "shape": tune["shape"],
+                      "candidates_s": [[m, sh, round(t, 5)] for m, sh, t in tune["table"]]},
         "one_at_a_time": {"value": work / (ms_alone / 1e3), "ms_per_step": ms_alone / rounds},
         "batch_speedup": ms_alone / ms, "clocks": clk.summary(),
     }
@@ -342,8 +346,14 @@ def main():
     build.build()
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
-    tree = ltsoct.Octree(w["spec"])
+    ltsoct.Octree(workloads.advection_gauss(l_min=2, l_max=3)["spec"])   # the build's kernels loaded
+    torch.cuda.synchronize()
+    t_tree = time.perf_counter()
+    tree = ltsoct.Octree(w["spec"])            # refinement, 2:1 balance and o2o on the device
+    t_plan = time.perf_counter()
     plan = ltsoct.Plan(tree, w["prob"], stream=stream)
+    torch.cuda.synchronize()
+    t_ready = time.perf_counter()
     st = plan.stats()
     n = st["n_octants"]
     L = st["l_max"] - st["l_min"]
@@ -453,6 +463,9 @@ def main():
                 "d2h_bytes_per_step": state_bytes},
         "clocks": clk.summary(),
         "lts_model_speedup": st["model_speedup"],
+        "setup_s": {"octree_build": round(t_plan - t_tree, 4), "plan_create": round(t_ready - t_plan, 4),
+                    "note": "octree_build: refinement, 2:1 balance, level order and o2o on the device, leaves "
+                            "and o2o copied to the host; plan_create: tables, padding and node maps"},
     }
     if nsub == 2 ** L:
         # useful work at GTS's count (every octant at dt_f) per LTS wall second

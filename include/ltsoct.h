@@ -237,13 +237,19 @@ lts_status lts_kernel_stats(lts_plan* plan, int64_t* launches, double* ms, doubl
 
 /* ---- batches: many independent solves advanced together (NEXT-2) ------------------ */
 /* A batch advances several plans together in rounds: in each round every plan with
- * substeps left performs one LTS substep of its own schedule (Alg. 2, Fig. blk_loop);
- * each RK stage of a round is one persistent launch (a fixed grid looping over the
- * active octants of all plans) of the prolongation and of the stage kernels, and the
- * schedule is advanced on the device, so a round is a fixed launch sequence that can be
- * captured once in a CUDA graph and replayed.  Results equal those of running each
- * plan alone.  The plans must share one stream and one precision; the batch keeps
- * pointers to them (they must outlive it).  Up to 1024 plans. */
+ * substeps left performs one LTS substep of its own schedule (Alg. 2, Fig. blk_loop),
+ * and the schedule is advanced on the device, so a round is a fixed launch sequence that
+ * can be captured once in a CUDA graph and replayed.  Two modes (lts_batch_set_mode):
+ *   persistent (the default): the whole round is one cooperative launch whose CTAs stay
+ *     resident and claim work items (the prolongations and octant-stages of all plans,
+ *     stage by stage, then the reconciles) between grid-wide barriers; every barrier
+ *     wait has a time limit (2 s), past which the launch is abandoned and the next
+ *     lts_batch_wait returns LTS_ETIMEOUT;
+ *   per-stage: each RK stage is a launch of the prolongation and one of the stage
+ *     kernel over all plans, with round start / end and reconcile launches around them.
+ * Results equal those of running each plan alone, in either mode.  The plans must share
+ * one stream and one precision; the batch keeps pointers to them (they must outlive
+ * it).  Up to 1024 plans. */
 typedef struct lts_batch lts_batch;
 lts_status lts_batch_create(lts_plan* const* plans, int n, lts_batch** out);
 /* An empty batch of n_slots slots on `stream` (cudaStream_t) for plans of one precision
@@ -258,8 +264,23 @@ void lts_batch_destroy(lts_batch* batch);
  * 0 for empty slots), in max(substeps) rounds.  use_graph: replay one captured round.
  * Asynchronous on the plans' stream. */
 lts_status lts_batch_run(lts_batch* batch, const int64_t* substeps, int use_graph);
-/* Grid sizes of the persistent launches (CTAs); set by an autotuner or by hand. */
+/* Grid sizes (CTAs) of the per-stage launches; set by an autotuner or by hand. */
 lts_status lts_batch_set_grid(lts_batch* batch, int grid_stage, int grid_prolong, int grid_sync);
+/* persistent = 1: one cooperative launch per round with ctas_per_sm CTAs on every SM (at
+ * most what the round kernel keeps resident; more: LTS_EINVAL); persistent = 0: the
+ * per-stage launches.  Drops the captured round. */
+lts_status lts_batch_set_mode(lts_batch* batch, int persistent, int ctas_per_sm);
+/* Waits for the batch's rounds and reports a device-side failure: LTS_ETIMEOUT if a grid
+ * barrier of a persistent round waited past its limit (the round was abandoned part way:
+ * the plans' states are then undefined; the error word is cleared). */
+lts_status lts_batch_wait(lts_batch* batch);
+/* Test of the barrier's time limit: one launch of the grid barrier alone over one CTA
+ * per SM, limit_s seconds per wait (0 < limit_s <= 60).  absent_cta in [0, SMs) makes
+ * that CTA leave without arriving, so the others' waits run out: LTS_ETIMEOUT; -1: every
+ * CTA arrives, LTS_OK.  Synchronises the batch's stream. */
+lts_status lts_batch_probe_barrier(lts_batch* batch, int absent_cta, double limit_s);
+/* launches: kernels launched by the batch's rounds so far; grid_stage: the grid of the
+ * current mode's stage work (the persistent launch's, in persistent mode). */
 lts_status lts_batch_stats(const lts_batch* batch, int64_t* launches, int* grid_stage, int* grid_prolong,
                            int* grid_sync);
 

@@ -40,7 +40,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-lineinfo"]
     jobs = []
     objs = []
-    for src in ("kernels.cu", "api.cu"):
+    for src in ("kernels.cu", "api.cu", "octree.cu"):
         obj = os.path.join(BUILD, src + ".o")
         cmd = [nvcc, *ARCH, *common, "-Xptxas", "-v" if verbose else "-O3", "-c", os.path.join(CSRC, src), "-o", obj]
         jobs.append(cmd)

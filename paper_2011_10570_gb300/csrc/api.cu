@@ -67,7 +67,7 @@ struct lts_plan {
   int* d_up_slot = nullptr;
   void* d_up = nullptr;                 // prolonged stage inputs [slot][nf][2197], stage type
   int* d_err = nullptr;
-  unsigned* d_padmap = nullptr;  // [N][2197] padding map, built once by padmap_kernel
+  unsigned char* d_padmap = nullptr;  // [N][2197] padding map (source slots), built once by padmap_kernel
   // compact shared-node maps (zip: copied nodes; hanging: interpolated nodes, per level)
   int* d_zl_dst = nullptr;
   int* d_zl_src = nullptr;
@@ -399,8 +399,14 @@ ltsoct::StageArgs stage_args(const lts_plan* P, int stage, int first, int lstar,
     a.cf.lc[l][2] = float(a.lc[l].inv12h2);
     a.cf.dt[l] = float(a.lc[l].dt);
   }
+  for (int l = 0; l < 32; ++l)
+    for (int q = 0; q < 4; ++q) {
+      a.dtw.next[l][q] = q < a.next.n ? a.lc[l].dt * a.next.w[q] : 0.0;
+      a.dtw.upd[l][q] = q < P->p ? a.lc[l].dt * a.w[q] : 0.0;
+      a.cf.dtw_next[l][q] = float(a.dtw.next[l][q]);
+      a.cf.dtw_upd[l][q] = float(a.dtw.upd[l][q]);
+    }
   for (int q = 0; q < 4; ++q) {
-    a.cf.next_w[q] = float(a.next.w[q]);
     a.cf.w[q] = float(a.w[q]);
     a.cf.orb[q] = float(a.orb[q]);
   }
@@ -539,9 +545,10 @@ lts_status gts_step(lts_plan* P) {
   ua.n = int(P->N);
   ua.oct = P->d_oct;
   ua.cur_mask = P->cur_mask;
-  ua.dt_f = P->dt_f;
-  ua.dt_ff = float(P->dt_f);
-  for (int q = 0; q < 4; ++q) ua.wf[q] = float(P->tab.w[q]);
+  for (int q = 0; q < 4; ++q) {
+    ua.dtw[q] = q < P->p ? P->dt_f * P->tab.w[q] : 0.0;
+    ua.dtwf[q] = float(ua.dtw[q]);
+  }
   CK(ltsoct::launch_update(ua, P->stream), "update kernel launch");
   P->launches++;
   for (int l = P->lmin; l <= P->lmax; ++l) P->cur_mask ^= 1u << l;
@@ -606,12 +613,20 @@ lts_status octree_build(const lts_refine_spec* spec, lts_octree** out) {
   if (!spec || !out) return fail(LTS_EINVAL, "octree_build: null argument");
   *out = nullptr;
   try {
+    const lts_refine_spec& sp = *spec;
+    if (!(sp.hi > sp.lo) || sp.l_min < 0 || sp.l_max < sp.l_min || sp.l_max > ltsoct::kMaxLevel || sp.kind < 0 ||
+        sp.kind > 3 || ((sp.kind == 0 || sp.kind == 3) && (sp.n_centers < 1 || sp.n_centers > 8)) ||
+        (sp.kind == 3 && !(sp.band > 0.0 && sp.eps > 0.0)))
+      return fail(LTS_EINVAL,
+                  "octree_build: invalid refinement spec (need lo < hi, 0 <= l_min <= l_max <= 18, kind 0..3, 1..8 "
+                  "centers; kind 3: band > 0, eps > 0)");
     auto* t = new lts_octree();
-    t->spec = *spec;
+    t->spec = sp;
     std::string err;
-    if (!ltsoct::build_octree(*spec, &t->leaves, &err)) {
+    const lts_status st = ltsoct::device_octree(sp, &t->leaves, &t->nb, &err);
+    if (st != LTS_OK) {
       delete t;
-      return fail(LTS_EINVAL, err);
+      return fail(st, err);
     }
     *out = t;
     return LTS_OK;
@@ -681,12 +696,7 @@ lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_
     P->lmax = std::max(P->lmax, int(o.l));
   }
   for (int l = 0; l <= 32; ++l) P->off[l + 1] = P->off[l] + P->count[l];
-  std::string err;
-  lts_status st = ltsoct::build_neighbours(P->octs, &P->nb, &err);
-  if (st != LTS_OK) {
-    delete P;
-    return fail(st, err);
-  }
+  P->nb = tree->nb;
   // octants with a coarser neighbour carry hanging nodes
   for (int64_t b = 0; b < P->N; ++b) {
     bool h = false;
@@ -802,7 +812,7 @@ lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_
   P->d_up_box = static_cast<int*>(dev_alloc(P, sizeof(int) * nup));
   P->d_up_slot = static_cast<int*>(dev_alloc(P, sizeof(int) * P->N));
   P->d_up = dev_alloc(P, P->es * nup * P->nf * ltsoct::kNT);
-  P->d_padmap = static_cast<unsigned*>(dev_alloc(P, sizeof(unsigned) * size_t(P->N) * ltsoct::kNT));
+  P->d_padmap = static_cast<unsigned char*>(dev_alloc(P, size_t(P->N) * ltsoct::kNT));
   const size_t ng = std::max<size_t>(P->grp.size(), 1);
   P->d_grp = static_cast<int*>(dev_alloc(P, sizeof(int) * ng));
   P->d_single = static_cast<int*>(dev_alloc(P, sizeof(int) * std::max<size_t>(P->single.size(), 1)));
@@ -867,7 +877,7 @@ lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_
     delete P;
     return fail(LTS_EINTERNAL, "lts_plan_create: padding map: a source lay outside its octant (unbalanced tree)");
   }
-  st = build_node_maps(P);
+  const lts_status st = build_node_maps(P);
   if (st != LTS_OK) {
     release(P);
     delete P;
@@ -962,7 +972,10 @@ static lts_status check_device_error(lts_plan* P) {
   int h = 0;
   CK(cudaMemcpyAsync(&h, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, P->stream), "error word read");
   CK(cudaStreamSynchronize(P->stream), "cudaStreamSynchronize");
-  if (h) return fail(LTS_EINTERNAL, "device guard: a padding source lay outside its octant (code " + std::to_string(h) + ")");
+  if (h)
+    return fail(LTS_EINTERNAL, "device guard (code " + std::to_string(h) +
+                                   "): bit 0 a padding source lay outside its octant, bit 1 a coarser source had no "
+                                   "prolonged inputs");
   return LTS_OK;
 }
 
@@ -1203,16 +1216,32 @@ struct lts_batch {
   cudaGraphExec_t exec = nullptr;
   int64_t launches = 0;
   bool slots = false;                // created empty with fixed capacity (attach / detach)
+  // persistent rounds: one cooperative launch per round over `grid_persistent` CTAs
+  int persistent = 1;
+  int grid_persistent = 0;           // resident CTAs (set at creation from the occupancy)
+  int resident_max = 0;              // CTAs per SM x SMs the persistent kernel can keep resident
+  int sms = 0;
+  unsigned* d_sync = nullptr;        // [0..1] grid barrier (count, generation), [2] error word
+  double barrier_limit_s = 2.0;      // a CTA waiting longer at a grid barrier ends the launch
 };
 
 namespace {
+
+// one round's launches: the persistent round kernel, or the per-stage launch sequence
+cudaError_t launch_round(lts_batch* B) {
+  if (B->persistent)
+    return ltsoct::launch_batch_substep(B->args, B->pmax, B->lmax_all, B->grid_persistent, B->mixed, B->d_sync,
+                                        reinterpret_cast<int*>(B->d_sync + 2),
+                                        static_cast<unsigned long long>(B->barrier_limit_s * 1e9), B->cap);
+  return ltsoct::launch_batch_round(B->args, B->pmax, B->lmax_all, B->grid_stage, B->grid_prolong, B->grid_sync,
+                                    B->mixed, B->cap);
+}
 
 lts_status batch_round(lts_batch* B, bool graph) {
   if (graph) {
     if (!B->exec) {
       CK(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
-      cudaError_t e = ltsoct::launch_batch_round(B->args, B->pmax, B->lmax_all, B->grid_stage, B->grid_prolong,
-                                                 B->grid_sync, B->mixed, B->cap);
+      cudaError_t e = launch_round(B);
       cudaGraph_t g = nullptr;
       cudaError_t e2 = cudaStreamEndCapture(B->cap, &g);
       if (e != cudaSuccess) return cuda_fail(e, "batch round capture");
@@ -1222,12 +1251,21 @@ lts_status batch_round(lts_batch* B, bool graph) {
     }
     CK(cudaGraphLaunch(B->exec, B->cap), "cudaGraphLaunch");
   } else {
-    CK(ltsoct::launch_batch_round(B->args, B->pmax, B->lmax_all, B->grid_stage, B->grid_prolong, B->grid_sync,
-                                  B->mixed, B->cap),
-       "batch round launch");
+    CK(launch_round(B), "batch round launch");
   }
-  B->launches += 3 + 2 * B->pmax + B->lmax_all;
+  B->launches += B->persistent ? 1 : 3 + 2 * B->pmax + B->lmax_all;
   return LTS_OK;
+}
+
+void drop_graph(lts_batch* B) {
+  if (B->exec) {
+    cudaGraphExecDestroy(B->exec);
+    B->exec = nullptr;
+  }
+  if (B->graph) {
+    cudaGraphDestroy(B->graph);
+    B->graph = nullptr;
+  }
 }
 
 // the host's copy of a plan's schedule, advanced by n substeps (the same arithmetic
@@ -1317,8 +1355,15 @@ lts_status batch_alloc(lts_batch* B, int n_slots) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(B->d_inst, empty.data(), sizeof(ltsoct::BatchInst) * n_slots, cudaMemcpyHostToDevice, B->cap);
   if (e == cudaSuccess) e = cudaMemsetAsync(B->d_pre, 0, sizeof(int) * pre_ints, B->cap);
+  if (e == cudaSuccess) e = cudaMalloc(&B->d_sync, 4 * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemsetAsync(B->d_sync, 0, 4 * sizeof(unsigned), B->cap);
   if (e == cudaSuccess) e = cudaStreamSynchronize(B->cap);
+  int per_sm = 0;
+  if (e == cudaSuccess) e = ltsoct::batch_substep_resident(B->mixed, &per_sm, &B->sms);
   if (e != cudaSuccess) return cuda_fail(e, "batch allocation");
+  B->resident_max = per_sm * B->sms;
+  B->grid_persistent = B->resident_max;
+  B->persistent = B->resident_max > 0 ? 1 : 0;
   B->plans.assign(n_slots, nullptr);
   B->args.inst = B->d_inst;
   B->args.n = n_slots;
@@ -1415,6 +1460,7 @@ void lts_batch_destroy(lts_batch* B) {
   if (B->cap) cudaStreamDestroy(B->cap);
   if (B->d_inst) cudaFree(B->d_inst);
   if (B->d_pre) cudaFree(B->d_pre);
+  if (B->d_sync) cudaFree(B->d_sync);
   delete B;
 }
 
@@ -1423,15 +1469,50 @@ lts_status lts_batch_set_grid(lts_batch* B, int grid_stage, int grid_prolong, in
   B->grid_stage = grid_stage;
   B->grid_prolong = grid_prolong;
   B->grid_sync = grid_sync;
-  if (B->exec) {
-    cudaGraphExecDestroy(B->exec);
-    B->exec = nullptr;
+  drop_graph(B);
+  return LTS_OK;
+}
+
+lts_status lts_batch_set_mode(lts_batch* B, int persistent, int ctas_per_sm) {
+  if (!B || (persistent != 0 && persistent != 1)) return fail(LTS_EINVAL, "lts_batch_set_mode: bad argument");
+  if (persistent) {
+    if (ctas_per_sm < 1 || ctas_per_sm * B->sms > B->resident_max)
+      return fail(LTS_EINVAL, "lts_batch_set_mode: " + std::to_string(ctas_per_sm) +
+                                  " CTAs per SM; the persistent round kernel keeps at most " +
+                                  std::to_string(B->sms ? B->resident_max / B->sms : 0) + " resident");
+    B->grid_persistent = ctas_per_sm * B->sms;
   }
-  if (B->graph) {
-    cudaGraphDestroy(B->graph);
-    B->graph = nullptr;
+  B->persistent = persistent;
+  drop_graph(B);
+  return LTS_OK;
+}
+
+lts_status lts_batch_wait(lts_batch* B) {
+  if (!B) return fail(LTS_EINVAL, "lts_batch_wait: null batch");
+  unsigned w[4] = {0, 0, 0, 0};
+  CK(cudaStreamSynchronize(B->cap), "cudaStreamSynchronize");
+  CK(cudaMemcpy(w, B->d_sync, sizeof(w), cudaMemcpyDeviceToHost), "error word read");
+  if (w[2] & unsigned(ltsoct::kErrTimeout)) {
+    CK(cudaMemset(B->d_sync, 0, sizeof(w)), "error word reset");
+    return fail(LTS_ETIMEOUT, "lts_batch_wait: a grid barrier of a persistent round waited longer than " +
+                                  std::to_string(B->barrier_limit_s) + " s; the round was abandoned");
   }
   return LTS_OK;
+}
+
+lts_status lts_batch_probe_barrier(lts_batch* B, int absent_cta, double limit_s) {
+  if (!B || !(limit_s > 0.0) || limit_s > 60.0 || absent_cta < -1 || absent_cta >= B->sms)
+    return fail(LTS_EINVAL, "lts_batch_probe_barrier: bad argument");
+  CK(cudaStreamSynchronize(B->cap), "cudaStreamSynchronize");
+  CK(cudaMemset(B->d_sync, 0, 4 * sizeof(unsigned)), "barrier reset");
+  CK(ltsoct::launch_barrier_probe(B->sms, B->d_sync, reinterpret_cast<int*>(B->d_sync + 2),
+                                  static_cast<unsigned long long>(limit_s * 1e9), absent_cta, B->cap),
+     "barrier probe launch");
+  const double keep = B->barrier_limit_s;
+  B->barrier_limit_s = limit_s;
+  lts_status st = lts_batch_wait(B);
+  B->barrier_limit_s = keep;
+  return st;
 }
 
 lts_status lts_batch_run(lts_batch* B, const int64_t* substeps, int use_graph) {
@@ -1474,7 +1555,7 @@ lts_status lts_batch_run(lts_batch* B, const int64_t* substeps, int use_graph) {
 lts_status lts_batch_stats(const lts_batch* B, int64_t* launches, int* grid_stage, int* grid_prolong, int* grid_sync) {
   if (!B) return fail(LTS_EINVAL, "lts_batch_stats: null batch");
   if (launches) *launches = B->launches;
-  if (grid_stage) *grid_stage = B->grid_stage;
+  if (grid_stage) *grid_stage = B->persistent ? B->grid_persistent : B->grid_stage;
   if (grid_prolong) *grid_prolong = B->grid_prolong;
   if (grid_sync) *grid_sync = B->grid_sync;
   return LTS_OK;

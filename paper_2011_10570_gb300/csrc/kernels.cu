@@ -55,6 +55,7 @@ __device__ unsigned short g_bnode[kBN];
 // 8-byte loads, but the FP64 kernel, bound by its FP64 pipe, measured no gain from it.)
 __device__ short g_rhs_node[kThreads];
 
+
 cudaError_t upload_tables(const Tables* rk4, const Tables* rk3, const double W[13][7], const double E[4][4]) {
   {
     unsigned short bn[kBN];
@@ -228,12 +229,25 @@ __device__ void load_neighbours(const DevTree& t, int b, NbrView& nv) {
 // stage input of a source node from its step-start state and RK stages,
 // u + dt * sum_t w_t K_(j_t), in FP64 (eq. rk_schemes with the corrected weights
 // of eqs. fc_1 / fc_2)
-template <typename R>
+//
+// C selects the load path: false, the read-only data path (data written by earlier
+// launches); true, loads through L2 (ld.global.cg) for data that the same launch may have
+// written (the persistent batch round, whose stages follow each other inside one launch).
+template <bool C, typename T>
+__device__ __forceinline__ T ld_in(const T* p) {
+  if constexpr (C) {
+    return __ldcg(p);
+  } else {
+    return __ldg(p);
+  }
+}
+
+template <typename R, bool C = false>
 __device__ __forceinline__ double corrected_value(const double* __restrict__ u, const R* __restrict__ k0,
                                                   long long kstride, const StageTerms& t, double dt) {
   double acc = 0.0;
-  for (int q = 0; q < t.n; ++q) acc = fma(t.w[q], static_cast<double>(__ldg(k0 + t.j[q] * kstride)), acc);
-  return fma(dt, acc, __ldg(u));
+  for (int q = 0; q < t.n; ++q) acc = fma(t.w[q], static_cast<double>(ld_in<C>(k0 + t.j[q] * kstride)), acc);
+  return fma(dt, acc, ld_in<C>(u));
 }
 
 // tensor-product Lagrange interpolation, x then y then z; even coordinates are nodes
@@ -311,29 +325,42 @@ __device__ __forceinline__ double lattice_to_x(double lo, double ext, int P6) {
 constexpr int kKindCoarser = 0, kKindSame = 1, kKindFiner = 2, kKindNone = 3;
 constexpr int kSlots = 256;  // slot values of a padding-map entry (kSlotNone = 255 included)
 
-template <int NF, typename R>
+// Shared memory of the stage kernel: NB tile buffers with their slot tables (the stage
+// kernel and the batch kernels use one).
+template <int NF, typename R, int NB>
 struct StageSmem {
-  R T[NF][kNT];               // padded tiles
-  StageTerms om[4];           // correction terms of this stage per relation
-  long long base[kSlots];     // per slot: element offset of its source in the array it is read from
-  unsigned char kind[kSlots]; // per slot: kKindCoarser / kKindSame / kKindFiner / kKindNone
+  R T[NB][NF][kNT];               // padded tiles
+  long long slot[NB][kSlots];     // per slot: base << 2 | kind (stage_slots)
+  StageTerms om[4];               // correction terms of this stage per relation
   R KV[sizeof(R) == sizeof(float) ? NF : 1][sizeof(R) == sizeof(float) ? kNV : 1];  // FP32: staged right-hand sides
-  R orb[2];                   // orbit centre x_1 at this octant's stage time
+  R orb[NB][2];                   // orbit centre x_1 at the octant's stage time
 };
 
 constexpr unsigned kExterior = 1u << 15;  // exterior flag of the 16-bit codes of the block map
 
-// padding-map entry: slot | off << 8 | rx << 20 | ry << 24 | rz << 28, with (rx, ry, rz)
-// the point's half-node coordinates in its source and off its element offset there
-// (rx + 13 ry + 169 rz in a coarser source's prolonged block, the node index otherwise)
-__device__ __forceinline__ unsigned pad_entry(unsigned slot, int rx, int ry, int rz, bool coarser) {
-  const unsigned off = coarser ? unsigned(rx + 13 * ry + 169 * rz) : unsigned((rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1));
-  return slot | off << 8 | unsigned(rx) << 20 | unsigned(ry) << 24 | unsigned(rz) << 28;
+// The padding map holds one byte per padded point: the slot of its source in the
+// octant's neighbour view (kSlotNone outside the domain).  Where the point lies in the
+// source follows from the slot's relation to the octant.  With (i, j, k) the point in
+// the octant's node units (each in [-3, 9]) and lin7 = i + 7 j + 49 k:
+//   same level, neighbour box d:        node (i, j, k) - 6 d           -> base + lin7
+//   finer, child c of the split box d:  node 2 (i, j, k) - 12 d - 6 c  -> base + 2 lin7
+//   coarser leaf N (its prolonged 13^3 block, half-node units of N):
+//                                       (i, j, k) + 6 (A_b - A_N) / e_b -> base + q
+// q being the point's tile index (i + 3) + 13 (j + 3) + 169 (k + 3); base is fixed per
+// slot and octant (stage_slots).
+__device__ __forceinline__ int lin7_of(int q) {
+  const int k = q / 169, rem = q - 169 * k;
+  const int j = rem / 13, i = rem - 13 * j;
+  return i + 7 * j + 49 * k - 171;  // (i, j, k) counted from -3: 3 + 7 * 3 + 49 * 3 = 171
 }
-__device__ __forceinline__ int pad_rx(unsigned e) { return int((e >> 20) & 15u); }
-__device__ __forceinline__ int pad_ry(unsigned e) { return int((e >> 24) & 15u); }
-__device__ __forceinline__ int pad_rz(unsigned e) { return int(e >> 28); }
-__device__ __forceinline__ unsigned pad_off(unsigned e) { return (e >> 8) & 4095u; }
+
+// element of point q in the source of its slot, from the slot's packed base << 2 | kind
+__device__ __forceinline__ long long slot_element(long long packed, int kind, int q) {
+  const long long base = packed >> 2;
+  return base + (kind == kKindCoarser ? q : (kind == kKindFiner ? 2 : 1) * lin7_of(q));
+}
+
+constexpr int kPer = (kNT + kThreads - 1) / kThreads;  // padded points per thread of a stage CTA
 
 // exterior padded point of octant (anchor me, edge eb): outside the domain
 __device__ __forceinline__ bool exterior_point(int4 me, int eb, int q) {
@@ -344,7 +371,7 @@ __device__ __forceinline__ bool exterior_point(int4 me, int eb, int q) {
 
 // exact boundary data (a reading of the paper): RK stage values of the closed-form solution
 template <int NF, typename R>
-__device__ __noinline__ void fill_exact(StageSmem<NF, R>& S, const StageArgs& A, int4 me, int eb, double dtb) {
+__device__ __noinline__ void fill_exact(R (*T)[kNT], const StageArgs& A, int4 me, int eb, double dtb) {
   for (int q = threadIdx.x; q < kNT; q += blockDim.x) {
     if (!exterior_point(me, eb, q)) continue;
     const int i = q % 13 - 3, j = (q / 13) % 13 - 3, k = q / 169 - 3;
@@ -359,14 +386,14 @@ __device__ __noinline__ void fill_exact(StageSmem<NF, R>& S, const StageArgs& A,
         dtp *= dtb;
         v = fma(A.gamma[m] * dtp, d[f][m + 1], v);
       }
-      S.T[f][q] = static_cast<R>(v);
+      T[f][q] = static_cast<R>(v);
     }
   }
 }
 
 // radiative boundary (a reading of the paper): cubic extrapolation along the outward normal, x then y then z
 template <int NF, typename R>
-__device__ __noinline__ void fill_extrapolated(StageSmem<NF, R>& S, int4 me, int eb) {
+__device__ __noinline__ void fill_extrapolated(R (*T)[kNT], int4 me, int eb) {
   const int anchor[3] = {me.x, me.y, me.z};
   constexpr int kRoot = 1 << kDepth;
   for (int a = 0; a < 3; ++a) {
@@ -386,13 +413,13 @@ __device__ __noinline__ void fill_extrapolated(StageSmem<NF, R>& S, int4 me, int
         for (int f = 0; f < NF; ++f) {
           if (lo_b) {
             R v = 0;
-            for (int qq = 0; qq < 4; ++qq) v = fma(R(c_E[m][qq]), S.T[f][base + qq * str], v);
-            S.T[f][base - m * str] = v;
+            for (int qq = 0; qq < 4; ++qq) v = fma(R(c_E[m][qq]), T[f][base + qq * str], v);
+            T[f][base - m * str] = v;
           }
           if (hi_b) {
             R v = 0;
-            for (int qq = 0; qq < 4; ++qq) v = fma(R(c_E[m][qq]), S.T[f][base + (6 - qq) * str], v);
-            S.T[f][base + (6 + m) * str] = v;
+            for (int qq = 0; qq < 4; ++qq) v = fma(R(c_E[m][qq]), T[f][base + (6 - qq) * str], v);
+            T[f][base + (6 + m) * str] = v;
           }
         }
       }
@@ -497,9 +524,10 @@ __device__ __forceinline__ void async_wait_all() { asm volatile("cp.async.wait_a
 
 // Stage epilogue of one node-field (o its index in the field arrays): the next stage's
 // input u + dt sum_j a[s+1][j] k_j, or after the last stage the new state
-// u + dt sum_j w_j k_j.  FP64: all in FP64.  Mixed: the stage input in FP32 from the
-// FP32 copy of u; the new state accumulates the FP32 increment dt sum_j w_j k_j into
-// FP64 u (and refreshes the FP32 copy).
+// u + dt sum_j w_j k_j, with the products dt a[s+1][j] and dt w_j of the octant's level
+// formed on the host (StageArgs::dtw).  FP64: all in FP64, one FMA per term.  Mixed: the
+// stage input in FP32 from the FP32 copy of u; the new state accumulates the FP32
+// increment sum_j (dt w_j) k_j into FP64 u (and refreshes the FP32 copy).
 struct EpilogueOut {
   double unew;
   double uin_d;
@@ -509,35 +537,34 @@ struct EpilogueOut {
 
 template <typename R>
 __device__ __forceinline__ EpilogueOut stage_epilogue(const StageArgs& A, const R* K, long long kstride, long long o,
-                                                      R kvf, const double* u0, const float* us0, double dt, float dtf,
-                                                      int s, int p) {
+                                                      R kvf, const double* u0, const float* us0, int lb, int s,
+                                                      int p) {
   EpilogueOut out{0.0, 0.0, 0.0f, 0.0f};
   if constexpr (sizeof(R) == sizeof(double)) {
     const double kd = kvf;
     if (s < p - 1) {
-      double acc = 0.0;
+      double v = u0[o];
       for (int q = 0; q < A.next.n; ++q)
-        acc = fma(A.next.w[q], A.next.j[q] == s ? kd : static_cast<double>(K[(long long)A.next.j[q] * kstride + o]),
-                  acc);
-      out.uin_d = fma(dt, acc, u0[o]);
+        v = fma(A.dtw.next[lb][q],
+                A.next.j[q] == s ? kd : static_cast<double>(K[(long long)A.next.j[q] * kstride + o]), v);
+      out.uin_d = v;
     } else if (A.write_update) {
-      double acc = 0.0;
-      for (int q = 0; q < p - 1; ++q) acc = fma(A.w[q], static_cast<double>(K[(long long)q * kstride + o]), acc);
-      acc = fma(A.w[p - 1], kd, acc);
-      out.unew = fma(dt, acc, u0[o]);
+      double v = u0[o];
+      for (int q = 0; q < p - 1; ++q) v = fma(A.dtw.upd[lb][q], static_cast<double>(K[(long long)q * kstride + o]), v);
+      out.unew = fma(A.dtw.upd[lb][p - 1], kd, v);
     }
   } else {
     if (s < p - 1) {
-      float acc = 0.0f;
+      float v = us0[o];
       for (int q = 0; q < A.next.n; ++q)
-        acc = fmaf(A.cf.next_w[q], A.next.j[q] == s ? float(kvf) : float(K[(long long)A.next.j[q] * kstride + o]),
-                   acc);
-      out.uin_f = fmaf(dtf, acc, us0[o]);
+        v = fmaf(A.cf.dtw_next[lb][q], A.next.j[q] == s ? float(kvf) : float(K[(long long)A.next.j[q] * kstride + o]),
+                 v);
+      out.uin_f = v;
     } else if (A.write_update) {
       float acc = 0.0f;
-      for (int q = 0; q < p - 1; ++q) acc = fmaf(A.cf.w[q], float(K[(long long)q * kstride + o]), acc);
-      acc = fmaf(A.cf.w[p - 1], float(kvf), acc);
-      out.unew = u0[o] + static_cast<double>(dtf * acc);
+      for (int q = 0; q < p - 1; ++q) acc = fmaf(A.cf.dtw_upd[lb][q], float(K[(long long)q * kstride + o]), acc);
+      acc = fmaf(A.cf.dtw_upd[lb][p - 1], float(kvf), acc);
+      out.unew = u0[o] + static_cast<double>(acc);
       out.unew_s = static_cast<float>(out.unew);
     }
   }
@@ -574,133 +601,187 @@ __device__ __noinline__ R wave_source(const StageArgs& A, const int P6[3], R chi
   return src;
 }
 
-// One RK stage of octant b (Alg. 2 compute_stage, or Alg. 1 when A.gts): called by
-// every thread of a CTA of TPB threads, with S in shared memory.
-template <int NF, typename R, int TPB>
-__device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int b) {
-  constexpr int kPer = (kNT + TPB - 1) / TPB;  // padded points per thread
+// the octant of work item `it` of a stage launch
+__device__ __forceinline__ int stage_item(const StageArgs& A, int it) {
+  return A.list ? __ldg(A.list + A.first + it) : A.first + it;
+}
+
+// padding-map bytes of this thread's points of octant b (points tid + r * kThreads),
+// four to a register
+constexpr int kSlw = (kPer + 3) / 4;
+struct Slots {
+  unsigned w[kSlw];
+  __device__ __forceinline__ unsigned operator[](int r) const { return (w[r >> 2] >> (8 * (r & 3))) & 255u; }
+};
+
+__device__ __forceinline__ void load_slots(const StageArgs& A, int b, Slots& sl) {
+  const unsigned char* __restrict__ pm = A.padmap + (long long)b * kNT;
+#pragma unroll
+  for (int i = 0; i < kSlw; ++i) sl.w[i] = 0u;
+#pragma unroll
+  for (int r = 0; r < kPer; ++r) {
+    const int q = threadIdx.x + r * kThreads;
+    const unsigned v = q < kNT ? unsigned(__ldg(pm + q)) : kSlotNone;
+    sl.w[r >> 2] |= v << (8 * (r & 3));
+  }
+}
+
+// One RK stage of an octant (Alg. 2 compute_stage, or Alg. 1 when A.gts), in four
+// phases over a tile buffer of the CTA:
+//   stage_slots    the octant's neighbour view: kind and base of every slot, from the tree
+//   stage_gather   the padded tile (Sec. 3.3, Fig. unzip): asynchronous copies of the
+//                  sources' stage inputs (coarser sources: their prolonged inputs)
+//   stage_finer    points with a finer source under LTS: injection with the time
+//                  correction of eq. fc_1 (FP64)
+//   stage_compute  physical boundary, right-hand side, RK stage and update
+// Between the phases the caller synchronises (stage_octant, stage_kernel).
+
+// Returns 1 if some slot holds a finer leaf.  No barrier inside.
+template <int NF, typename R, int NB>
+__device__ int stage_slots(StageSmem<NF, R, NB>& S, int nb, const StageArgs& A, int b, int4 me) {
+  const int lb = me.w;
+  const int sh = kDepth - lb;  // log2 of the octant's edge
+  int my_finer = 0;
+  for (int t = threadIdx.x; t < kSlots; t += blockDim.x) {
+    int kind = kKindNone;
+    long long base = 0;
+    if (t == 13) {
+      kind = kKindSame;
+      base = (long long)b * kNV;
+    } else if (t < 27) {
+      // the leaf covering the same-size box in direction d = t (same level or coarser),
+      // < 0: outside the domain, or a box with children
+      const int leaf = __ldg(A.tree.nbr + (long long)b * 27 + t);
+      if (leaf >= 0) {
+        const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
+        const int4 so = __ldg(A.tree.oct + leaf);
+        if (so.w == lb) {
+          kind = kKindSame;
+          base = (long long)leaf * kNV - 6 * (dx + 7 * dy + 49 * dz);
+        } else if (so.w == lb - 1) {
+          const int us = __ldg(A.up_slot + leaf);
+          if (us >= 0) {
+            kind = kKindCoarser;
+            const int mx = (me.x - so.x) >> sh, my = (me.y - so.y) >> sh, mz = (me.z - so.z) >> sh;
+            base = (long long)us * NF * kNT - 549 + 6 * (mx + 13 * my + 169 * mz);
+          } else {
+            atomicOr(A.err, 2);  // a coarser source without prolonged inputs: never on a valid plan
+          }
+        }
+      }
+    } else if (t < 27 + 27 * 8) {  // slots 243..255 hold no leaf
+      const int d = (t - 27) >> 3, c = (t - 27) & 7;
+      const int e = __ldg(A.tree.nbr + (long long)b * 27 + d);
+      const int leaf = e <= -2 ? __ldg(A.tree.fine + (long long)(-e - 2) * 8 + c) : -1;
+      if (leaf >= 0) {
+        const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+        const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+        kind = kKindFiner;
+        base = (long long)leaf * kNV - 6 * ((2 * dx + cx) + 7 * (2 * dy + cy) + 49 * (2 * dz + cz));
+        my_finer = 1;
+      }
+    }
+    S.slot[nb][t] = base * 4 + kind;
+  }
+  return my_finer;
+}
+
+// The tile's gathers into buffer nb: same-level (and own) sources read the stage
+// inputs, coarser sources their prolonged stage inputs (prepared by prolong_kernel),
+// and under GTS finer sources are read directly.  At stage 0 the stage input is the
+// state u itself.  Points outside the domain are zeroed (the boundary fill overwrites
+// them); points with a finer source under LTS are left to stage_finer.
+template <int NF, typename R, int NB>
+__device__ void stage_gather(StageSmem<NF, R, NB>& S, int nb, const StageArgs& A, int lb,
+                             const Slots& sl) {
+  const double* u0 = A.u[(A.cur_mask >> lb) & 1];
+  const float* us0 = A.us[(A.cur_mask >> lb) & 1];
+  const R* st_in = A.stage == 0 ? state_array<R>(u0, us0) : static_cast<const R*>(A.Uin);
+  const R* up_all = static_cast<const R*>(A.up);
+#pragma unroll
+  for (int r = 0; r < kPer; ++r) {
+    const int q = threadIdx.x + r * kThreads;
+    if (q >= kNT) break;
+    const long long packed = S.slot[nb][sl[r]];
+    const int kind = int(packed & 3);
+    if (kind == kKindCoarser) {
+      const R* up = up_all + slot_element(packed, kind, q);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) async_copy(&S.T[nb][f][q], up + f * kNT);
+    } else if (kind == kKindSame || (kind == kKindFiner && A.gts)) {
+      const R* src = st_in + slot_element(packed, kind, q);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) async_copy(&S.T[nb][f][q], src + f * A.fstride);
+    } else if (kind == kKindNone) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) S.T[nb][f][q] = 0;
+    }
+  }
+}
+
+// Points with a finer source (injection) under LTS, with the coarse <- fine correction of
+// eq. fc_1 applied to the source's step-start state and stages (FP64).
+template <int NF, typename R, int NB, bool C = false>
+__device__ void stage_finer(StageSmem<NF, R, NB>& S, int nb, const StageArgs& A, int lb,
+                            const Slots& sl) {
+  const int ls = lb + 1;
+  const double* ub = A.u[(A.cur_mask >> ls) & 1];
+  const R* K = static_cast<const R*>(A.K);
+  const long long kstride = (long long)A.nf * A.fstride;
+  const double dts = A.lc[ls].dt;
+#pragma unroll
+  for (int r = 0; r < kPer; ++r) {
+    const int q = threadIdx.x + r * kThreads;
+    if (q >= kNT) break;
+    const long long packed = S.slot[nb][sl[r]];
+    if (int(packed & 3) != kKindFiner) continue;
+    const long long off = slot_element(packed, kKindFiner, q);
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+      S.T[nb][f][q] =
+          static_cast<R>(corrected_value<R, C>(ub + f * A.fstride + off, K + f * A.fstride + off, kstride, S.om[1], dts));
+  }
+}
+
+// orbit centre x_1 = R (cos W t_s, sin W t_s, 0) at the stage time t_s = t_b + c_s dt of
+// level lb (one thread)
+template <typename R>
+__device__ __forceinline__ void orbit_centre(const StageArgs& A, int lb, R* out) {
+  double c, sn;
+  sincos(A.orb[1] * fma(A.c_s, A.lc[lb].dt, A.t_b), &sn, &c);
+  out[0] = R(A.orb[0] * c);
+  out[1] = R(A.orb[0] * sn);
+}
+
+// Physical boundary, right-hand side on the 7^3 interior (stage type R), and the stage,
+// next stage input and RK update of every node (stage_epilogue), from the complete tile
+// in buffer cb.  Barriers inside are uniform over the CTA.
+template <int NF, typename R, int NB>
+__device__ void stage_compute(StageSmem<NF, R, NB>& S, int cb, const StageArgs& A, const int b, const int4 me) {
   const int tid = threadIdx.x;
   const int p = A.p;
   const int s = A.stage;
-  const int4 me = A.tree.oct[b];
   const int lb = me.w;
   const int eb = 1 << (kDepth - lb);
   const long long kstride = (long long)A.nf * A.fstride;
   R* __restrict__ K = static_cast<R*>(A.K);
-
-  if (tid < 4) S.om[tid] = A.om[tid];
-  if (tid == 0 && A.orbit) {
-    // x_1 = R (cos W t_s, sin W t_s, 0) at the stage time t_s = t_b + c_s dt of this level
-    double c, sn;
-    sincos(A.orb[1] * fma(A.c_s, A.lc[lb].dt, A.t_b), &sn, &c);
-    S.orb[0] = R(A.orb[0] * c);
-    S.orb[1] = R(A.orb[0] * sn);
-  }
-
-  // 1. sources: the padding map gives every padded point its source (coarsest leaf
-  //    containing it, then smallest Morton key) as a slot of the neighbour view and an
-  //    element offset in that source; each slot's kind and base offset are resolved
-  //    here once per octant
-  const R* Uin = static_cast<const R*>(A.Uin);
   const double* u0 = A.u[(A.cur_mask >> lb) & 1];
   const float* us0 = A.us[(A.cur_mask >> lb) & 1];
-  const R* up_all = static_cast<const R*>(A.up);
-  const R* st_in = s == 0 ? state_array<R>(u0, us0) : Uin;
-  // The map entries are loaded first, all at once (their latency overlaps the slot
-  // table's): each copy's address depends on its entry, and the copies are ordered
-  // memory operations.
-  const unsigned* __restrict__ pm = A.padmap + (long long)b * kNT;
-  unsigned ev[kPer];
-#pragma unroll
-  for (int r = 0; r < kPer; ++r) ev[r] = tid + r * TPB < kNT ? __ldg(pm + tid + r * TPB) : kSlotNone;
-  int my_finer = 0;
-  for (int t = tid; t < kSlots; t += blockDim.x) {
-    // the leaf in slot t of the neighbour view (as slot_leaf), read from the tree directly
-    int leaf = -1;
-    if (t == 13) {
-      leaf = b;
-    } else if (t < 27) {
-      leaf = __ldg(A.tree.nbr + (long long)b * 27 + t);  // < 0: outside, or a box with children
-    } else if (t < 27 + 27 * 8) {  // slots 243..255 hold no leaf
-      const int e = __ldg(A.tree.nbr + (long long)b * 27 + ((t - 27) >> 3));
-      leaf = e <= -2 ? __ldg(A.tree.fine + (long long)(-e - 2) * 8 + ((t - 27) & 7)) : -1;
-    }
-    int kind = kKindNone;
-    long long base = 0;
-    if (leaf >= 0) {
-      // the 26 direct neighbours are coarser or same-level leaves, the children slots finer
-      const int ls = t == 13 ? lb : (t < 27 ? A.tree.oct[leaf].w : lb + 1);
-      kind = (ls >= lb - 1 && ls <= lb + 1) ? ls - lb + 1 : kKindNone;  // 2:1 balance: always in range
-      base = kind == kKindCoarser ? (long long)__ldg(A.up_slot + leaf) * NF * kNT : (long long)leaf * kNV;
-      my_finer |= kind == kKindFiner;
-    }
-    S.kind[t] = static_cast<unsigned char>(kind);
-    S.base[t] = base;
-  }
-  const bool any_finer = __syncthreads_or(my_finer) != 0;  // also publishes the table, om and orb
+  R(*T)[kNT] = S.T[cb];
 
-  // 2. gathers, batched for memory parallelism: own interior and same-level sources
-  //    read the stage inputs; coarser sources read their prolonged stage inputs
-  //    (prepared by prolong_kernel); under GTS every source is read directly.  At
-  //    stage 0 the stage input is the state u itself.
-#pragma unroll
-  for (int r = 0; r < kPer; ++r) {
-    const int q = tid + r * TPB;
-    if (q >= kNT) break;
-    const unsigned e = ev[r];
-    const unsigned slot = e & 255u;
-    const int kind = S.kind[slot];
-    if (kind == kKindCoarser) {
-      const R* up = up_all + S.base[slot] + pad_off(e);
-#pragma unroll
-      for (int f = 0; f < NF; ++f) async_copy(&S.T[f][q], up + f * kNT);
-    } else if (kind == kKindSame || (kind == kKindFiner && A.gts)) {
-      const R* src = st_in + S.base[slot] + pad_off(e);
-#pragma unroll
-      for (int f = 0; f < NF; ++f) async_copy(&S.T[f][q], src + f * A.fstride);
-    } else if (kind == kKindNone) {
-#pragma unroll
-      for (int f = 0; f < NF; ++f) S.T[f][q] = 0;  // the boundary fill overwrites it
-    }
-    // finer sources under LTS: the correction pass below writes them
-  }
-
-  // 3. finer sources (injection) with the coarse<-fine correction of eq. fc_1 (FP64)
-  if (!A.gts && any_finer) {
-    const int ls = lb + 1;
-    const double* ub = A.u[(A.cur_mask >> ls) & 1];
-#pragma unroll
-    for (int r = 0; r < kPer; ++r) {
-      const int q = tid + r * TPB;
-      if (q >= kNT) break;
-      const unsigned e = ev[r];
-      const unsigned slot = e & 255u;
-      if (S.kind[slot] != kKindFiner) continue;
-      const long long off = S.base[slot] + pad_off(e);
-#pragma unroll
-      for (int f = 0; f < NF; ++f)
-        S.T[f][q] = static_cast<R>(corrected_value<R>(ub + f * A.fstride + off, K + f * A.fstride + off, kstride,
-                                                      S.om[1], A.lc[ls].dt));
-    }
-  }
-  async_wait_all();
-  __syncthreads();
-
-  // 4. physical boundary
+  // physical boundary
   const LevelConst lc = A.lc[lb];
   constexpr int kRoot = 1 << kDepth;
   const bool touches = me.x == 0 || me.y == 0 || me.z == 0 || me.x + eb == kRoot || me.y + eb == kRoot ||
                        me.z + eb == kRoot;
   if (touches) {  // uniform over the CTA
     if (A.bc == LTS_BC_EXACT)
-      fill_exact<NF, R>(S, A, me, eb, lc.dt);
+      fill_exact<NF, R>(T, A, me, eb, lc.dt);
     else
-      fill_extrapolated<NF, R>(S, me, eb);
+      fill_extrapolated<NF, R>(T, me, eb);
     __syncthreads();
   }
 
-  // 5. right-hand side on the 7^3 interior (stage type R) and 6. stage, next stage
-  //    input and RK update (stage_epilogue) of node n
   auto rhs_at = [&](int n, R (&kv)[NF]) {
     const int i = n % 7, j = (n / 7) % 7, k = n / 49;
     const int c0 = (i + 3) + 13 * (j + 3) + 169 * (k + 3);
@@ -709,12 +790,12 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
     const R inv12h2 = sizeof(R) == sizeof(double) ? R(lc.inv12h2) : R(A.cf.lc[lb][2]);
     const R* Tt[NF];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) Tt[f] = S.T[f];
+    for (int f = 0; f < NF; ++f) Tt[f] = T[f];
     rhs_node<NF, R, 13, 169>(Tt, c0, A, kos, inv12h, inv12h2, kv);
     if (A.pde != LTS_PDE_ADVECTION) {
       if (A.cf.sources) {
         const int P6[3] = {6 * me.x + i * eb, 6 * me.y + j * eb, 6 * me.z + k * eb};
-        kv[NF - 1] += wave_source<R>(A, P6, Tt[0][c0], S.orb[0], S.orb[1]);
+        kv[NF - 1] += wave_source<R>(A, P6, Tt[0][c0], S.orb[cb][0], S.orb[cb][1]);
       }
       if (A.bc == LTS_BC_RADIATIVE && touches) {
         const int P6[3] = {6 * me.x + i * eb, 6 * me.y + j * eb, 6 * me.z + k * eb};
@@ -732,7 +813,7 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
     for (int f = 0; f < NF; ++f) {
       const long long o = f * A.fstride + node;
       K[(long long)s * kstride + o] = kv[f];
-      const EpilogueOut e = stage_epilogue<R>(A, K, kstride, o, kv[f], u0, us0, lc.dt, A.cf.dt[lb], s, p);
+      const EpilogueOut e = stage_epilogue<R>(A, K, kstride, o, kv[f], u0, us0, lb, s, p);
       if (s < p - 1) {
         Uout[o] = sizeof(R) == sizeof(double) ? R(e.uin_d) : R(e.uin_f);
       } else if (A.write_update) {
@@ -751,7 +832,6 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
   } else {
     // FP32: right-hand sides in the bank-conflict-free order of g_rhs_node, staged in
     // shared memory, then the epilogue in node order (coalesced stores)
-    static_assert(TPB == kThreads, "g_rhs_node is laid out for kThreads threads");
     const int n = g_rhs_node[tid];
     if (n >= 0) {
       R kv[NF];
@@ -760,7 +840,7 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
       for (int f = 0; f < NF; ++f) S.KV[f][n] = kv[f];
     }
     __syncthreads();
-    for (int m = tid; m < kNV; m += TPB) {
+    for (int m = tid; m < kNV; m += kThreads) {
       R kv[NF];
 #pragma unroll
       for (int f = 0; f < NF; ++f) kv[f] = S.KV[f][m];
@@ -769,21 +849,41 @@ __device__ void stage_octant(StageSmem<NF, R>& S, const StageArgs& A, const int 
   }
 }
 
+// One RK stage of octant b by a CTA of kThreads threads with one tile buffer (the batch
+// kernels): the four phases in sequence.  The caller separates consecutive calls by a
+// barrier.
+template <int NF, typename R, bool C = false>
+__device__ void stage_octant(StageSmem<NF, R, 1>& S, const StageArgs& A, const int b) {
+  if (threadIdx.x < 4) S.om[threadIdx.x] = A.om[threadIdx.x];
+  const int4 me = __ldg(A.tree.oct + b);
+  Slots sl;
+  load_slots(A, b, sl);
+  const bool any_finer = __syncthreads_or(stage_slots<NF, R, 1>(S, 0, A, b, me)) != 0;  // also publishes om
+  if (threadIdx.x == 0 && A.orbit) orbit_centre<R>(A, me.w, S.orb[0]);
+  stage_gather<NF, R, 1>(S, 0, A, me.w, sl);
+  if (!A.gts && any_finer) stage_finer<NF, R, 1, C>(S, 0, A, me.w, sl);
+  async_wait_all();
+  __syncthreads();
+  stage_compute<NF, R, 1>(S, 0, A, b, me);
+}
+
 // Threads per CTA and CTAs per SM of the stage kernel: 352 threads (the 343 interior
-// nodes in one pass) and 5 CTAs per SM (1,760 of 2,048 threads; 39 KB of shared memory
-// each in FP64, 21 KB in mixed precision).  Mixed precision with 128 threads and 10
-// CTAs per SM (more octants in flight, no register spills) measured 13% slower.
+// nodes in one pass) and 5 CTAs per SM (1,760 of 2,048 threads; 38 KB of shared memory
+// each in FP64, 20 KB in mixed precision).  Measured slower: mixed precision with 128
+// threads and 10 CTAs per SM (13%); persistent CTAs stepping their octants with two tile
+// buffers, the next octant's gathers in flight during the current one's right-hand sides
+// (FP64 25%: 3 CTAs per SM fit; mixed 27%: the slot table's loads stall the whole CTA).
 template <typename R> struct StageShape {
-  static constexpr int kTPB = kThreads;
   static constexpr int kMinBlocks = 5;
 };
 
+// The stage kernel: CTA x steps octant list[first + x] (or first + x).
 template <int NF, typename R>
-__global__ void __launch_bounds__(StageShape<R>::kTPB, StageShape<R>::kMinBlocks)
+__global__ void __launch_bounds__(kThreads, StageShape<R>::kMinBlocks)
     stage_kernel(const __grid_constant__ StageArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  StageSmem<NF, R>& S = *reinterpret_cast<StageSmem<NF, R>*>(smem_raw);
-  stage_octant<NF, R, StageShape<R>::kTPB>(S, A, A.list ? A.list[A.first + blockIdx.x] : A.first + blockIdx.x);
+  StageSmem<NF, R, 1>& S = *reinterpret_cast<StageSmem<NF, R, 1>*>(smem_raw);
+  stage_octant<NF, R>(S, A, stage_item(A, blockIdx.x));
 }
 
 // ---------------------------------------------------------------------------
@@ -1025,7 +1125,7 @@ __global__ void __launch_bounds__(kBlockThreads, (sizeof(R) == 8 ? 2 : 4))
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       const long long fo = f * A.fstride;
-      const EpilogueOut e = stage_epilogue<R>(A, K, kstride, fo + own, kv[f], u0, us0, lc.dt, A.cf.dt[lb], s, p);
+      const EpilogueOut e = stage_epilogue<R>(A, K, kstride, fo + own, kv[f], u0, us0, lb, s, p);
       const R uout = sizeof(R) == sizeof(double) ? R(e.uin_d) : R(e.uin_f);
       for (int cz = cz0; cz <= cz1; ++cz)
         for (int cy = cy0; cy <= cy1; ++cy)
@@ -1065,10 +1165,10 @@ cudaError_t launch_block(const StageArgs& a, int count, cudaStream_t s) {
 
 // Padding of the ghost points of every sibling group's block tile: a point p in [-3, 15]^3 (child node
 // units from the parent's anchor) lies in the padded tile of child c (c_a = 1 iff
-// p_a > 6) at local coordinate p - 6 c in [-3, 9]; its source and code are that
-// child's padding-map entry, with the slot resolved to the leaf.
+// p_a > 6) at local coordinate p - 6 c in [-3, 9]; its source is given by that child's
+// padding-map slot, and its code holds its half-node coordinates in the source.
 __global__ void __launch_bounds__(256) groupmap_kernel(const DevTree T, const int* __restrict__ grp, int count,
-                                                       const unsigned* __restrict__ padmap, int* __restrict__ gsrc,
+                                                       const unsigned char* __restrict__ padmap, int* __restrict__ gsrc,
                                                        unsigned short* __restrict__ gcode) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)count * kBG;
        e += (long long)gridDim.x * blockDim.x) {
@@ -1076,9 +1176,9 @@ __global__ void __launch_bounds__(256) groupmap_kernel(const DevTree T, const in
     const int px = q % kBW - 3, py = (q / kBW) % kBW - 3, pz = q / (kBW * kBW) - 3;
     const int cx = px > 6, cy = py > 6, cz = pz > 6;
     const int c = grp[g] + cx + 2 * cy + 4 * cz;
-    const int lq = (px - 6 * cx + 3) + 13 * (py - 6 * cy + 3) + 169 * (pz - 6 * cz + 3);
-    const unsigned w = padmap[(long long)c * kNT + lq];
-    const unsigned slot = w & 255u;
+    const int li = px - 6 * cx, lj = py - 6 * cy, lk = pz - 6 * cz;
+    const int lq = (li + 3) + 13 * (lj + 3) + 169 * (lk + 3);
+    const unsigned slot = padmap[(long long)c * kNT + lq];
     int src = -1;
     if (slot == 13u) {
       src = c;
@@ -1091,15 +1191,20 @@ __global__ void __launch_bounds__(256) groupmap_kernel(const DevTree T, const in
     }
     unsigned code = kExterior;
     if (src >= 0) {
-      const int rel = T.oct[src].w - T.oct[c].w + 1;
-      code = unsigned(pad_rx(w)) | unsigned(pad_ry(w)) << 4 | unsigned(pad_rz(w)) << 8 | unsigned(rel) << 12;
+      const int4 co = T.oct[c], so = T.oct[src];
+      const int ec = 1 << (kDepth - co.w);
+      const int rx = half_node(6 * co.x + li * ec, so.x, so.w);
+      const int ry = half_node(6 * co.y + lj * ec, so.y, so.w);
+      const int rz = half_node(6 * co.z + lk * ec, so.z, so.w);
+      const int rel = so.w - co.w + 1;
+      code = unsigned(rx) | unsigned(ry) << 4 | unsigned(rz) << 8 | unsigned(rel) << 12;
     }
     gsrc[e] = src;
     gcode[e] = static_cast<unsigned short>(code);
   }
 }
 
-cudaError_t launch_groupmap(const DevTree& t, const int* grp, int count, const unsigned* padmap, int* gsrc,
+cudaError_t launch_groupmap(const DevTree& t, const int* grp, int count, const unsigned char* padmap, int* gsrc,
                             unsigned short* gcode, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   groupmap_kernel<<<152 * 8, 256, 0, s>>>(t, grp, count, padmap, gsrc, gcode);
@@ -1111,14 +1216,14 @@ static cudaError_t launch_stage_t(const StageArgs& a, int count, cudaStream_t s)
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(stage_kernel<NF, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(StageSmem<NF, R>));
+                                         (int)sizeof(StageSmem<NF, R, 1>));
     if (e != cudaSuccess) return e;
     // all of the unified L1 / shared memory as shared memory: the occupancy above needs it
     e = cudaFuncSetAttribute(stage_kernel<NF, R>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  stage_kernel<NF, R><<<count, StageShape<R>::kTPB, sizeof(StageSmem<NF, R>), s>>>(a);
+  stage_kernel<NF, R><<<count, kThreads, sizeof(StageSmem<NF, R, 1>), s>>>(a);
   return cudaGetLastError();
 }
 
@@ -1191,7 +1296,7 @@ __device__ __forceinline__ void interp_line(const R (&v)[7], int r0, int n, unsi
 // passes run along axes a, b, c (a permutation of x, y, z chosen per source on the
 // host); V, X1 and X2 hold the source's values in that frame, and only positions
 // whose class box is in the source's set (or its projections) are computed.
-template <int NF, typename R>
+template <int NF, typename R, bool C = false>
 __device__ void prolong_octant(ProlongSmem<NF, R>& S, const ProlongArgs& A, const int b) {
   const int tid = threadIdx.x;
   const int slot = A.up_slot[b];
@@ -1240,12 +1345,12 @@ __device__ void prolong_octant(ProlongSmem<NF, R>& S, const ProlongArgs& A, cons
     const long long off = (long long)b * kNV + ja * sna + jb * snb + jc * snc;
     R v;
     if (rel != 0)
-      v = static_cast<R>(corrected_value<R>(ub + f * A.fstride + off, K + f * A.fstride + off, kstride, A.om[rel],
-                                            A.lc[lb].dt));
+      v = static_cast<R>(corrected_value<R, C>(ub + f * A.fstride + off, K + f * A.fstride + off, kstride, A.om[rel],
+                                               A.lc[lb].dt));
     else if (A.stage == 0)
-      v = static_cast<R>(__ldg(A.u[cur] + f * A.fstride + off));
+      v = static_cast<R>(ld_in<C>(A.u[cur] + f * A.fstride + off));
     else
-      v = __ldg(Uin + f * A.fstride + off);
+      v = ld_in<C>(Uin + f * A.fstride + off);
     S.V[f][n] = v;
   }
   __syncthreads();
@@ -1322,7 +1427,6 @@ cudaError_t launch_prolong(const ProlongArgs& a, cudaStream_t s) {
 template <typename R>
 __global__ void update_kernel(UpdateArgs A) {
   const long long total = (long long)A.nf * A.fstride;
-  const DevTables& tab = c_tab[A.scheme];
   const long long kstride = (long long)A.nf * A.fstride;
   const R* K = static_cast<const R*>(A.K);
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
@@ -1330,17 +1434,17 @@ __global__ void update_kernel(UpdateArgs A) {
     const long long inf = e % A.fstride;
     const int b = int(inf / kNV);
     const int cur = (A.cur_mask >> A.oct[b].w) & 1;
+    // as the stage epilogue (the same products dt w_j, the same order), so that GTS on a
+    // one-level tree equals LTS bit for bit
     if constexpr (sizeof(R) == sizeof(double)) {
-      double acc = 0.0;
-      for (int q = 0; q < A.p - 1; ++q) acc = fma(tab.w[q], static_cast<double>(K[q * kstride + e]), acc);
-      acc = fma(tab.w[A.p - 1], static_cast<double>(K[(A.p - 1) * kstride + e]), acc);
-      A.u[cur ^ 1][e] = fma(A.dt_f, acc, A.u[cur][e]);
+      double v = A.u[cur][e];
+      for (int q = 0; q < A.p; ++q) v = fma(A.dtw[q], static_cast<double>(K[q * kstride + e]), v);
+      A.u[cur ^ 1][e] = v;
     } else {
-      // as the mixed-precision stage epilogue: FP32 increment accumulated into FP64 u
+      // FP32 increment accumulated into FP64 u
       float acc = 0.0f;
-      for (int q = 0; q < A.p - 1; ++q) acc = fmaf(A.wf[q], float(K[q * kstride + e]), acc);
-      acc = fmaf(A.wf[A.p - 1], float(K[(A.p - 1) * kstride + e]), acc);
-      const double un = A.u[cur][e] + static_cast<double>(A.dt_ff * acc);
+      for (int q = 0; q < A.p; ++q) acc = fmaf(A.dtwf[q], float(K[q * kstride + e]), acc);
+      const double un = A.u[cur][e] + static_cast<double>(acc);
       A.u[cur ^ 1][e] = un;
       A.us[cur ^ 1][e] = static_cast<float>(un);
     }
@@ -1589,12 +1693,13 @@ cudaError_t launch_nodemap(const DevTree& t, const int* hang_pos, int* zipmap, i
 // with substeps left by one substep of its own schedule (Fig. blk_loop): one
 // persistent launch per stage covers the active octants of all instances.
 // ---------------------------------------------------------------------------
+template <bool C = false>
 __device__ __forceinline__ int batch_find(const int* pre, int n, int item) {
   // largest i with pre[i] <= item (pre is non-decreasing, pre[0] = 0)
   int lo = 0, hi = n - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (__ldg(pre + mid) <= item)
+    if (ld_in<C>(pre + mid) <= item)
       lo = mid;
     else
       hi = mid - 1;
@@ -1602,9 +1707,10 @@ __device__ __forceinline__ int batch_find(const int* pre, int n, int item) {
   return lo;
 }
 
-__global__ void batch_round_begin(BatchArgs B) {
-  const int i = threadIdx.x;
-  if (i < B.n) {
+// Start of a round (one CTA): each instance's active level l* and argument blocks for
+// this substep, prefix sums of the work items over instances, work counters zeroed.
+__device__ void round_begin_body(const BatchArgs& B) {
+  for (int i = threadIdx.x; i < B.n; i += blockDim.x) {
     BatchInst& I = B.inst[i];
     I.reconcile = 0;
     I.active = I.remaining > 0;
@@ -1647,9 +1753,10 @@ __global__ void batch_round_begin(BatchArgs B) {
   }
 }
 
-__global__ void batch_round_end(BatchArgs B) {
-  const int i = threadIdx.x;
-  if (i < B.n) {
+// End of a round (one CTA): schedules advanced, instances that finish a macro step marked
+// for the reconcile, prefix sums of its work items.
+__device__ void round_end_body(const BatchArgs& B) {
+  for (int i = threadIdx.x; i < B.n; i += blockDim.x) {
     BatchInst& I = B.inst[i];
     if (I.active) {
       for (int l = I.lstar; l <= I.lmax; ++l) I.cur_mask ^= 1u << l;
@@ -1680,13 +1787,17 @@ __global__ void batch_round_end(BatchArgs B) {
   }
 }
 
+__global__ void batch_round_begin(BatchArgs B) { round_begin_body(B); }
+
+__global__ void batch_round_end(BatchArgs B) { round_end_body(B); }
+
 // copies an argument block into shared memory (all threads of the CTA)
-template <typename T>
+template <bool C = false, typename T>
 __device__ __forceinline__ void copy_args(T* dst, const T* src) {
   static_assert(sizeof(T) % 8 == 0, "argument blocks are 8-byte multiples");
   const unsigned long long* s = reinterpret_cast<const unsigned long long*>(src);
   unsigned long long* d = reinterpret_cast<unsigned long long*>(dst);
-  for (int q = threadIdx.x; q < int(sizeof(T) / 8); q += blockDim.x) d[q] = __ldg(s + q);
+  for (int q = threadIdx.x; q < int(sizeof(T) / 8); q += blockDim.x) d[q] = ld_in<C>(s + q);
 }
 
 // Work items (octant-stages of all instances, in instance order) are claimed one at
@@ -1719,9 +1830,9 @@ __global__ void __launch_bounds__(kThreads, 4) batch_stage_kernel(const __grid_c
     }
     const int b = args.first + (item - pre[i]);
     if (args.nf == 1)
-      stage_octant<1, R, kThreads>(*reinterpret_cast<StageSmem<1, R>*>(smem_raw), args, b);
+      stage_octant<1, R>(*reinterpret_cast<StageSmem<1, R, 1>*>(smem_raw), args, b);
     else
-      stage_octant<2, R, kThreads>(*reinterpret_cast<StageSmem<2, R>*>(smem_raw), args, b);
+      stage_octant<2, R>(*reinterpret_cast<StageSmem<2, R, 1>*>(smem_raw), args, b);
   }
 }
 
@@ -1772,17 +1883,207 @@ __global__ void __launch_bounds__(128) batch_hanging_kernel(const __grid_constan
   }
 }
 
+// ---------------------------------------------------------------------------
+// The persistent round: one cooperative launch per substep of all instances.  Its
+// phases (round start, per RK stage the prolongation and the stage over the work items
+// of every instance, round end, reconcile) are separated by a grid-wide barrier.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier of a launch whose CTAs are all resident (a cooperative launch):
+// bar[0] counts the CTAs that arrived, bar[1] is the barrier's generation.  Thread 0 of
+// each CTA arrives after a fence (its CTA's writes are published); the last to arrive
+// resets the count and advances the generation; the others poll the generation.  A CTA
+// that polls longer than limit_ns, or finds kErrTimeout set in the error word, sets it
+// and returns false, and so does every later barrier of the launch: all CTAs then leave
+// the launch within about limit_ns, and the host reads kErrTimeout.  After the barrier
+// every thread fences, so that its later loads see what the other CTAs wrote before it.
+__device__ bool grid_barrier(unsigned* bar, int* err, unsigned long long limit_ns) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile int* verr = err;
+    int ok = (*verr & kErrTimeout) == 0;
+    if (ok) {
+      volatile unsigned* gen = bar + 1;
+      const unsigned g = *gen;
+      __threadfence();
+      if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+        atomicExch(bar, 0u);
+        __threadfence();
+        atomicAdd(bar + 1, 1u);
+      } else {
+        const unsigned long long t0 = global_ns();
+        while (*gen == g) {
+          if ((*verr & kErrTimeout) || global_ns() - t0 > limit_ns) {
+            atomicOr(err, kErrTimeout);
+            ok = 0;
+            break;
+          }
+          __nanosleep(128);
+        }
+      }
+      __threadfence();
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  const int ok = s_ok;
+  __threadfence();
+  return ok != 0;
+}
+
+template <typename R>
+union BatchSmem {
+  StageSmem<2, R, 1> st;
+  ProlongSmem<2, R> pr;
+  SyncSmem sy;
+};
+
+// One round of a batch in one launch: grid-stride work claiming as in the per-stage
+// kernels above, the phases separated by grid_barrier.  Every load of data that an
+// earlier phase of the launch wrote goes through L2 (C = true) or is ordered by the
+// barrier's fences (the asynchronous gathers, plain loads).
+template <typename R>
+__global__ void __launch_bounds__(kThreads, 3)
+    batch_substep_kernel(const __grid_constant__ BatchArgs B, int pmax, int lmax_all, unsigned* bar, int* err,
+                         unsigned long long limit_ns) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  BatchSmem<R>& S = *reinterpret_cast<BatchSmem<R>*>(smem_raw);
+  __shared__ StageArgs sargs;
+  __shared__ ProlongArgs pargs;
+  __shared__ SyncArgs yargs;
+  __shared__ int s_item;
+  if (blockIdx.x == 0) round_begin_body(B);
+  if (!grid_barrier(bar, err, limit_ns)) return;
+  for (int st = 0; st < pmax; ++st) {
+    {  // prolongation of the coarser sources of every instance
+      const int* pre = B.prol_pre + st * (kMaxBatch + 1);
+      const int total = __ldcg(pre + B.n);  // the same value in every CTA
+      if (total > 0) {
+        int cur = -1;
+        for (;;) {
+          const int item = claim_item(B.next_item + st, &s_item);
+          if (item >= total) break;
+          const int i = batch_find<true>(pre, B.n + 1, item);
+          if (i != cur) {
+            copy_args<true>(&pargs, &B.inst[i].pr[st]);
+            __syncthreads();
+            cur = i;
+          }
+          const int b = __ldg(pargs.list + (item - __ldcg(pre + i)));
+          if (pargs.nf == 1)
+            prolong_octant<1, R, true>(*reinterpret_cast<ProlongSmem<1, R>*>(&S.pr), pargs, b);
+          else
+            prolong_octant<2, R, true>(S.pr, pargs, b);
+        }
+        if (!grid_barrier(bar, err, limit_ns)) return;
+      }
+    }
+    {  // the stage over the active octants of every instance
+      const int* pre = B.stage_pre + st * (kMaxBatch + 1);
+      const int total = __ldcg(pre + B.n);
+      if (total > 0) {
+        int cur = -1;
+        for (;;) {
+          const int item = claim_item(B.next_item + 4 + st, &s_item);
+          if (item >= total) break;
+          const int i = batch_find<true>(pre, B.n + 1, item);
+          if (i != cur) {
+            copy_args<true>(&sargs, &B.inst[i].st[st]);
+            __syncthreads();
+            cur = i;
+          }
+          const int b = sargs.first + (item - __ldcg(pre + i));
+          if (sargs.nf == 1)
+            stage_octant<1, R, true>(*reinterpret_cast<StageSmem<1, R, 1>*>(&S.st), sargs, b);
+          else
+            stage_octant<2, R, true>(S.st, sargs, b);
+        }
+        if (!grid_barrier(bar, err, limit_ns)) return;
+      }
+    }
+  }
+  if (blockIdx.x == 0) round_end_body(B);
+  if (!grid_barrier(bar, err, limit_ns)) return;
+  {  // reconcile of the instances that finished a macro step: zip, then hanging nodes by level
+    const int total = __ldcg(B.zip_pre + B.n);
+    if (total > 0) {
+      int cur = -1;
+      for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int i = batch_find<true>(B.zip_pre, B.n + 1, item);
+        if (i != cur) {
+          __syncthreads();
+          copy_args<true>(&yargs, &B.inst[i].zip);
+          __syncthreads();
+          cur = i;
+        }
+        sync_zip_octant<double>(S.sy, yargs, item - __ldcg(B.zip_pre + i));
+        __syncthreads();
+      }
+      if (!grid_barrier(bar, err, limit_ns)) return;
+    }
+  }
+  for (int l = 1; l <= lmax_all; ++l) {
+    const int* pre = B.hang_pre + l * (kMaxBatch + 1);
+    const int total = __ldcg(pre + B.n);
+    if (total == 0) continue;
+    int cur = -1;
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+      const int i = batch_find<true>(pre, B.n + 1, item);
+      if (i != cur) {
+        __syncthreads();
+        copy_args<true>(&yargs, &B.inst[i].hang);
+        __syncthreads();
+        cur = i;
+      }
+      const BatchInst& I = B.inst[i];
+      sync_hanging_octant<double>(S.sy, yargs, __ldg(I.hang_list + I.hang_off[l] + (item - __ldcg(pre + i))));
+      __syncthreads();
+    }
+    if (!grid_barrier(bar, err, limit_ns)) return;
+  }
+}
+
+// The barrier alone, for its time limit: CTA `absent` returns without arriving (-1: all
+// arrive), so that the other CTAs' waits run out and set kErrTimeout.
+__global__ void barrier_probe_kernel(unsigned* bar, int* err, unsigned long long limit_ns, int absent) {
+  if (int(blockIdx.x) == absent) return;
+  grid_barrier(bar, err, limit_ns);
+}
+
 cudaError_t prepare_batch_kernels() {
   cudaError_t e = cudaFuncSetAttribute(batch_stage_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(StageSmem<2, double>));
+                                       (int)sizeof(StageSmem<2, double, 1>));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(batch_stage_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)sizeof(StageSmem<2, float>));
+  e = cudaFuncSetAttribute(batch_stage_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(StageSmem<2, float, 1>));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(batch_substep_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(BatchSmem<double>));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(batch_substep_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sizeof(BatchSmem<float>));
+}
+
+cudaError_t batch_substep_resident(int mixed, int* per_sm, int* sms) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  return mixed ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_substep_kernel<float>, kThreads,
+                                                               sizeof(BatchSmem<float>))
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_substep_kernel<double>, kThreads,
+                                                               sizeof(BatchSmem<double>));
 }
 
 template <typename R>
 static cudaError_t batch_round_t(const BatchArgs& a, int pmax, int lmax_all, int gs, int gp, int gy, cudaStream_t s) {
-  const size_t smem_stage = sizeof(StageSmem<2, R>);
+  const size_t smem_stage = sizeof(StageSmem<2, R, 1>);
   const size_t smem_prol = sizeof(ProlongSmem<2, R>);
   batch_round_begin<<<1, kMaxBatch, 0, s>>>(a);
   for (int st = 0; st < pmax; ++st) {
@@ -1799,6 +2100,46 @@ cudaError_t launch_batch_round(const BatchArgs& a, int pmax, int lmax_all, int g
                                int grid_sync, int mixed, cudaStream_t s) {
   return mixed ? batch_round_t<float>(a, pmax, lmax_all, grid_stage, grid_prolong, grid_sync, s)
                : batch_round_t<double>(a, pmax, lmax_all, grid_stage, grid_prolong, grid_sync, s);
+}
+
+template <typename R>
+static cudaError_t batch_substep_t(const BatchArgs& a, int pmax, int lmax_all, int grid, unsigned* bar, int* err,
+                                   unsigned long long limit_ns, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(grid));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = sizeof(BatchSmem<R>);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, batch_substep_kernel<R>, a, pmax, lmax_all, bar, err, limit_ns);
+}
+
+cudaError_t launch_batch_substep(const BatchArgs& a, int pmax, int lmax_all, int grid, int mixed, unsigned* bar,
+                                 int* err, unsigned long long limit_ns, cudaStream_t s) {
+  return mixed ? batch_substep_t<float>(a, pmax, lmax_all, grid, bar, err, limit_ns, s)
+               : batch_substep_t<double>(a, pmax, lmax_all, grid, bar, err, limit_ns, s);
+}
+
+cudaError_t launch_barrier_probe(int grid, unsigned* bar, int* err, unsigned long long limit_ns, int absent,
+                                 cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(grid));
+  cfg.blockDim = dim3(32);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, barrier_probe_kernel, bar, err, limit_ns, absent);
 }
 
 // ---------------------------------------------------------------------------
@@ -1847,12 +2188,12 @@ cudaError_t launch_init(const InitArgs& a, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// Padding map (Fig. unzip): for every octant and padded point, the source's slot in
-// the octant's neighbour view, the point's element offset in the source and its
-// half-node coordinates there (pad_entry).  The tree is static, so this is resolved
-// once per plan instead of at every stage.
+// Padding map (Fig. unzip): for every octant and padded point, the slot of its source in
+// the octant's neighbour view (one byte; kSlotNone outside the domain).  The tree is
+// static, so this is resolved once per plan instead of at every stage; where the point
+// lies in the source follows from the slot (stage_slots).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) padmap_kernel(const DevTree T, unsigned* __restrict__ out, int* err) {
+__global__ void __launch_bounds__(256) padmap_kernel(const DevTree T, unsigned char* __restrict__ out, int* err) {
   __shared__ NbrView nv;
   for (int b = blockIdx.x; b < T.n; b += gridDim.x) {
     __syncthreads();
@@ -1865,7 +2206,7 @@ __global__ void __launch_bounds__(256) padmap_kernel(const DevTree T, unsigned* 
       const int i = q % 13 - 3, j = (q / 13) % 13 - 3, k = q / 169 - 3;
       unsigned entry;
       if (i >= 0 && i <= 6 && j >= 0 && j <= 6 && k >= 0 && k <= 6) {
-        entry = pad_entry(13u, 2 * i, 2 * j, 2 * k, false);
+        entry = 13u;
       } else {
         unsigned slot;
         const int src = resolve_source(nv, i, j, k, b, false, &slot);
@@ -1883,16 +2224,16 @@ __global__ void __launch_bounds__(256) padmap_kernel(const DevTree T, unsigned* 
             atomicOr(err, 1);  // never on a balanced tree: reported, and the point becomes a zero ghost
             entry = kSlotNone;
           } else {
-            entry = pad_entry(slot, rx, ry, rz, coarser);
+            entry = slot;
           }
         }
       }
-      out[(long long)b * kNT + q] = entry;
+      out[(long long)b * kNT + q] = static_cast<unsigned char>(entry);
     }
   }
 }
 
-cudaError_t launch_padmap(const DevTree& t, unsigned* out, int* err, cudaStream_t s) {
+cudaError_t launch_padmap(const DevTree& t, unsigned char* out, int* err, cudaStream_t s) {
   if (t.n <= 0) return cudaSuccess;
   const int blocks = t.n < 152 * 8 ? t.n : 152 * 8;
   padmap_kernel<<<blocks, 256, 0, s>>>(t, out, err);
@@ -1913,13 +2254,18 @@ __global__ void maps_kernel(MapArgs A) {
   const int npts = A.nodes ? kNV : kNT;
   if (!A.nodes && A.padmap) {
     for (int q = threadIdx.x; q < kNT; q += blockDim.x) {
-      const unsigned e = A.padmap[(long long)b * kNT + q];
-      const int src = slot_leaf(S.nv, e & 255u, b);
+      const int src = slot_leaf(S.nv, A.padmap[(long long)b * kNT + q], b);
+      const int i = q % 13 - 3, j = (q / 13) % 13 - 3, k = q / 169 - 3;
       const long long o = (long long)blockIdx.x * kNT + q;
       A.src[o] = src;
-      A.r[o * 3 + 0] = src >= 0 ? pad_rx(e) : -1;
-      A.r[o * 3 + 1] = src >= 0 ? pad_ry(e) : -1;
-      A.r[o * 3 + 2] = src >= 0 ? pad_rz(e) : -1;
+      int r[3] = {-1, -1, -1};
+      if (src >= 0) {
+        const int4 so = A.tree.oct[src];
+        r[0] = half_node(6 * me.x + i * eb, so.x, so.w);
+        r[1] = half_node(6 * me.y + j * eb, so.y, so.w);
+        r[2] = half_node(6 * me.z + k * eb, so.z, so.w);
+      }
+      for (int a = 0; a < 3; ++a) A.r[o * 3 + a] = r[a];
     }
     return;
   }

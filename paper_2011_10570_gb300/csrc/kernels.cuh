@@ -42,13 +42,21 @@ struct StageTerms {
 struct StageConstF {
   float lc[32][3];       // per level: kos, inv12h, inv12h2
   float dt[32];          // per level: dt
-  float next_w[4];       // weights of the next stage input (StageArgs::next)
+  float dtw_next[32][4]; // per level: dt * the weights of the next stage input (StageArgs::next)
+  float dtw_upd[32][4];  // per level: dt * the RK weights
   float w[4];            // RK weights
   float adv[3];
   float nl_c;
   float orb[4];          // orbit radius, angular speed, width, amplitude
   float lo, xscale;      // x = lo + xscale * (lattice6 coordinate)
   int sources;           // 1: the wave equation has source terms
+};
+
+// per level l: dt_l times the weights of the next stage input (next[l][q] for the
+// terms of StageArgs::next) and of the RK update (upd[l][j])
+struct StageWeights {
+  double next[32][4];
+  double upd[32][4];
 };
 
 struct StageArgs {
@@ -71,16 +79,18 @@ struct StageArgs {
   LevelConst lc[32];
   StageTerms om[4];      // this stage's correction terms per relation (eqs. fc_1, fc_2)
   StageTerms next;       // a[stage+1][.] terms of the next stage input
+  StageWeights dtw;      // the same and the RK weights, times dt of each level
   double w[4];           // RK weights
   double gamma[4];       // gamma[stage][.] for exact boundary data
   IcParams icp;
-  int* err;              // device error word: bit 0 source coordinate out of range
+  int* err;              // device error word: bit 0 source coordinate out of range, bit 1 a coarser
+                         // source without prolonged inputs
   const void* up;        // prolonged stage inputs of coarser sources, [slot][nf][2197], stage type
   int mixed;             // 1: FP32 stages, tile and right-hand side; FP64 state and corrections
   float* us[2];          // mixed: FP32 copies of u[2], kept equal to float(u) (stage inputs read them)
   const int* up_slot;    // slot of an octant in `up` (-1: not a coarser source)
-  const unsigned* padmap;  // [N][2197]: slot | offset << 8 | rx << 20 | ry << 24 | rz << 28 per padded point
-  const int* list;         // stage_kernel: CTA x steps list[first + x] (nullptr: octant first + x)
+  const unsigned char* padmap;  // [N][2197]: slot of the source of every padded point in the neighbour view
+  const int* list;         // stage_kernel: work item x is octant list[first + x] (nullptr: first + x)
   // block kernel (Sec. 3.2.5 octree-to-block decomposition): CTA x steps the complete
   // sibling group grp[first + x] (8 consecutive octants) as one 13^3-node block
   const int* grp;
@@ -152,9 +162,8 @@ struct UpdateArgs {
   int n;
   const int4* oct;
   unsigned cur_mask;
-  double dt_f;
-  float dt_ff;           // dt_f and the RK weights in FP32 (mixed precision)
-  float wf[4];
+  double dtw[4];         // dt_f times the RK weights
+  float dtwf[4];         // the same in FP32 (mixed precision)
 };
 
 struct InitArgs {
@@ -174,7 +183,7 @@ struct MapArgs {
   int nodes;             // 0: 2197 padded points, 1: 343 nodes
   int* src;
   int* r;
-  const unsigned* padmap;  // padding maps: decode this plan's padding map (nullptr: resolve)
+  const unsigned char* padmap;  // padding maps: decode this plan's padding map (nullptr: resolve)
 };
 
 // ---- batches: many instances advanced together ------------------------------
@@ -217,11 +226,19 @@ struct BatchArgs {
 cudaError_t prepare_batch_kernels();  // outside any stream capture
 cudaError_t launch_batch_round(const BatchArgs& a, int pmax, int lmax_all, int grid_stage, int grid_prolong,
                                int grid_sync, int mixed, cudaStream_t s);
+// persistent rounds: one cooperative launch per round, phases separated by a grid barrier
+// with a time limit (kErrTimeout in *err when a CTA waited longer than limit_ns)
+constexpr int kErrTimeout = 1 << 4;
+cudaError_t batch_substep_resident(int mixed, int* per_sm, int* sms);  // CTAs per SM and SMs
+cudaError_t launch_batch_substep(const BatchArgs& a, int pmax, int lmax_all, int grid, int mixed, unsigned* bar,
+                                 int* err, unsigned long long limit_ns, cudaStream_t s);
+cudaError_t launch_barrier_probe(int grid, unsigned* bar, int* err, unsigned long long limit_ns, int absent,
+                                 cudaStream_t s);
 
 cudaError_t upload_tables(const Tables* rk4, const Tables* rk3, const double W[13][7], const double E[4][4]);
 cudaError_t launch_stage(const StageArgs& a, int count, cudaStream_t s);
 cudaError_t launch_block(const StageArgs& a, int count, cudaStream_t s);
-cudaError_t launch_groupmap(const DevTree& t, const int* grp, int count, const unsigned* padmap, int* gsrc,
+cudaError_t launch_groupmap(const DevTree& t, const int* grp, int count, const unsigned char* padmap, int* gsrc,
                             unsigned short* gcode, cudaStream_t s);
 constexpr int kBW = 19;               // padded block width of a sibling group: 13 nodes + 2 x 3
 constexpr int kBT = kBW * kBW * kBW;  // 6859 padded points
@@ -234,7 +251,7 @@ cudaError_t launch_nodemap(const DevTree& t, const int* hang_pos, int* zipmap, i
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
 cudaError_t launch_init(const InitArgs& a, cudaStream_t s);
 cudaError_t launch_maps(const MapArgs& a, cudaStream_t s);
-cudaError_t launch_padmap(const DevTree& t, unsigned* out, int* err, cudaStream_t s);
+cudaError_t launch_padmap(const DevTree& t, unsigned char* out, int* err, cudaStream_t s);
 cudaError_t launch_widen(const float* in, double* out, long long n, cudaStream_t s);
 cudaError_t launch_narrow(const double* in, float* out, long long n, cudaStream_t s);
 

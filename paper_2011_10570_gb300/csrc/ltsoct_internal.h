@@ -35,9 +35,6 @@ bool make_tables(int rk, Tables* t);
 void lagrange_7_to_13(double W[13][7]);
 void cubic_extrapolation(double E[4][4]);
 
-uint64_t morton_key(uint32_t x, uint32_t y, uint32_t z);
-bool build_octree(const lts_refine_spec& spec, std::vector<Oct>* leaves, std::string* err);
-
 // Neighbour tables (o2o): nbr[b*27+d] >= 0 leaf covering the same-size box in
 // direction d (same size or one level coarser), -1 outside the domain, <= -2:
 // the box is split and fine[(-nbr-2)*8 + c] holds child c (-1: not a leaf).
@@ -45,14 +42,19 @@ struct Neighbours {
   std::vector<int32_t> nbr;
   std::vector<int32_t> fine;
 };
-lts_status build_neighbours(const std::vector<Oct>& octs, Neighbours* out, std::string* err);
+
+// Sec. 3.2.2 - 3.2.4 on the device (octree.cu): refinement, 2:1 balance, the leaves in
+// level order and their o2o table, on the current device.
+lts_status device_octree(const lts_refine_spec& spec, std::vector<Oct>* leaves, Neighbours* nb, std::string* err);
 
 void set_last_error(const std::string& msg);
 
 }  // namespace ltsoct
 
-// The opaque octree handle.
+// The opaque octree handle: the leaves and their o2o table, built on the device and
+// kept on the host for the plans' set-up.
 struct lts_octree {
   lts_refine_spec spec;
   std::vector<ltsoct::Oct> leaves;  // level order
+  ltsoct::Neighbours nb;
 };

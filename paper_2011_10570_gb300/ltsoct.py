@@ -16,6 +16,9 @@ from . import build as _build
 
 _lib = None
 
+# lts_status codes (include/ltsoct.h)
+LTS_OK, LTS_EINVAL, LTS_ENOMEM, LTS_ECUDA, LTS_ETIMEOUT, LTS_EUNBALANCED, LTS_ESTATE, LTS_EINTERNAL = range(8)
+
 
 class LtsError(RuntimeError):
     def __init__(self, status, where):
@@ -55,7 +58,8 @@ EXPORTS = ["octree_build", "octree_size", "octree_export", "octree_destroy", "lt
            "lts_run_substeps", "lts_advance", "gts_steps", "gts_advance", "lts_export_o2o", "lts_export_pad_map",
            "lts_export_node_map", "lts_export_pad_map_static", "lts_set_blocking", "lts_set_profiling", "lts_kernel_stats", "lts_batch_create", "lts_batch_destroy", "lts_batch_run",
            "lts_batch_set_grid", "lts_batch_stats", "lts_batch_create_slots", "lts_batch_attach",
-           "lts_batch_detach", "lts_strerror", "lts_last_error"]
+           "lts_batch_detach", "lts_batch_set_mode", "lts_batch_wait", "lts_batch_probe_barrier", "lts_strerror",
+           "lts_last_error"]
 
 
 def library_path():
@@ -105,6 +109,9 @@ def load(path=None):
         "lts_batch_create_slots": ([C.c_int, vp, C.c_int, C.POINTER(vp)], st),
         "lts_batch_attach": ([vp, C.c_int, vp], st),
         "lts_batch_detach": ([vp, C.c_int], st),
+        "lts_batch_set_mode": ([vp, C.c_int, C.c_int], st),
+        "lts_batch_wait": ([vp], st),
+        "lts_batch_probe_barrier": ([vp, C.c_int, C.c_double], st),
         "lts_strerror": ([st], C.c_char_p),
         "lts_last_error": ([], C.c_char_p),
     }
@@ -373,6 +380,19 @@ class Batch:
     def set_grid(self, stage, prolong, sync):
         _check(_lib.lts_batch_set_grid(self.h, stage, prolong, sync), "lts_batch_set_grid")
 
+    def set_mode(self, persistent=True, ctas_per_sm=1):
+        """persistent: one cooperative launch per round (ctas_per_sm CTAs per SM); else
+        the per-stage launches"""
+        _check(_lib.lts_batch_set_mode(self.h, 1 if persistent else 0, int(ctas_per_sm)), "lts_batch_set_mode")
+
+    def wait(self):
+        """synchronise; raises LtsError (LTS_ETIMEOUT) if a round's grid barrier timed out"""
+        _check(_lib.lts_batch_wait(self.h), "lts_batch_wait")
+
+    def probe_barrier(self, absent_cta=-1, limit_s=0.05):
+        """the grid barrier alone; returns the status (0 ok, LTS_ETIMEOUT when a CTA is absent)"""
+        return _lib.lts_batch_probe_barrier(self.h, int(absent_cta), float(limit_s))
+
     def stats(self):
         n = C.c_int64()
         g = [C.c_int(), C.c_int(), C.c_int()]
@@ -380,24 +400,41 @@ class Batch:
         return dict(launches=n.value, grid_stage=g[0].value, grid_prolong=g[1].value, grid_sync=g[2].value)
 
     def autotune(self, rounds=4, candidates=None):
-        """Choose the persistent grid sizes by timing `rounds` rounds for each candidate
-        (advances the plans: re-set their state afterwards)."""
+        """Choose the launch shape of the rounds by timing `rounds` rounds for each
+        candidate: the persistent round kernel with 1 .. (resident) CTAs per SM, and the
+        per-stage launches with grid sizes in multiples of the SMs (advances the plans:
+        re-set their state afterwards).  Returns the best shape and every timing."""
         import time
         live = [p for p in self.plans if p is not None]
         torch = live[0].torch
         sms = torch.cuda.get_device_properties(live[0].device).multi_processor_count
-        candidates = candidates or [(sms * a, sms * b, sms * 8) for a in (2, 3, 4, 6) for b in (4, 6)]
-        best = None
-        for c in candidates:
-            self.set_grid(*c)
+        if candidates is None:
+            candidates = [("persistent", k) for k in (1, 2, 3, 4)]
+            candidates += [("per-stage", (sms * a, sms * b, sms * 8)) for a in (2, 4, 6) for b in (4, 6)]
+        best, table = None, []
+        for mode, shape in candidates:
+            try:
+                if mode == "persistent":
+                    self.set_mode(True, shape)
+                else:
+                    self.set_mode(False)
+                    self.set_grid(*shape)
+            except LtsError:
+                continue            # more CTAs per SM than the kernel keeps resident
             steps = [rounds if p is not None else 0 for p in self.plans]
             self.run(steps, graph=True)    # capture + warm
-            torch.cuda.synchronize()
+            self.wait()
             t0 = time.perf_counter()
             self.run(steps, graph=True)
-            torch.cuda.synchronize()
+            self.wait()
             dt = time.perf_counter() - t0
-            if best is None or dt < best[0]:
-                best = (dt, c)
-        self.set_grid(*best[1])
-        return dict(grid=best[1], seconds=best[0])
+            table.append((mode, shape, dt))
+            if best is None or dt < best[2]:
+                best = (mode, shape, dt)
+        mode, shape, dt = best
+        if mode == "persistent":
+            self.set_mode(True, shape)
+        else:
+            self.set_mode(False)
+            self.set_grid(*shape)
+        return dict(mode=mode, shape=shape, seconds=dt, table=table)

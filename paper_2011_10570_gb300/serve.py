@@ -18,6 +18,17 @@ active levels of all of them.  Between chunks of rounds the server
 A single resident solve runs on its own plan's kernels (no batch indirection).
 Latency is arrival to result; throughput is node-updates per second of wall time.
 
+Two policies choose the order of admission and the solves each chunk advances:
+  * ``fcfs``: requests are admitted in arrival order, and every resident solve
+    advances in every chunk (saturation bounds the admissions, as above);
+  * ``srpt``: shortest remaining work first.  Waiting requests are admitted in order
+    of their work (node-updates to their end time, eq. w_nuts per macro step), and
+    each chunk advances the resident solves with the least remaining work while
+    their summed load stays within `saturation` (at least one).  The others stay
+    resident and paused: their state does not move until they are scheduled again.
+    Small solves that arrive behind a large one no longer wait for it to finish,
+    at the same total work.
+
 ``serve_one_at_a_time`` solves the same stream first-come-first-served, one
 request at a time, for comparison.
 """
@@ -50,6 +61,8 @@ class Result:
     substeps: int
     node_updates: float
     state: np.ndarray = field(repr=False, default=None)
+    t_requested: float = 0.0   # the request's end time
+    t_reached: float = 0.0     # the time the solve reached (whole macro steps, see substeps_to)
 
     @property
     def latency(self):
@@ -66,10 +79,23 @@ def state_bytes(n_octants, nf, precision, p=4):
 
 
 def substeps_to(plan, t_end):
-    """whole macro steps from the plan's current time up to (about) t_end"""
+    """whole macro steps from the plan's current time up to the macro-step boundary
+    nearest t_end (at least one): the solve ends at that boundary, which Result
+    records as t_reached next to the requested t_end"""
     st = plan.stats()
     n_macro = max(1, int(round((t_end - st["time"]) / st["dt_coarsest"])))
     return n_macro * (1 << (st["l_max"] - st["l_min"]))
+
+
+def estimated_work(spec, prob, levels, t_end):
+    """node-updates of a request before its plan exists: macro steps of the coarsest step
+    dt_c = cfl * h_(l_min) (h the node spacing) to t_end, times the LTS work of one macro
+    step, sum_l n_l 2^(l - l_min) octant-steps of 343 nodes (eq. w_nuts)"""
+    levels = np.asarray(levels)
+    lmin = int(levels.min())
+    dt_c = prob["cfl"] * (spec["hi"] - spec["lo"]) / (6.0 * 2.0 ** lmin)
+    n_macro = max(1, int(round(t_end / dt_c)))
+    return float(n_macro * 343 * np.sum(np.ldexp(1.0, levels.astype(np.int64) - lmin)))
 
 
 def mean_active_octants(levels):
@@ -92,8 +118,11 @@ def node_updates(st, n_sub0, n):
 
 class Server:
     def __init__(self, slots=16, hbm_budget=64 << 30, chunk=8, precision=0, keep_results=True,
-                 saturation=8192.0):
+                 saturation=8192.0, policy="fcfs"):
         import torch
+        if policy not in ("fcfs", "srpt"):
+            raise ValueError("policy must be 'fcfs' or 'srpt'")
+        self.policy = policy
         self.torch = torch
         self.stream = torch.cuda.current_stream()
         self.batch = ltsoct.Batch.slots(slots, self.stream, precision)
@@ -129,19 +158,26 @@ class Server:
             if req.rid not in trees:
                 tree = ltsoct.Octree(req.work["spec"])
                 nf = 2 if req.work["prob"]["pde"] == 1 else 1
-                trees[req.rid] = (tree, state_bytes(len(tree), nf, self.precision),
-                                  mean_active_octants(tree.export()[1]))
+                levels = tree.export()[1]
+                trees[req.rid] = (tree, state_bytes(len(tree), nf, self.precision), mean_active_octants(levels),
+                                  estimated_work(req.work["spec"], req.work["prob"], levels, req.t_end))
             return trees[req.rid]
 
+        srpt = self.policy == "srpt"
         while pending or active:
             mark("idle_or_host")
             # admit while a slot is free and the budget holds
             while pending and (not realtime or pending[0].arrival <= now()) and len(active) < self.nslots:
-                req = pending[0]
-                tree, est, ld = prepare(req)
-                if active and (used + est > self.budget or load + ld > self.saturation):
+                if srpt:
+                    # the arrived request with the least work
+                    arrived = [r for r in pending if not realtime or r.arrival <= now()]
+                    req = min(arrived, key=lambda r: (prepare(r)[3], r.arrival))
+                else:
+                    req = pending[0]
+                tree, est, ld, _ = prepare(req)
+                if active and (used + est > self.budget or (not srpt and load + ld > self.saturation)):
                     break                # wait for memory to be freed or the GPU to have room
-                pending.popleft()
+                pending.remove(req)
                 del trees[req.rid]
                 prob = dict(req.work["prob"], precision=self.precision)
                 plan = ltsoct.Plan(tree, prob, stream=self.stream)
@@ -149,7 +185,7 @@ class Server:
                 n = substeps_to(plan, req.t_end)
                 slot = next(s for s in range(self.nslots) if s not in active)
                 self.batch.attach(slot, plan)
-                active[slot] = [req, plan, n, now(), est, node_updates(plan.stats(), 0, n), ld]
+                active[slot] = [req, plan, n, now(), est, node_updates(plan.stats(), 0, n), ld, n]
                 used += est
                 load += ld
                 mark("admit")
@@ -158,15 +194,27 @@ class Server:
                     time.sleep(max(0.0, min(0.01, pending[0].arrival - now())))
                 continue
             steps = [0] * self.nslots
-            k = min(self.chunk, min(a[2] for a in active.values()))
-            if len(active) == 1 and load >= self.saturation:
-                # nothing can join a solve that fills the GPU: run it to its end in one go
-                k = next(iter(active.values()))[2]
-            for s, a in active.items():
-                steps[s] = min(k, a[2])
-            if len(active) == 1:
-                (s0, a0), = active.items()
-                a0[1].run_substeps(steps[s0])
+            if srpt:
+                # the resident solves with the least remaining work, within the saturation load
+                order = sorted(active, key=lambda s: (active[s][5] * active[s][2] / active[s][7], active[s][0].arrival))
+                run, ld_run = [], 0.0
+                for s in order:
+                    if run and ld_run + active[s][6] > self.saturation:
+                        break
+                    run.append(s)
+                    ld_run += active[s][6]
+                k = min(self.chunk, min(active[s][2] for s in run))
+            else:
+                run = list(active)
+                k = min(self.chunk, min(a[2] for a in active.values()))
+                if len(active) == 1 and load >= self.saturation:
+                    # nothing can join a solve that fills the GPU: run it to its end in one go
+                    k = next(iter(active.values()))[2]
+            for s in run:
+                steps[s] = min(k, active[s][2])
+            if len(run) == 1:
+                a0 = active[run[0]]
+                a0[1].run_substeps(steps[run[0]])
             else:
                 self.batch.run(steps, graph=True)
             mark("launch")
@@ -187,7 +235,8 @@ class Server:
                     t = now()
                     st = plan.stats()
                     results.append(Result(req.rid, req.arrival, a[3], t, st["n_octants"],
-                                          int(round(st["time"] / st["dt_finest"])), a[5], state))
+                                          int(round(st["time"] / st["dt_finest"])), a[5], state,
+                                          t_requested=req.t_end, t_reached=st["time"]))
                     self.batch.detach(s)
                     used -= a[4]
                     load -= a[6]
@@ -216,7 +265,7 @@ def serve_one_at_a_time(requests, precision=0, realtime=True, keep_results=True)
         state = plan.get_state() if keep_results else None
         st = plan.stats()
         results.append(Result(req.rid, req.arrival, admitted, now(), st["n_octants"], n,
-                              node_updates(st, 0, n), state))
+                              node_updates(st, 0, n), state, t_requested=req.t_end, t_reached=st["time"]))
         del plan
     return results, now()
 

@@ -1,10 +1,9 @@
-"""The C ABI: the library loads, exports every entry point include/ltsoct.h
-declares, and its host-side octree construction (Sec. 3.2.2-3.2.3) matches the
-oracle bit for bit.  No GPU needed."""
+"""The C ABI: the library loads, exports every entry point include/ltsoct.h declares,
+and rejects an invalid refinement spec before touching a device.  No GPU needed (the
+octree build itself runs on the device: tests/test_gpu_octree.py)."""
 import os
 import re
 
-import numpy as np
 import pytest
 
 from paper_2011_10570_gb300 import workloads as W
@@ -48,32 +47,3 @@ def test_error_reporting_without_gpu(lt):
         lt.Octree(bad)
     assert ei.value.status == 1 and "octree_build" in str(ei.value)
     assert lt.load().lts_strerror(5).decode() == "octree is not 2:1 balanced"
-
-
-@pytest.mark.parametrize("mk", [lambda: W.advection_gauss(), lambda: W.advection_gauss(l_min=2, l_max=4),
-                                lambda: W.advection_poly(5), lambda: W.wave_shell(l_min=3, l_max=6, half=10.0)])
-def test_octree_bit_exact_vs_oracle(lt, orc, mk):
-    w = mk()
-    a = lt.Octree(w["spec"])
-    b = orc.Tree.build(w["spec"])
-    xa, la = a.export()
-    xb, lb = b.export()
-    assert np.array_equal(la, lb) and np.array_equal(xa, xb)
-
-
-def test_octree_bit_exact_random_specs(lt, orc):
-    from test_oracle_octree import random_spec
-    for seed in range(12):
-        spec = random_spec(seed, l_min=seed % 3, l_max=3 + seed % 4, kind=seed % 2)
-        xa, la = lt.Octree(spec).export()
-        xb, lb = orc.Tree.build(spec).export()
-        assert np.array_equal(la, lb) and np.array_equal(xa, xb), seed
-
-
-@pytest.mark.slow
-def test_octree_bit_exact_full_wave_config(lt, orc):
-    w = W.wave_shell()
-    xa, la = lt.Octree(w["spec"]).export()
-    xb, lb = orc.Tree.build(w["spec"]).export()
-    assert len(la) == 154400
-    assert np.array_equal(la, lb) and np.array_equal(xa, xb)

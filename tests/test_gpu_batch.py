@@ -1,7 +1,9 @@
-"""Batching (many independent solves advanced together, one persistent launch per
-stage, rounds captured in a CUDA graph): every instance ends exactly where it ends
-when run alone, for instances of different PDEs, RK schemes, level ranges and
-substep counts (whole and partial macro steps)."""
+"""Batching (many independent solves advanced together; a round is one persistent
+cooperative launch, or a launch per stage; rounds captured in a CUDA graph): every
+instance ends exactly where it ends when run alone, for instances of different PDEs,
+RK schemes, level ranges and substep counts (whole and partial macro steps), in both
+modes and every autotuned shape; the grid barrier of the persistent round gives up
+after its time limit and reports LTS_ETIMEOUT (a CTA that never arrives)."""
 import numpy as np
 import pytest
 
@@ -29,8 +31,9 @@ def instances():
             W.wave_orbit(l_min=2, l_max=4, band=0.2, half=2.0, omega=3.0, precision=0)]
 
 
-@pytest.mark.parametrize("graph", [True, False])
-def test_batch_equals_instances_alone(lt, graph):
+@pytest.mark.parametrize("graph,mode", [(True, ("persistent", 2)), (False, ("persistent", 1)),
+                                        (True, ("per-stage", None)), (False, ("per-stage", None))])
+def test_batch_equals_instances_alone(lt, graph, mode):
     ws = instances()
     substeps = [9, 7, 16, 5, 40, 6, 11]
     alone, batched = [], []
@@ -44,8 +47,15 @@ def test_batch_equals_instances_alone(lt, graph):
     for p, n in zip(alone, substeps):
         p.run_substeps(n)
     batch = lt.Batch(batched)
+    if mode[0] == "persistent":
+        batch.set_mode(True, mode[1])
+    else:
+        batch.set_mode(False)
     batch.run(substeps[:2] + [0] * (len(ws) - 2), graph=graph)     # a first call, some plans idle
     batch.run([0, 0] + substeps[2:], graph=graph)
+    batch.wait()
+    if mode[0] == "persistent":
+        assert batch.stats()["launches"] == max(substeps[:2]) + max(substeps[2:])   # one launch per round
     for a, b, n in zip(alone, batched, substeps):
         assert a.stats()["time"] == b.stats()["time"]
         assert a.stats()["substep"] == b.stats()["substep"]
@@ -66,16 +76,45 @@ def test_batch_matches_oracle(lt, orc):
         p.set_initial(0.0)
     batch = lt.Batch(plans)
     tune = batch.autotune(rounds=2)
-    assert len(tune["grid"]) == 3
-    for p in plans:
-        p.set_initial(0.0)
-    batch.run([8, 8, 8])
-    for w, p in zip(ws, plans):
+    assert tune["mode"] in ("persistent", "per-stage") and len(tune["table"]) >= 2
+    refs = []
+    for w in ws:
         sol = orc.Solver(orc.Tree.build(w["spec"]), w["spec"], w["prob"])
         sol.set_initial(0.0)
         sol.lts_substeps(8)
-        ref = sol.state()
-        assert np.abs(p.get_state() - ref).max() / np.abs(ref).max() <= 1e-12
+        refs.append(sol.state())
+    # the tuned shape, then every shape the autotuner timed
+    for mode, shape, _ in [(tune["mode"], tune["shape"], 0.0)] + tune["table"]:
+        if mode == "persistent":
+            batch.set_mode(True, shape)
+        else:
+            batch.set_mode(False)
+            batch.set_grid(*shape)
+        for p in plans:
+            p.set_initial(0.0)
+        batch.run([8, 8, 8])
+        batch.wait()
+        for p, ref in zip(plans, refs):
+            assert np.abs(p.get_state() - ref).max() / np.abs(ref).max() <= 1e-12, (mode, shape)
+
+
+def test_grid_barrier_time_limit(lt):
+    """The persistent round's grid barrier gives up after its limit: with one CTA that
+    never arrives, every other CTA's wait runs out and LTS_ETIMEOUT comes back; the
+    batch is usable afterwards."""
+    w = W.advection_gauss(l_min=2, l_max=3)
+    plan = lt.Plan(lt.Octree(w["spec"]), w["prob"])
+    plan.set_initial(0.0)
+    batch = lt.Batch([plan])
+    assert batch.probe_barrier(-1, 0.5) == 0                 # all arrive
+    assert batch.probe_barrier(3, 0.05) == lt.LTS_ETIMEOUT   # CTA 3 never arrives
+    batch.wait()                                             # the error word was cleared
+    ref = lt.Plan(lt.Octree(w["spec"]), w["prob"])
+    ref.set_initial(0.0)
+    ref.run_substeps(4)
+    batch.run([4])
+    batch.wait()
+    assert np.array_equal(plan.get_state(), ref.get_state())
 
 
 def test_batch_rejects_mixed_streams_or_precision(lt):

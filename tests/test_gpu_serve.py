@@ -1,7 +1,9 @@
 """Continuous batching: requests that arrive while others run are admitted into
 free slots and advanced together; each request's result is the same as when it is
-solved alone (relative L-infinity <= 1e-13), and the server respects its slot
-count and device-memory budget."""
+solved alone (relative L-infinity <= 1e-13) and, for the small trees, the same as the
+CPU oracle's solve to the same time (1e-12), under both scheduling policies
+(first come first served, shortest remaining work first with paused solves); the
+server respects its slot count and device-memory budget."""
 import numpy as np
 import pytest
 
@@ -30,11 +32,12 @@ def small_requests():
     return ws, t_ends
 
 
-def test_results_same_alone_and_in_the_mix(srv):
+@pytest.mark.parametrize("policy", ["fcfs", "srpt"])
+def test_results_same_alone_and_in_the_mix(srv, policy):
     ws, t_ends = small_requests()
     reqs = [srv.Request(i, 0.002 * i, dict(spec=w["spec"], prob=w["prob"]), t) for i, (w, t) in
             enumerate(zip(ws, t_ends))]
-    server = srv.Server(slots=3, chunk=4)          # fewer slots than requests: some must wait
+    server = srv.Server(slots=3, chunk=4, policy=policy)   # fewer slots than requests: some must wait
     mixed, wall = server.serve(reqs, realtime=True)
     alone, _ = srv.serve_one_at_a_time(reqs, realtime=False)
     assert [r.rid for r in mixed] == [r.rid for r in alone] == list(range(len(reqs)))
@@ -82,3 +85,29 @@ def test_saturated_gpu_serves_first_come_first_served(srv):
     alone, _ = srv.serve_one_at_a_time(reqs, realtime=False)
     for a, b in zip(alone, res):
         assert np.array_equal(a.state, b.state)
+
+
+@pytest.mark.parametrize("policy", ["fcfs", "srpt"])
+def test_served_results_match_the_oracle(srv, orc, policy):
+    """Every served solve on a small tree (levels up to 4) equals the CPU oracle's LTS
+    solve over the same substeps, and the reached time is that of the oracle."""
+    ws, t_ends = small_requests()
+    reqs = [srv.Request(i, 0.0, dict(spec=w["spec"], prob=w["prob"]), t) for i, (w, t) in
+            enumerate(zip(ws, t_ends))]
+    server = srv.Server(slots=3, chunk=4, policy=policy, saturation=1500.0)
+    served, _ = server.serve(reqs, realtime=False)
+    checked = 0
+    for r, w in zip(served, ws):
+        assert r.t_requested == t_ends[r.rid]
+        if w["spec"]["l_max"] > 4:
+            continue
+        ot = orc.Tree.build(w["spec"])
+        sol = orc.Solver(ot, w["spec"], w["prob"])
+        sol.set_initial(0.0)
+        sol.lts_substeps(r.substeps)
+        ref = sol.state()
+        err = np.abs(r.state - ref).max() / np.abs(ref).max()
+        assert err <= 1e-12, (r.rid, err)
+        assert r.t_reached == pytest.approx(sol.time, rel=1e-13)
+        checked += 1
+    assert checked == 4
