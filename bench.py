@@ -31,8 +31,8 @@ UNIT = "node-updates/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x flops/FMA x max clock
 # DRAM bytes (read + write) per node-stage of stage_kernel<2, double> / <2, float>, from ncu
 # captures of one stage launch on the levels 4..8 wave case; None whenever the kernel changes
-STAGE_DRAM_BYTES_PER_NODE_STAGE = 117.5
-STAGE_DRAM_BYTES_PER_NODE_STAGE_MIXED = 74.3
+STAGE_DRAM_BYTES_PER_NODE_STAGE = 97.0
+STAGE_DRAM_BYTES_PER_NODE_STAGE_MIXED = 54.3
 
 
 def measured_peaks():
@@ -249,6 +249,23 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def serve_sample(args, n=32, rate=32.0):
+    """A short served stream beside the main line (NEXT-3): n small shell solves (levels
+    3..4, 736 to 3,536 octants, end times 0.5..5) arriving as a Poisson stream, served by
+    continuous batching (shortest remaining work first) and by one solve at a time,
+    first come first served; latency is arrival to the end of the solve on the GPU."""
+    from paper_2011_10570_gb300 import serve, workloads
+    raw = workloads.serving_requests(seed=4, n=n, rate=rate, lmax_choices=(4,))
+    reqs = [serve.Request(r["rid"], r["arrival"], r["work"], r["t_end"]) for r in raw]
+    out = {"requests": n, "rate_per_s": rate, "workload": "shell solves, levels 3..4 (seed 4)"}
+    server = serve.Server(slots=16, chunk=8, keep_results=False, policy="srpt")
+    res_b, wall_b = server.serve(reqs, realtime=True)
+    out["continuous_batching_srpt"] = serve.summary(res_b, wall_b)
+    res_1, wall_1 = serve.serve_one_at_a_time(reqs, realtime=True, keep_results=False)
+    out["one_at_a_time_fcfs"] = serve.summary(res_1, wall_1)
+    return out
+
+
 def run_serve(args):
     """Serving (NEXT-3): a Poisson stream of wave solves, continuous batching against
     first-come-first-served one-at-a-time solving, per arrival rate."""
@@ -263,13 +280,14 @@ def run_serve(args):
         raw = workloads.serving_requests(seed=4, n=args.serve_n, rate=rate, lmax_choices=tuple(args.serve_lmax))
         reqs = [serve.Request(r["rid"], r["arrival"], r["work"], r["t_end"]) for r in raw]
         row = {"rate_per_s": rate}
-        for sat in args.serve_saturation:
-            server = serve.Server(slots=args.serve_slots, chunk=args.serve_chunk, keep_results=False,
-                                  saturation=sat)
-            res_b, wall_b = server.serve(reqs, realtime=True)
-            row["continuous_batching_sat%g" % sat] = dict(serve.summary(res_b, wall_b),
-                                                           phases_s={k: round(v, 4) for k, v in server.phases.items()})
-            del server
+        for policy in args.serve_policy:
+            for sat in args.serve_saturation:
+                server = serve.Server(slots=args.serve_slots, chunk=args.serve_chunk, keep_results=False,
+                                      saturation=sat, policy=policy)
+                res_b, wall_b = server.serve(reqs, realtime=True)
+                row["continuous_batching_%s_sat%g" % (policy, sat)] = dict(
+                    serve.summary(res_b, wall_b), phases_s={k: round(v, 4) for k, v in server.phases.items()})
+                del server
         res_1, wall_1 = serve.serve_one_at_a_time(reqs, realtime=True, keep_results=False)
         octs = sorted(r.octants for r in res_1)
         row["one_at_a_time"] = serve.summary(res_1, wall_1)
@@ -291,6 +309,7 @@ def main():
     ap.add_argument("--no-gts", action="store_true",
                     help="skip the GTS comparison (GTS over the same physical time, and the LTS-GTS difference)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-serve", action="store_true", help="skip the short served stream beside the main line")
     ap.add_argument("--batch", type=int, default=0, help="batched mode: number of instances (64 for the C4 workload)")
     ap.add_argument("--rounds", type=int, default=64, help="batched mode: timed rounds")
     ap.add_argument("--batch-fmax", type=float, default=20.0,
@@ -302,6 +321,8 @@ def main():
                     help="finest levels the request trees draw from (5 6: about 4k to 180k octants)")
     ap.add_argument("--serve-saturation", type=float, nargs="+", default=[8192.0],
                     help="admission limit on the resident solves' mean active octants per substep")
+    ap.add_argument("--serve-policy", nargs="+", default=["fcfs", "srpt"], choices=["fcfs", "srpt"],
+                    help="admission / scheduling policies of the continuous-batching server")
     ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--serve-chunk", type=int, default=8)
     ap.add_argument("--workload", default="shell", choices=["shell", "nonlinear", "orbit"],
@@ -494,6 +515,8 @@ def main():
                               "stage_share_of_step": ks["ms"] / ms}
     if gts:
         line["gts"] = gts
+    if not args.no_serve and rank == 0:
+        line["serving"] = serve_sample(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         del plan
         torch.cuda.empty_cache()
