@@ -498,20 +498,37 @@ def main():
         per_ns = STAGE_DRAM_BYTES_PER_NODE_STAGE if args.precision == "fp64" else STAGE_DRAM_BYTES_PER_NODE_STAGE_MIXED
         traffic = per_ns * ks["node_stages"] / ks["launches"] if per_ns else None
         hbm_peak = measured_peaks().get("hbm_gbs")
+        # DRAM bytes the kernel moves per launch (ncu's per-node-stage figure for this build)
+        # over its live launch time: the HBM rate it reaches, beside the algorithmic one
+        dram_gbs = traffic / (avg_ms / 1e3) / 1e9 if traffic else None
         if args.precision == "mixed":
             gbs = ks["bytes"] / (ks["ms"] / 1e3) / 1e9
             line["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                                 "frac": gbs / hbm_peak if hbm_peak else None, "traffic": traffic,
                                 "traffic_source": "ncu dram bytes per node-stage (levels 4..8 capture) x node-stages per launch",
                                 "kernel": "stage_kernel<2, float>", "peak_source": "measured (MEASURED_PEAKS.json)",
-                                "fp64_tflops_algorithmic": achieved, "stage_share_of_step": ks["ms"] / ms}
+                                "fp64_tflops_algorithmic": achieved, "stage_share_of_step": ks["ms"] / ms,
+                                "dram_gbs_measured_bytes": dram_gbs,
+                                "dram_frac_measured_bytes": dram_gbs / hbm_peak if dram_gbs and hbm_peak else None}
         else:
+            fl = flops_per_launch / (ks["node_stages"] / ks["launches"])
             line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                               "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                              "flops_per_node_stage": fl,
+                              "flops_note": "counted from the kernel's formulas, FMA = 2 (an estimate of 65 "
+                                            "per node-stage gives frac %.3f)" % (achieved * 65 / fl / FP64_PEAK_TFLOPS),
+                              "frac_vs_fma_probe": achieved / 1.20,
+                              "fma_probe_note": "1.20 TFLOP/s: an FP64 FMA loop measured on a GB300 of this pool",
                               "traffic_source": "ncu dram bytes per node-stage (levels 4..8 capture) x node-stages per launch",
                               "kernel": "stage_kernel<2>", "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 x 2.07 GHz",
                               "hbm_gbs_algorithmic": ks["bytes"] / (ks["ms"] / 1e3) / 1e9,
-                              "hbm_peak_gbs": measured_peaks().get("hbm_gbs"),
+                              "hbm_peak_gbs": hbm_peak,
+                              "dram_gbs_measured_bytes": dram_gbs,
+                              # FP64 pipe operations (an FMA or an add is one) per node-stage of the
+                              # wave: right-hand side 41, RK4 epilogue 3.5 on average; the pipe
+                              # completes 2 per clock per SM
+                              "fp64_ops_per_node_stage": 44.5,
+                              "fp64_pipe_frac": 44.5 * ks["node_stages"] / (ks["ms"] / 1e3) / (152 * 2 * 2.070e9),
                               "stage_share_of_step": ks["ms"] / ms}
     if gts:
         line["gts"] = gts

@@ -240,13 +240,14 @@ lts_status lts_kernel_stats(lts_plan* plan, int64_t* launches, double* ms, doubl
  * substeps left performs one LTS substep of its own schedule (Alg. 2, Fig. blk_loop),
  * and the schedule is advanced on the device, so a round is a fixed launch sequence that
  * can be captured once in a CUDA graph and replayed.  Two modes (lts_batch_set_mode):
- *   persistent (the default): the whole round is one cooperative launch whose CTAs stay
+ *   persistent: the whole round is one cooperative launch whose CTAs stay
  *     resident and claim work items (the prolongations and octant-stages of all plans,
  *     stage by stage, then the reconciles) between grid-wide barriers; every barrier
  *     wait has a time limit (2 s), past which the launch is abandoned and the next
  *     lts_batch_wait returns LTS_ETIMEOUT;
- *   per-stage: each RK stage is a launch of the prolongation and one of the stage
- *     kernel over all plans, with round start / end and reconcile launches around them.
+ *   per-stage (the default): each RK stage is a launch of the prolongation and one of
+ *     the stage kernel over all plans, with round start / end and reconcile launches
+ *     around them.
  * Results equal those of running each plan alone, in either mode.  The plans must share
  * one stream and one precision; the batch keeps pointers to them (they must outlive
  * it).  Up to 1024 plans. */

@@ -1216,8 +1216,10 @@ struct lts_batch {
   cudaGraphExec_t exec = nullptr;
   int64_t launches = 0;
   bool slots = false;                // created empty with fixed capacity (attach / detach)
-  // persistent rounds: one cooperative launch per round over `grid_persistent` CTAs
-  int persistent = 1;
+  // persistent rounds: one cooperative launch per round over `grid_persistent` CTAs (off by
+  // default: the per-stage launches measured faster on the batches tested; the autotuner
+  // chooses per batch)
+  int persistent = 0;
   int grid_persistent = 0;           // resident CTAs (set at creation from the occupancy)
   int resident_max = 0;              // CTAs per SM x SMs the persistent kernel can keep resident
   int sms = 0;
@@ -1363,7 +1365,6 @@ lts_status batch_alloc(lts_batch* B, int n_slots) {
   if (e != cudaSuccess) return cuda_fail(e, "batch allocation");
   B->resident_max = per_sm * B->sms;
   B->grid_persistent = B->resident_max;
-  B->persistent = B->resident_max > 0 ? 1 : 0;
   B->plans.assign(n_slots, nullptr);
   B->args.inst = B->d_inst;
   B->args.n = n_slots;

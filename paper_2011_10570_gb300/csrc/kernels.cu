@@ -606,7 +606,7 @@ __device__ __forceinline__ int stage_item(const StageArgs& A, int it) {
   return A.list ? __ldg(A.list + A.first + it) : A.first + it;
 }
 
-// padding-map bytes of this thread's points of octant b (points tid + r * kThreads),
+// padding-map bytes of this thread's points of octant b (points tid + r * TPB),
 // four to a register
 constexpr int kSlw = (kPer + 3) / 4;
 struct Slots {
@@ -614,13 +614,14 @@ struct Slots {
   __device__ __forceinline__ unsigned operator[](int r) const { return (w[r >> 2] >> (8 * (r & 3))) & 255u; }
 };
 
+template <int TPB>
 __device__ __forceinline__ void load_slots(const StageArgs& A, int b, Slots& sl) {
   const unsigned char* __restrict__ pm = A.padmap + (long long)b * kNT;
 #pragma unroll
   for (int i = 0; i < kSlw; ++i) sl.w[i] = 0u;
 #pragma unroll
   for (int r = 0; r < kPer; ++r) {
-    const int q = threadIdx.x + r * kThreads;
+    const int q = threadIdx.x + r * TPB;
     const unsigned v = q < kNT ? unsigned(__ldg(pm + q)) : kSlotNone;
     sl.w[r >> 2] |= v << (8 * (r & 3));
   }
@@ -691,7 +692,7 @@ __device__ int stage_slots(StageSmem<NF, R, NB>& S, int nb, const StageArgs& A, 
 // and under GTS finer sources are read directly.  At stage 0 the stage input is the
 // state u itself.  Points outside the domain are zeroed (the boundary fill overwrites
 // them); points with a finer source under LTS are left to stage_finer.
-template <int NF, typename R, int NB>
+template <int NF, typename R, int NB, int TPB>
 __device__ void stage_gather(StageSmem<NF, R, NB>& S, int nb, const StageArgs& A, int lb,
                              const Slots& sl) {
   const double* u0 = A.u[(A.cur_mask >> lb) & 1];
@@ -700,7 +701,7 @@ __device__ void stage_gather(StageSmem<NF, R, NB>& S, int nb, const StageArgs& A
   const R* up_all = static_cast<const R*>(A.up);
 #pragma unroll
   for (int r = 0; r < kPer; ++r) {
-    const int q = threadIdx.x + r * kThreads;
+    const int q = threadIdx.x + r * TPB;
     if (q >= kNT) break;
     const long long packed = S.slot[nb][sl[r]];
     const int kind = int(packed & 3);
@@ -721,7 +722,7 @@ __device__ void stage_gather(StageSmem<NF, R, NB>& S, int nb, const StageArgs& A
 
 // Points with a finer source (injection) under LTS, with the coarse <- fine correction of
 // eq. fc_1 applied to the source's step-start state and stages (FP64).
-template <int NF, typename R, int NB, bool C = false>
+template <int NF, typename R, int NB, int TPB, bool C = false>
 __device__ void stage_finer(StageSmem<NF, R, NB>& S, int nb, const StageArgs& A, int lb,
                             const Slots& sl) {
   const int ls = lb + 1;
@@ -731,7 +732,7 @@ __device__ void stage_finer(StageSmem<NF, R, NB>& S, int nb, const StageArgs& A,
   const double dts = A.lc[ls].dt;
 #pragma unroll
   for (int r = 0; r < kPer; ++r) {
-    const int q = threadIdx.x + r * kThreads;
+    const int q = threadIdx.x + r * TPB;
     if (q >= kNT) break;
     const long long packed = S.slot[nb][sl[r]];
     if (int(packed & 3) != kKindFiner) continue;
@@ -756,7 +757,7 @@ __device__ __forceinline__ void orbit_centre(const StageArgs& A, int lb, R* out)
 // Physical boundary, right-hand side on the 7^3 interior (stage type R), and the stage,
 // next stage input and RK update of every node (stage_epilogue), from the complete tile
 // in buffer cb.  Barriers inside are uniform over the CTA.
-template <int NF, typename R, int NB>
+template <int NF, typename R, int NB, int TPB>
 __device__ void stage_compute(StageSmem<NF, R, NB>& S, int cb, const StageArgs& A, const int b, const int4 me) {
   const int tid = threadIdx.x;
   const int p = A.p;
@@ -824,12 +825,13 @@ __device__ void stage_compute(StageSmem<NF, R, NB>& S, int cb, const StageArgs& 
   };
   if constexpr (sizeof(R) == sizeof(double)) {
     // FP64: node order; the FP64 pipe, not shared memory, bounds this kernel
-    if (tid < kNV) {
+    for (int n = tid; n < kNV; n += TPB) {
       R kv[NF];
-      rhs_at(tid, kv);
-      finish(tid, kv);
+      rhs_at(n, kv);
+      finish(n, kv);
     }
   } else {
+    static_assert(TPB == kThreads, "g_rhs_node is laid out for kThreads threads");
     // FP32: right-hand sides in the bank-conflict-free order of g_rhs_node, staged in
     // shared memory, then the epilogue in node order (coalesced stores)
     const int n = g_rhs_node[tid];
@@ -840,7 +842,7 @@ __device__ void stage_compute(StageSmem<NF, R, NB>& S, int cb, const StageArgs& 
       for (int f = 0; f < NF; ++f) S.KV[f][n] = kv[f];
     }
     __syncthreads();
-    for (int m = tid; m < kNV; m += kThreads) {
+    for (int m = tid; m < kNV; m += TPB) {
       R kv[NF];
 #pragma unroll
       for (int f = 0; f < NF; ++f) kv[f] = S.KV[f][m];
@@ -849,41 +851,43 @@ __device__ void stage_compute(StageSmem<NF, R, NB>& S, int cb, const StageArgs& 
   }
 }
 
-// One RK stage of octant b by a CTA of kThreads threads with one tile buffer (the batch
+// One RK stage of octant b by a CTA of TPB threads with one tile buffer (the stage and batch
 // kernels): the four phases in sequence.  The caller separates consecutive calls by a
 // barrier.
-template <int NF, typename R, bool C = false>
+template <int NF, typename R, int TPB = kThreads, bool C = false>
 __device__ void stage_octant(StageSmem<NF, R, 1>& S, const StageArgs& A, const int b) {
   if (threadIdx.x < 4) S.om[threadIdx.x] = A.om[threadIdx.x];
   const int4 me = __ldg(A.tree.oct + b);
   Slots sl;
-  load_slots(A, b, sl);
+  load_slots<TPB>(A, b, sl);
   const bool any_finer = __syncthreads_or(stage_slots<NF, R, 1>(S, 0, A, b, me)) != 0;  // also publishes om
   if (threadIdx.x == 0 && A.orbit) orbit_centre<R>(A, me.w, S.orb[0]);
-  stage_gather<NF, R, 1>(S, 0, A, me.w, sl);
-  if (!A.gts && any_finer) stage_finer<NF, R, 1, C>(S, 0, A, me.w, sl);
+  stage_gather<NF, R, 1, TPB>(S, 0, A, me.w, sl);
+  if (!A.gts && any_finer) stage_finer<NF, R, 1, TPB, C>(S, 0, A, me.w, sl);
   async_wait_all();
   __syncthreads();
-  stage_compute<NF, R, 1>(S, 0, A, b, me);
+  stage_compute<NF, R, 1, TPB>(S, 0, A, b, me);
 }
 
 // Threads per CTA and CTAs per SM of the stage kernel: 352 threads (the 343 interior
-// nodes in one pass) and 5 CTAs per SM (1,760 of 2,048 threads; 38 KB of shared memory
+// nodes in one pass) and 5 CTAs per SM (1,760 of 2,048 threads; 37 KB of shared memory
 // each in FP64, 20 KB in mixed precision).  Measured slower: mixed precision with 128
-// threads and 10 CTAs per SM (13%); persistent CTAs stepping their octants with two tile
+// threads and 10 CTAs per SM (13%); FP64 with 320 threads and 6 CTAs per SM (1%: the
+// 23 nodes of a second pass); persistent CTAs stepping their octants with two tile
 // buffers, the next octant's gathers in flight during the current one's right-hand sides
 // (FP64 25%: 3 CTAs per SM fit; mixed 27%: the slot table's loads stall the whole CTA).
 template <typename R> struct StageShape {
+  static constexpr int kTPB = kThreads;
   static constexpr int kMinBlocks = 5;
 };
 
 // The stage kernel: CTA x steps octant list[first + x] (or first + x).
 template <int NF, typename R>
-__global__ void __launch_bounds__(kThreads, StageShape<R>::kMinBlocks)
+__global__ void __launch_bounds__(StageShape<R>::kTPB, StageShape<R>::kMinBlocks)
     stage_kernel(const __grid_constant__ StageArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StageSmem<NF, R, 1>& S = *reinterpret_cast<StageSmem<NF, R, 1>*>(smem_raw);
-  stage_octant<NF, R>(S, A, stage_item(A, blockIdx.x));
+  stage_octant<NF, R, StageShape<R>::kTPB>(S, A, stage_item(A, blockIdx.x));
 }
 
 // ---------------------------------------------------------------------------
@@ -1223,7 +1227,7 @@ static cudaError_t launch_stage_t(const StageArgs& a, int count, cudaStream_t s)
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  stage_kernel<NF, R><<<count, kThreads, sizeof(StageSmem<NF, R, 1>), s>>>(a);
+  stage_kernel<NF, R><<<count, StageShape<R>::kTPB, sizeof(StageSmem<NF, R, 1>), s>>>(a);
   return cudaGetLastError();
 }
 
@@ -2000,9 +2004,9 @@ __global__ void __launch_bounds__(kThreads, 3)
           }
           const int b = sargs.first + (item - __ldcg(pre + i));
           if (sargs.nf == 1)
-            stage_octant<1, R, true>(*reinterpret_cast<StageSmem<1, R, 1>*>(&S.st), sargs, b);
+            stage_octant<1, R, kThreads, true>(*reinterpret_cast<StageSmem<1, R, 1>*>(&S.st), sargs, b);
           else
-            stage_octant<2, R, true>(S.st, sargs, b);
+            stage_octant<2, R, kThreads, true>(S.st, sargs, b);
         }
         if (!grid_barrier(bar, err, limit_ns)) return;
       }
