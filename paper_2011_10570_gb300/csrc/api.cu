@@ -68,6 +68,13 @@ struct lts_plan {
   void* d_up = nullptr;                 // prolonged stage inputs [slot][nf][2197], stage type
   int* d_err = nullptr;
   unsigned char* d_padmap = nullptr;  // [N][2197] padding map (source slots), built once by padmap_kernel
+  int* d_slotmap = nullptr;             // [N][256] per octant and slot: base << 2 | kind (slotmap_kernel)
+  // finer sources: the leaves some padding map takes a point from through a child slot
+  std::vector<int32_t> dn_list;         // level order
+  int64_t dn_off[34] = {};              // per level ranges in dn_list
+  int* d_dn_list = nullptr;
+  int* d_dn_slot = nullptr;             // per octant: its position in dn_list, or -1
+  void* d_inj = nullptr;                // injected stage inputs of finer sources [dn][nf][64], stage type
   // compact shared-node maps (zip: copied nodes; hanging: interpolated nodes, per level)
   int* d_zl_dst = nullptr;
   int* d_zl_src = nullptr;
@@ -385,6 +392,8 @@ ltsoct::StageArgs stage_args(const lts_plan* P, int stage, int first, int lstar,
   a.up = P->d_up;
   a.up_slot = P->d_up_slot;
   a.padmap = P->d_padmap;
+  a.slotmap = P->d_slotmap;
+  a.inj = P->d_inj;
   a.grp = P->d_grp;
   a.gsrc = P->d_gsrc;
   a.gcode = P->d_gcode;
@@ -450,6 +459,43 @@ lts_status launch_prolong_for(lts_plan* P, const ltsoct::StageArgs& sa, int lsta
   return LTS_OK;
 }
 
+// the injection arguments of a stage (InjectArgs), all but the octant range
+ltsoct::InjectArgs inject_args(const lts_plan* P, const ltsoct::StageArgs& sa) {
+  ltsoct::InjectArgs a{};
+  a.tree = sa.tree;
+  a.inj = P->d_inj;
+  a.u[0] = sa.u[0];
+  a.u[1] = sa.u[1];
+  a.us[0] = sa.us[0];
+  a.us[1] = sa.us[1];
+  a.K = sa.K;
+  a.Uin = sa.Uin;
+  a.fstride = sa.fstride;
+  a.nf = sa.nf;
+  a.stage = sa.stage;
+  a.gts = sa.gts;
+  a.mixed = sa.mixed;
+  a.cur_mask = sa.cur_mask;
+  for (int l = 0; l < 32; ++l) a.lc[l] = sa.lc[l];
+  a.om1 = sa.om[1];
+  return a;
+}
+
+// the stage inputs of the finer sources read in this stage: those on levels > lstar (a
+// finer source of an active octant is on an active level; all of them under GTS)
+lts_status launch_inject_for(lts_plan* P, const ltsoct::StageArgs& sa, int lstar) {
+  const int lo = std::min(lstar + 1, 33);
+  const int64_t first = P->dn_off[lo], count = int64_t(P->dn_list.size()) - first;
+  if (count <= 0) return LTS_OK;
+  ltsoct::InjectArgs a = inject_args(P, sa);
+  a.list = P->d_dn_list + first;
+  a.first = int(first);
+  a.count = int(count);
+  CK(ltsoct::launch_inject(a, P->stream), "injection kernel launch");
+  P->launches++;
+  return LTS_OK;
+}
+
 // one RK stage of the octants of levels >= lstar: complete sibling groups by the
 // block kernel, the other octants by the stage kernel (or every octant by the stage
 // kernel when blocking is off)
@@ -498,6 +544,8 @@ lts_status lts_substep(lts_plan* P) {
     const ltsoct::StageArgs sa = stage_args(P, s, first, lstar, 0);
     lts_status st = launch_prolong_for(P, sa, lstar);
     if (st != LTS_OK) return st;
+    st = launch_inject_for(P, sa, lstar);
+    if (st != LTS_OK) return st;
     st = launch_stage_timed(P, sa, lstar);
     if (st != LTS_OK) return st;
   }
@@ -518,6 +566,8 @@ lts_status gts_step(lts_plan* P) {
   for (int s = 0; s < P->p; ++s) {
     const ltsoct::StageArgs sa = stage_args(P, s, 0, P->lmin, 1);
     lts_status st = launch_prolong_for(P, sa, P->lmin);
+    if (st != LTS_OK) return st;
+    st = launch_inject_for(P, sa, P->lmin);
     if (st != LTS_OK) return st;
     st = launch_stage_timed(P, sa, P->lmin);
     if (st != LTS_OK) return st;
@@ -711,6 +761,7 @@ lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_
     while (P->hang_off[l + 1] < int64_t(P->hang.size()) && P->octs[P->hang[P->hang_off[l + 1]]].l == l)
       P->hang_off[l + 1]++;
   }
+
   // coarser sources: octants with a split neighbour box.  The half-node positions
   // their finer neighbours read lie within 3 half-node units of the faces, edges
   // and corners those neighbours touch: per axis, a direction -1 / 0 / +1 covers the
@@ -774,6 +825,13 @@ lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_
     while (P->single_off[l + 1] < int64_t(P->single.size()) && P->octs[P->single[P->single_off[l + 1]]].l == l)
       P->single_off[l + 1]++;
   }
+  // the slot map packs base << 2 | kind in 32 bits: every base offset must stay below 2^29
+  if (P->N * kNV >= (int64_t(1) << 29) - 4096 ||
+      int64_t(P->up_list.size()) * P->nf * ltsoct::kNT >= (int64_t(1) << 29) - 4096) {
+    delete P;
+    return fail(LTS_EINVAL, "lts_plan_create: octree too large for the stage kernel's 32-bit source offsets "
+                            "(at most 1.5 M octants and 120 k octants with finer neighbours)");
+  }
   // reading of the CFL condition (Sec. 3.4): dt_f = cfl * node spacing of the finest level
   const double h_f = (P->spec.hi - P->spec.lo) / (6.0 * double(int64_t(1) << P->lmax));
   P->dt_f = prob->cfl * h_f;
@@ -813,6 +871,8 @@ lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_
   P->d_up_slot = static_cast<int*>(dev_alloc(P, sizeof(int) * P->N));
   P->d_up = dev_alloc(P, P->es * nup * P->nf * ltsoct::kNT);
   P->d_padmap = static_cast<unsigned char*>(dev_alloc(P, size_t(P->N) * ltsoct::kNT));
+  P->d_slotmap = static_cast<int*>(dev_alloc(P, sizeof(int) * size_t(P->N) * 256));
+  P->d_dn_slot = static_cast<int*>(dev_alloc(P, sizeof(int) * P->N));
   const size_t ng = std::max<size_t>(P->grp.size(), 1);
   P->d_grp = static_cast<int*>(dev_alloc(P, sizeof(int) * ng));
   P->d_single = static_cast<int*>(dev_alloc(P, sizeof(int) * std::max<size_t>(P->single.size(), 1)));
@@ -820,6 +880,7 @@ lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_
   P->d_gcode = static_cast<unsigned short*>(dev_alloc(P, sizeof(unsigned short) * ng * ltsoct::kBG));
   if (!P->d_oct || !P->d_nbr || !P->d_fine || !P->d_hang || !P->d_u[0] || !P->d_u[1] || !P->d_K || !P->d_err ||
       !P->d_U[0] || !P->d_U[1] || !P->d_up_list || !P->d_up_box || !P->d_up_slot || !P->d_up || !P->d_padmap ||
+      !P->d_slotmap || !P->d_dn_slot ||
       !P->d_grp || !P->d_single || !P->d_gsrc || !P->d_gcode ||
       (P->mixed && (!P->d_us[0] || !P->d_us[1]))) {
     release(P);
@@ -843,6 +904,7 @@ lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_
                                        : cudaMemcpyAsync(P->d_up_box, P->up_box.data(), sizeof(int) * P->up_box.size(),
                                                          cudaMemcpyHostToDevice, P->stream);
   cudaError_t e12 = cudaMemcpyAsync(P->d_up_slot, P->up_slot.data(), sizeof(int) * P->N, cudaMemcpyHostToDevice, P->stream);
+
   cudaError_t e5 = cudaMemsetAsync(P->d_K, 0, sbytes * P->p, P->stream);
   cudaError_t e6 = cudaMemsetAsync(P->d_u[0], 0, fbytes, P->stream);
   cudaError_t e7 = cudaMemsetAsync(P->d_u[1], 0, fbytes, P->stream);
@@ -851,6 +913,40 @@ lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_
                         ? ltsoct::launch_padmap(dev_tree(P), P->d_padmap, P->d_err, P->stream)
                         : cudaErrorInvalidValue;
   if (e13 == cudaSuccess) P->launches++;
+  // finer sources: the leaves the padding maps read through child slots (marked on the
+  // device), listed in level order
+  std::vector<unsigned char> mark(P->N, 0);
+  unsigned char* d_mark = static_cast<unsigned char*>(dev_alloc(P, std::max<size_t>(P->N, 1)));
+  cudaError_t e18 = d_mark ? cudaMemsetAsync(d_mark, 0, P->N, P->stream) : cudaErrorMemoryAllocation;
+  if (e18 == cudaSuccess && e13 == cudaSuccess) e18 = ltsoct::launch_finemark(dev_tree(P), P->d_padmap, d_mark, P->stream);
+  if (e18 == cudaSuccess) e18 = cudaMemcpyAsync(mark.data(), d_mark, P->N, cudaMemcpyDeviceToHost, P->stream);
+  if (e18 == cudaSuccess) e18 = cudaStreamSynchronize(P->stream);
+  std::vector<int32_t> dn_slot(P->N, -1);
+  for (int64_t b = 0; b < P->N && e18 == cudaSuccess; ++b)
+    if (mark[b]) {
+      dn_slot[b] = int32_t(P->dn_list.size());
+      P->dn_list.push_back(int32_t(b));
+    }
+  for (int l = 0; l <= 32; ++l) {
+    P->dn_off[l + 1] = P->dn_off[l];
+    while (P->dn_off[l + 1] < int64_t(P->dn_list.size()) && P->octs[P->dn_list[P->dn_off[l + 1]]].l == l)
+      P->dn_off[l + 1]++;
+  }
+  const size_t ndn = std::max<size_t>(P->dn_list.size(), 1);
+  P->d_dn_list = static_cast<int*>(dev_alloc(P, sizeof(int) * ndn));
+  P->d_inj = dev_alloc(P, P->es * ndn * P->nf * 64);
+  if (e18 == cudaSuccess && (!P->d_dn_list || !P->d_inj)) e18 = cudaErrorMemoryAllocation;
+  if (e18 == cudaSuccess && !P->dn_list.empty())
+    e18 = cudaMemcpyAsync(P->d_dn_list, P->dn_list.data(), sizeof(int) * P->dn_list.size(), cudaMemcpyHostToDevice,
+                          P->stream);
+  if (e18 == cudaSuccess)
+    e18 = cudaMemcpyAsync(P->d_dn_slot, dn_slot.data(), sizeof(int) * P->N, cudaMemcpyHostToDevice, P->stream);
+  cudaError_t e19 = (e12 == cudaSuccess && e18 == cudaSuccess && e13 == cudaSuccess)
+                        ? ltsoct::launch_slotmap(dev_tree(P), P->d_up_slot, P->d_dn_slot, P->nf, P->d_slotmap, P->d_err,
+                                                 P->stream)
+                        : cudaErrorInvalidValue;
+  if (e19 == cudaSuccess) P->launches++;
+  if (e18 == cudaSuccess) e18 = cudaStreamSynchronize(P->stream);  // dn_slot (host) goes out of scope
   cudaError_t e15 = P->grp.empty() ? cudaSuccess
                                    : cudaMemcpyAsync(P->d_grp, P->grp.data(), sizeof(int) * P->grp.size(),
                                                      cudaMemcpyHostToDevice, P->stream);
@@ -866,7 +962,7 @@ lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_
   int herr = 0;
   cudaError_t e14 = cudaMemcpyAsync(&herr, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, P->stream);
   cudaError_t e8 = cudaStreamSynchronize(P->stream);
-  for (cudaError_t e : {e1, e2, e3, e4, e5, e6, e7, e9, e10, e11, e12, e13, e15, e16, e17, e14, e8})
+  for (cudaError_t e : {e1, e2, e3, e4, e5, e6, e7, e9, e10, e11, e12, e13, e15, e16, e17, e18, e19, e14, e8})
     if (e != cudaSuccess) {
       release(P);
       delete P;
@@ -875,7 +971,8 @@ lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_
   if (herr) {
     release(P);
     delete P;
-    return fail(LTS_EINTERNAL, "lts_plan_create: padding map: a source lay outside its octant (unbalanced tree)");
+    return fail(LTS_EINTERNAL, "lts_plan_create: padding or slot map: a source lay outside its octant, or lacked "
+                               "prolonged or injected inputs (code " + std::to_string(herr) + ")");
   }
   const lts_status st = build_node_maps(P);
   if (st != LTS_OK) {
@@ -1255,7 +1352,7 @@ lts_status batch_round(lts_batch* B, bool graph) {
   } else {
     CK(launch_round(B), "batch round launch");
   }
-  B->launches += B->persistent ? 1 : 3 + 2 * B->pmax + B->lmax_all;
+  B->launches += B->persistent ? 1 : 3 + 3 * B->pmax + B->lmax_all;
   return LTS_OK;
 }
 
@@ -1311,6 +1408,7 @@ ltsoct::BatchInst batch_descriptor(lts_plan* P) {
     a.mixed = P->mixed;
     for (int l = 0; l < 32; ++l) a.lc[l] = I.st[s].lc[l];
     for (int r = 0; r < 4; ++r) a.om[r] = I.st[s].om[r];
+    I.in[s] = inject_args(P, I.st[s]);  // octant range and schedule set per round on the device
   }
   for (ltsoct::SyncArgs* y : {&I.zip, &I.hang}) {
     y->tree = I.st[0].tree;
@@ -1326,10 +1424,12 @@ ltsoct::BatchInst batch_descriptor(lts_plan* P) {
   }
   I.up_list = P->d_up_list;
   I.hang_list = P->d_hang;
+  I.dn_list = P->d_dn_list;
   for (int l = 0; l < 34; ++l) {
     I.off[l] = int(P->off[l]);
     I.up_off[l] = int(P->up_off[l]);
     I.hang_off[l] = int(P->hang_off[l]);
+    I.dn_off[l] = int(P->dn_off[l]);
   }
   I.n = int(P->N);
   I.nf = P->nf;
@@ -1345,7 +1445,7 @@ ltsoct::BatchInst batch_descriptor(lts_plan* P) {
 }
 
 lts_status batch_alloc(lts_batch* B, int n_slots) {
-  const size_t pre_ints = size_t(ltsoct::kMaxBatch + 1) * (4 + 4 + 1 + ltsoct::kMaxLevel + 2) + 8;
+  const size_t pre_ints = size_t(ltsoct::kMaxBatch + 1) * (4 + 4 + 4 + 1 + ltsoct::kMaxLevel + 2) + 12;
   std::vector<ltsoct::BatchInst> empty(n_slots);
   std::memset(empty.data(), 0, sizeof(ltsoct::BatchInst) * n_slots);
   cudaError_t e = ltsoct::prepare_batch_kernels();
@@ -1370,9 +1470,10 @@ lts_status batch_alloc(lts_batch* B, int n_slots) {
   B->args.n = n_slots;
   B->args.stage_pre = B->d_pre;
   B->args.prol_pre = B->d_pre + 4 * (ltsoct::kMaxBatch + 1);
-  B->args.zip_pre = B->d_pre + 8 * (ltsoct::kMaxBatch + 1);
-  B->args.hang_pre = B->d_pre + 9 * (ltsoct::kMaxBatch + 1);
-  B->args.next_item = B->d_pre + (ltsoct::kMaxBatch + 1) * (4 + 4 + 1 + ltsoct::kMaxLevel + 2);
+  B->args.inj_pre = B->d_pre + 8 * (ltsoct::kMaxBatch + 1);
+  B->args.zip_pre = B->d_pre + 12 * (ltsoct::kMaxBatch + 1);
+  B->args.hang_pre = B->d_pre + 13 * (ltsoct::kMaxBatch + 1);
+  B->args.next_item = B->d_pre + (ltsoct::kMaxBatch + 1) * (4 + 4 + 4 + 1 + ltsoct::kMaxLevel + 2);
   return LTS_OK;
 }
 

@@ -330,8 +330,7 @@ constexpr int kSlots = 256;  // slot values of a padding-map entry (kSlotNone = 
 template <int NF, typename R, int NB>
 struct StageSmem {
   R T[NB][NF][kNT];               // padded tiles
-  long long slot[NB][kSlots];     // per slot: base << 2 | kind (stage_slots)
-  StageTerms om[4];               // correction terms of this stage per relation
+  int slot[NB][kSlots];           // per slot: base << 2 | kind (the plan's slot map)
   R KV[sizeof(R) == sizeof(float) ? NF : 1][sizeof(R) == sizeof(float) ? kNV : 1];  // FP32: staged right-hand sides
   R orb[NB][2];                   // orbit centre x_1 at the octant's stage time
 };
@@ -341,23 +340,34 @@ constexpr unsigned kExterior = 1u << 15;  // exterior flag of the 16-bit codes o
 // The padding map holds one byte per padded point: the slot of its source in the
 // octant's neighbour view (kSlotNone outside the domain).  Where the point lies in the
 // source follows from the slot's relation to the octant.  With (i, j, k) the point in
-// the octant's node units (each in [-3, 9]) and lin7 = i + 7 j + 49 k:
-//   same level, neighbour box d:        node (i, j, k) - 6 d           -> base + lin7
-//   finer, child c of the split box d:  node 2 (i, j, k) - 12 d - 6 c  -> base + 2 lin7
-//   coarser leaf N (its prolonged 13^3 block, half-node units of N):
-//                                       (i, j, k) + 6 (A_b - A_N) / e_b -> base + q
+// the octant's node units (each in [-3, 9]):
+//   same level, neighbour box d: node (i, j, k) - 6 d of the stage inputs
+//                                -> base + lin7,  lin7 = i + 7 j + 49 k
+//   finer, child c of the split box d: node 2 ((i, j, k) - 6 d - 3 c), even, whose stage
+//                                input the injection pass put at even-node index
+//                                (i, j, k) - 6 d - 3 c (4 per axis)
+//                                -> base + lin4,  lin4 = i + 4 j + 16 k
+//   coarser leaf N: its prolonged 13^3 block, half-node (i, j, k) + 6 (A_b - A_N) / e_b
+//                                -> base + q
 // q being the point's tile index (i + 3) + 13 (j + 3) + 169 (k + 3); base is fixed per
-// slot and octant (stage_slots).
-__device__ __forceinline__ int lin7_of(int q) {
-  const int k = q / 169, rem = q - 169 * k;
-  const int j = rem / 13, i = rem - 13 * j;
-  return i + 7 * j + 49 * k - 171;  // (i, j, k) counted from -3: 3 + 7 * 3 + 49 * 3 = 171
+// slot and octant (the plan's slot map, slotmap_kernel).
+__device__ __forceinline__ void tile_ijk(int q, int& i, int& j, int& k) {
+  k = q / 169;
+  const int rem = q - 169 * k;
+  j = rem / 13;
+  i = rem - 13 * j;
+  i -= 3;
+  j -= 3;
+  k -= 3;
 }
 
-// element of point q in the source of its slot, from the slot's packed base << 2 | kind
-__device__ __forceinline__ long long slot_element(long long packed, int kind, int q) {
+// element of point q in the source array of its slot, from the slot's packed base << 2 | kind
+__device__ __forceinline__ long long slot_element(int packed, int kind, int q) {
   const long long base = packed >> 2;
-  return base + (kind == kKindCoarser ? q : (kind == kKindFiner ? 2 : 1) * lin7_of(q));
+  if (kind == kKindCoarser) return base + q;
+  int i, j, k;
+  tile_ijk(q, i, j, k);
+  return base + (kind == kKindFiner ? i + 4 * j + 16 * k : i + 7 * j + 49 * k);
 }
 
 constexpr int kPer = (kNT + kThreads - 1) / kThreads;  // padded points per thread of a stage CTA
@@ -627,71 +637,118 @@ __device__ __forceinline__ void load_slots(const StageArgs& A, int b, Slots& sl)
   }
 }
 
-// One RK stage of an octant (Alg. 2 compute_stage, or Alg. 1 when A.gts), in four
+// One RK stage of an octant (Alg. 2 compute_stage, or Alg. 1 when A.gts), in three
 // phases over a tile buffer of the CTA:
-//   stage_slots    the octant's neighbour view: kind and base of every slot, from the tree
+//   stage_slots    the octant's neighbour view: kind and base of every slot (the plan's
+//                  slot map)
 //   stage_gather   the padded tile (Sec. 3.3, Fig. unzip): asynchronous copies of the
-//                  sources' stage inputs (coarser sources: their prolonged inputs)
-//   stage_finer    points with a finer source under LTS: injection with the time
-//                  correction of eq. fc_1 (FP64)
+//                  sources' stage inputs (coarser sources: their prolonged inputs; finer
+//                  sources: their injected inputs)
 //   stage_compute  physical boundary, right-hand side, RK stage and update
-// Between the phases the caller synchronises (stage_octant, stage_kernel).
+// Between the phases the caller synchronises (stage_octant).
 
-// Returns 1 if some slot holds a finer leaf.  No barrier inside.
+// Per slot of octant b's neighbour view, base << 2 | kind (slotmap_kernel).  No barrier
+// inside.
 template <int NF, typename R, int NB>
-__device__ int stage_slots(StageSmem<NF, R, NB>& S, int nb, const StageArgs& A, int b, int4 me) {
-  const int lb = me.w;
-  const int sh = kDepth - lb;  // log2 of the octant's edge
-  int my_finer = 0;
-  for (int t = threadIdx.x; t < kSlots; t += blockDim.x) {
-    int kind = kKindNone;
-    long long base = 0;
-    if (t == 13) {
-      kind = kKindSame;
-      base = (long long)b * kNV;
-    } else if (t < 27) {
-      // the leaf covering the same-size box in direction d = t (same level or coarser),
-      // < 0: outside the domain, or a box with children
-      const int leaf = __ldg(A.tree.nbr + (long long)b * 27 + t);
-      if (leaf >= 0) {
-        const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
-        const int4 so = __ldg(A.tree.oct + leaf);
-        if (so.w == lb) {
-          kind = kKindSame;
-          base = (long long)leaf * kNV - 6 * (dx + 7 * dy + 49 * dz);
-        } else if (so.w == lb - 1) {
-          const int us = __ldg(A.up_slot + leaf);
-          if (us >= 0) {
-            kind = kKindCoarser;
-            const int mx = (me.x - so.x) >> sh, my = (me.y - so.y) >> sh, mz = (me.z - so.z) >> sh;
-            base = (long long)us * NF * kNT - 549 + 6 * (mx + 13 * my + 169 * mz);
-          } else {
-            atomicOr(A.err, 2);  // a coarser source without prolonged inputs: never on a valid plan
+__device__ __forceinline__ void stage_slots(StageSmem<NF, R, NB>& S, int nb, const StageArgs& A, int b) {
+  const int* __restrict__ row = A.slotmap + (long long)b * kSlots;
+  for (int t = threadIdx.x; t < kSlots; t += blockDim.x) S.slot[nb][t] = __ldg(row + t);
+}
+
+// The slot map of one octant (once per plan): for each slot of its neighbour view, the
+// kind of its leaf (same level, coarser, finer, none) and the base offset of the array
+// the stage kernel reads it from (see slot_element): the stage inputs (same level), the
+// prolonged inputs of a coarser source (slot up_slot[leaf]), or the injected inputs of a
+// finer source (slot dn_slot[leaf]; a finer leaf that no padding map reads has none).
+__global__ void __launch_bounds__(256) slotmap_kernel(const DevTree T, const int* __restrict__ up_slot,
+                                                      const int* __restrict__ dn_slot, int nf, int* __restrict__ out,
+                                                      int* err) {
+  for (int b = blockIdx.x; b < T.n; b += gridDim.x) {
+    const int4 me = T.oct[b];
+    const int lb = me.w;
+    const int sh = kDepth - lb;  // log2 of the octant's edge
+    for (int t = threadIdx.x; t < kSlots; t += blockDim.x) {
+      int kind = kKindNone;
+      long long base = 0;
+      if (t == 13) {
+        kind = kKindSame;
+        base = (long long)b * kNV;
+      } else if (t < 27) {
+        // the leaf covering the same-size box in direction d = t (same level or coarser),
+        // < 0: outside the domain, or a box with children
+        const int leaf = T.nbr[(long long)b * 27 + t];
+        if (leaf >= 0) {
+          const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
+          const int4 so = T.oct[leaf];
+          if (so.w == lb) {
+            kind = kKindSame;
+            base = (long long)leaf * kNV - 6 * (dx + 7 * dy + 49 * dz);
+          } else if (so.w == lb - 1) {
+            const int us = up_slot[leaf];
+            if (us >= 0) {
+              kind = kKindCoarser;
+              const int mx = (me.x - so.x) >> sh, my = (me.y - so.y) >> sh, mz = (me.z - so.z) >> sh;
+              base = (long long)us * nf * kNT - 549 + 6 * (mx + 13 * my + 169 * mz);
+            } else {
+              atomicOr(err, 2);  // a coarser source without prolonged inputs: never on a valid plan
+            }
+          }
+        }
+      } else if (t < 27 + 27 * 8) {  // slots 243..255 hold no leaf
+        const int d = (t - 27) >> 3, c = (t - 27) & 7;
+        const int e = T.nbr[(long long)b * 27 + d];
+        const int leaf = e <= -2 ? T.fine[(long long)(-e - 2) * 8 + c] : -1;
+        if (leaf >= 0) {
+          // dn_slot < 0: no padding map reads this leaf (nor this octant's), the slot stays unused
+          const int ds = dn_slot[leaf];
+          if (ds >= 0) {
+            const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+            const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+            kind = kKindFiner;
+            base = (long long)ds * nf * 64 - ((6 * dx + 3 * cx) + 4 * (6 * dy + 3 * cy) + 16 * (6 * dz + 3 * cz));
           }
         }
       }
-    } else if (t < 27 + 27 * 8) {  // slots 243..255 hold no leaf
-      const int d = (t - 27) >> 3, c = (t - 27) & 7;
-      const int e = __ldg(A.tree.nbr + (long long)b * 27 + d);
-      const int leaf = e <= -2 ? __ldg(A.tree.fine + (long long)(-e - 2) * 8 + c) : -1;
-      if (leaf >= 0) {
-        const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
-        const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
-        kind = kKindFiner;
-        base = (long long)leaf * kNV - 6 * ((2 * dx + cx) + 7 * (2 * dy + cy) + 49 * (2 * dz + cz));
-        my_finer = 1;
-      }
+      out[(long long)b * kSlots + t] = int(base * 4 + kind);  // |base| < 2^29: checked by the plan
     }
-    S.slot[nb][t] = base * 4 + kind;
   }
-  return my_finer;
+}
+
+// The finer sources of the padding maps: mark[leaf] = 1 for every leaf that some octant's
+// padding map takes a point from through a child slot (a finer leaf).  Such a leaf need not
+// touch the octant: on the face between two finer siblings the padding rule may pick the
+// far one.
+__global__ void __launch_bounds__(256) finemark_kernel(const DevTree T, const unsigned char* __restrict__ padmap,
+                                                       unsigned char* __restrict__ mark) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)T.n * kNT;
+       e += (long long)gridDim.x * blockDim.x) {
+    const unsigned slot = padmap[e];
+    if (slot < 27u || slot >= kSlotNone) continue;
+    const long long b = e / kNT;
+    const int d = int(slot - 27u) >> 3, c = int(slot - 27u) & 7;
+    const int box = T.nbr[b * 27 + d];
+    const int leaf = box <= -2 ? T.fine[(long long)(-box - 2) * 8 + c] : -1;
+    if (leaf >= 0) mark[leaf] = 1;
+  }
+}
+
+cudaError_t launch_finemark(const DevTree& t, const unsigned char* padmap, unsigned char* mark, cudaStream_t s) {
+  if (t.n <= 0) return cudaSuccess;
+  finemark_kernel<<<152 * 16, 256, 0, s>>>(t, padmap, mark);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slotmap(const DevTree& t, const int* up_slot, const int* dn_slot, int nf, int* out, int* err,
+                           cudaStream_t s) {
+  if (t.n <= 0) return cudaSuccess;
+  slotmap_kernel<<<t.n < 152 * 8 ? t.n : 152 * 8, 256, 0, s>>>(t, up_slot, dn_slot, nf, out, err);
+  return cudaGetLastError();
 }
 
 // The tile's gathers into buffer nb: same-level (and own) sources read the stage
-// inputs, coarser sources their prolonged stage inputs (prepared by prolong_kernel),
-// and under GTS finer sources are read directly.  At stage 0 the stage input is the
-// state u itself.  Points outside the domain are zeroed (the boundary fill overwrites
-// them); points with a finer source under LTS are left to stage_finer.
+// inputs, coarser sources their prolonged stage inputs (prolong_kernel), finer sources
+// their injected stage inputs (inject_kernel).  At stage 0 the stage input is the state
+// u itself.  Points outside the domain are zeroed (the boundary fill overwrites them).
 template <int NF, typename R, int NB, int TPB>
 __device__ void stage_gather(StageSmem<NF, R, NB>& S, int nb, const StageArgs& A, int lb,
                              const Slots& sl) {
@@ -699,49 +756,77 @@ __device__ void stage_gather(StageSmem<NF, R, NB>& S, int nb, const StageArgs& A
   const float* us0 = A.us[(A.cur_mask >> lb) & 1];
   const R* st_in = A.stage == 0 ? state_array<R>(u0, us0) : static_cast<const R*>(A.Uin);
   const R* up_all = static_cast<const R*>(A.up);
+  const R* inj_all = static_cast<const R*>(A.inj);
 #pragma unroll
   for (int r = 0; r < kPer; ++r) {
     const int q = threadIdx.x + r * TPB;
     if (q >= kNT) break;
-    const long long packed = S.slot[nb][sl[r]];
-    const int kind = int(packed & 3);
+    const int packed = S.slot[nb][sl[r]];
+    const int kind = packed & 3;
     if (kind == kKindCoarser) {
       const R* up = up_all + slot_element(packed, kind, q);
 #pragma unroll
       for (int f = 0; f < NF; ++f) async_copy(&S.T[nb][f][q], up + f * kNT);
-    } else if (kind == kKindSame || (kind == kKindFiner && A.gts)) {
+    } else if (kind == kKindSame) {
       const R* src = st_in + slot_element(packed, kind, q);
 #pragma unroll
       for (int f = 0; f < NF; ++f) async_copy(&S.T[nb][f][q], src + f * A.fstride);
-    } else if (kind == kKindNone) {
+    } else if (kind == kKindFiner) {
+      const R* src = inj_all + slot_element(packed, kind, q);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) async_copy(&S.T[nb][f][q], src + f * 64);
+    } else {
 #pragma unroll
       for (int f = 0; f < NF; ++f) S.T[nb][f][q] = 0;
     }
   }
 }
 
-// Points with a finer source (injection) under LTS, with the coarse <- fine correction of
-// eq. fc_1 applied to the source's step-start state and stages (FP64).
-template <int NF, typename R, int NB, int TPB, bool C = false>
-__device__ void stage_finer(StageSmem<NF, R, NB>& S, int nb, const StageArgs& A, int lb,
-                            const Slots& sl) {
-  const int ls = lb + 1;
-  const double* ub = A.u[(A.cur_mask >> ls) & 1];
-  const R* K = static_cast<const R*>(A.K);
+// Injection pass (Fig. unzip, fine -> coarse) of one finer source b (every thread of a
+// CTA, item slot = its position in the plan's list of octants with a coarser neighbour):
+// the stage input at each of its 64 even nodes as a coarser neighbour reads it, under LTS
+// u + dt_b sum_j omega[1][s][j] k_j of b's own step (the coarse <- fine correction of
+// eq. fc_1, FP64), under GTS the stage input itself.
+template <int NF, typename R, bool C = false>
+__device__ void inject_octant(const InjectArgs& A, const int b, const int slot) {
+  const int ls = A.tree.oct[b].w;
+  const int cur = (A.cur_mask >> ls) & 1;
   const long long kstride = (long long)A.nf * A.fstride;
-  const double dts = A.lc[ls].dt;
-#pragma unroll
-  for (int r = 0; r < kPer; ++r) {
-    const int q = threadIdx.x + r * TPB;
-    if (q >= kNT) break;
-    const long long packed = S.slot[nb][sl[r]];
-    if (int(packed & 3) != kKindFiner) continue;
-    const long long off = slot_element(packed, kKindFiner, q);
-#pragma unroll
-    for (int f = 0; f < NF; ++f)
-      S.T[nb][f][q] =
-          static_cast<R>(corrected_value<R, C>(ub + f * A.fstride + off, K + f * A.fstride + off, kstride, S.om[1], dts));
+  const R* K = static_cast<const R*>(A.K);
+  R* out = static_cast<R*>(A.inj) + (long long)slot * NF * 64;
+  for (int t = threadIdx.x; t < NF * 64; t += blockDim.x) {
+    const int f = t >> 6, e = t & 63;
+    const int node = 2 * (e & 3) + 14 * ((e >> 2) & 3) + 98 * (e >> 4);
+    const long long off = (long long)b * kNV + node + f * A.fstride;
+    R v;
+    if (!A.gts) {
+      v = static_cast<R>(corrected_value<R, C>(A.u[cur] + off, K + off, kstride, A.om1, A.lc[ls].dt));
+    } else if (A.stage == 0) {
+      v = sizeof(R) == sizeof(double) ? R(ld_in<C>(A.u[cur] + off)) : R(ld_in<C>(A.us[cur] + off));
+    } else {
+      v = ld_in<C>(static_cast<const R*>(A.Uin) + off);
+    }
+    out[f * 64 + e] = v;
   }
+}
+
+template <int NF, typename R>
+__global__ void __launch_bounds__(128) inject_kernel(const __grid_constant__ InjectArgs A) {
+  for (int item = blockIdx.x; item < A.count; item += gridDim.x)
+    inject_octant<NF, R>(A, __ldg(A.list + item), A.first + item);
+}
+
+template <int NF, typename R>
+static cudaError_t launch_inject_t(const InjectArgs& a, cudaStream_t s) {
+  const int grid = a.count < 152 * 16 ? a.count : 152 * 16;
+  inject_kernel<NF, R><<<grid, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inject(const InjectArgs& a, cudaStream_t s) {
+  if (a.count <= 0) return cudaSuccess;
+  if (a.nf == 1) return a.mixed ? launch_inject_t<1, float>(a, s) : launch_inject_t<1, double>(a, s);
+  return a.mixed ? launch_inject_t<2, float>(a, s) : launch_inject_t<2, double>(a, s);
 }
 
 // orbit centre x_1 = R (cos W t_s, sin W t_s, 0) at the stage time t_s = t_b + c_s dt of
@@ -854,16 +939,15 @@ __device__ void stage_compute(StageSmem<NF, R, NB>& S, int cb, const StageArgs& 
 // One RK stage of octant b by a CTA of TPB threads with one tile buffer (the stage and batch
 // kernels): the four phases in sequence.  The caller separates consecutive calls by a
 // barrier.
-template <int NF, typename R, int TPB = kThreads, bool C = false>
+template <int NF, typename R, int TPB = kThreads>
 __device__ void stage_octant(StageSmem<NF, R, 1>& S, const StageArgs& A, const int b) {
-  if (threadIdx.x < 4) S.om[threadIdx.x] = A.om[threadIdx.x];
   const int4 me = __ldg(A.tree.oct + b);
   Slots sl;
   load_slots<TPB>(A, b, sl);
-  const bool any_finer = __syncthreads_or(stage_slots<NF, R, 1>(S, 0, A, b, me)) != 0;  // also publishes om
+  stage_slots<NF, R, 1>(S, 0, A, b);
   if (threadIdx.x == 0 && A.orbit) orbit_centre<R>(A, me.w, S.orb[0]);
+  __syncthreads();
   stage_gather<NF, R, 1, TPB>(S, 0, A, me.w, sl);
-  if (!A.gts && any_finer) stage_finer<NF, R, 1, TPB, C>(S, 0, A, me.w, sl);
   async_wait_all();
   __syncthreads();
   stage_compute<NF, R, 1, TPB>(S, 0, A, b, me);
@@ -1051,9 +1135,14 @@ __global__ void __launch_bounds__(kBlockThreads, (sizeof(R) == 8 ? 2 : 4))
 #pragma unroll
         for (int f = 0; f < NF; ++f) async_copy(&S.T[f][q], up + f * kNT);
       } else if (rel_code == 1 || A.gts) {
+        // under GTS a finer source's stage-0 input is its own level's state (levels may sit in
+        // different halves of the double-buffered state after LTS substeps)
+        const R* sin = (rel_code == 2 && s == 0)
+                           ? state_array<R>(A.u[(A.cur_mask >> (lb + 1)) & 1], A.us[(A.cur_mask >> (lb + 1)) & 1])
+                           : st_in;
         const long long off = (long long)src * kNV + (rx >> 1) + 7 * (ry >> 1) + 49 * (rz >> 1);
 #pragma unroll
-        for (int f = 0; f < NF; ++f) async_copy(&S.T[f][q], st_in + f * A.fstride + off);
+        for (int f = 0; f < NF; ++f) async_copy(&S.T[f][q], sin + f * A.fstride + off);
       } else {
         S.any_finer = 1;
       }
@@ -1738,20 +1827,28 @@ __device__ void round_begin_body(const BatchArgs& B) {
       P.count = hi >= lo ? I.up_off[hi + 1] - I.up_off[lo] : 0;
       P.lstar = lstar;
       P.cur_mask = I.cur_mask;
+      // finer sources of the active octants: the padding maps' finer leaves on levels > l*
+      InjectArgs& J = I.in[s];
+      J.first = I.dn_off[lstar + 1];
+      J.list = I.dn_list + J.first;
+      J.count = I.dn_off[I.lmax + 1] - J.first;
+      J.cur_mask = I.cur_mask;
     }
   }
   __syncthreads();
-  if (threadIdx.x < 8) B.next_item[threadIdx.x] = 0;
+  if (threadIdx.x < 12) B.next_item[threadIdx.x] = 0;
   if (threadIdx.x == 0) {
     for (int s = 0; s < 4; ++s) {
       int* sp = B.stage_pre + s * (kMaxBatch + 1);
       int* pp = B.prol_pre + s * (kMaxBatch + 1);
-      sp[0] = pp[0] = 0;
+      int* ip = B.inj_pre + s * (kMaxBatch + 1);
+      sp[0] = pp[0] = ip[0] = 0;
       for (int k = 0; k < B.n; ++k) {
         const BatchInst& I = B.inst[k];
         const bool on = I.active && s < I.p;
         sp[k + 1] = sp[k] + (on ? I.n - I.off[I.lstar] : 0);
         pp[k + 1] = pp[k] + (on ? I.pr[s].count : 0);
+        ip[k + 1] = ip[k] + (on ? I.in[s].count : 0);
       }
     }
   }
@@ -1865,6 +1962,30 @@ __global__ void __launch_bounds__(256) batch_prolong_kernel(const __grid_constan
   }
 }
 
+template <typename R>
+__global__ void __launch_bounds__(128) batch_inject_kernel(const __grid_constant__ BatchArgs B, int stage) {
+  __shared__ InjectArgs args;
+  __shared__ int s_item;
+  const int* pre = B.inj_pre + stage * (kMaxBatch + 1);
+  const int total = pre[B.n];
+  int cur = -1;
+  for (;;) {
+    const int item = claim_item(B.next_item + 8 + stage, &s_item);
+    if (item >= total) break;
+    const int i = batch_find(pre, B.n + 1, item);
+    if (i != cur) {
+      copy_args(&args, &B.inst[i].in[stage]);
+      __syncthreads();
+      cur = i;
+    }
+    const int k = item - pre[i];
+    if (args.nf == 1)
+      inject_octant<1, R>(args, __ldg(args.list + k), args.first + k);
+    else
+      inject_octant<2, R>(args, __ldg(args.list + k), args.first + k);
+  }
+}
+
 __global__ void __launch_bounds__(128) batch_zip_kernel(const __grid_constant__ BatchArgs B) {
   __shared__ SyncSmem S;
   const int total = B.zip_pre[B.n];
@@ -1960,6 +2081,7 @@ __global__ void __launch_bounds__(kThreads, 3)
   BatchSmem<R>& S = *reinterpret_cast<BatchSmem<R>*>(smem_raw);
   __shared__ StageArgs sargs;
   __shared__ ProlongArgs pargs;
+  __shared__ InjectArgs jargs;
   __shared__ SyncArgs yargs;
   __shared__ int s_item;
   if (blockIdx.x == 0) round_begin_body(B);
@@ -1985,8 +2107,30 @@ __global__ void __launch_bounds__(kThreads, 3)
           else
             prolong_octant<2, R, true>(S.pr, pargs, b);
         }
-        if (!grid_barrier(bar, err, limit_ns)) return;
       }
+      // injection of the finer sources of every instance, in the same phase
+      const int* ipre = B.inj_pre + st * (kMaxBatch + 1);
+      const int itotal = __ldcg(ipre + B.n);
+      if (itotal > 0) {
+        int cur = -1;
+        for (;;) {
+          const int item = claim_item(B.next_item + 8 + st, &s_item);
+          if (item >= itotal) break;
+          const int i = batch_find<true>(ipre, B.n + 1, item);
+          if (i != cur) {
+            copy_args<true>(&jargs, &B.inst[i].in[st]);
+            __syncthreads();
+            cur = i;
+          }
+          const int k = item - __ldcg(ipre + i);
+          if (jargs.nf == 1)
+            inject_octant<1, R, true>(jargs, __ldg(jargs.list + k), jargs.first + k);
+          else
+            inject_octant<2, R, true>(jargs, __ldg(jargs.list + k), jargs.first + k);
+        }
+      }
+      if (total > 0 || itotal > 0)
+        if (!grid_barrier(bar, err, limit_ns)) return;
     }
     {  // the stage over the active octants of every instance
       const int* pre = B.stage_pre + st * (kMaxBatch + 1);
@@ -2004,9 +2148,9 @@ __global__ void __launch_bounds__(kThreads, 3)
           }
           const int b = sargs.first + (item - __ldcg(pre + i));
           if (sargs.nf == 1)
-            stage_octant<1, R, kThreads, true>(*reinterpret_cast<StageSmem<1, R, 1>*>(&S.st), sargs, b);
+            stage_octant<1, R, kThreads>(*reinterpret_cast<StageSmem<1, R, 1>*>(&S.st), sargs, b);
           else
-            stage_octant<2, R, kThreads, true>(S.st, sargs, b);
+            stage_octant<2, R, kThreads>(S.st, sargs, b);
         }
         if (!grid_barrier(bar, err, limit_ns)) return;
       }
@@ -2092,6 +2236,7 @@ static cudaError_t batch_round_t(const BatchArgs& a, int pmax, int lmax_all, int
   batch_round_begin<<<1, kMaxBatch, 0, s>>>(a);
   for (int st = 0; st < pmax; ++st) {
     batch_prolong_kernel<R><<<gp, 256, smem_prol, s>>>(a, st);
+    batch_inject_kernel<R><<<gp, 128, 0, s>>>(a, st);
     batch_stage_kernel<R><<<gs, kThreads, smem_stage, s>>>(a, st);
   }
   batch_round_end<<<1, kMaxBatch, 0, s>>>(a);

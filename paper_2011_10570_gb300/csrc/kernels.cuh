@@ -90,6 +90,8 @@ struct StageArgs {
   float* us[2];          // mixed: FP32 copies of u[2], kept equal to float(u) (stage inputs read them)
   const int* up_slot;    // slot of an octant in `up` (-1: not a coarser source)
   const unsigned char* padmap;  // [N][2197]: slot of the source of every padded point in the neighbour view
+  const int* slotmap;    // [N][256]: per octant and slot, base << 2 | kind (built once per plan)
+  const void* inj;       // finer sources' stage inputs at their even nodes, [slot][nf][64], stage type
   const int* list;         // stage_kernel: work item x is octant list[first + x] (nullptr: first + x)
   // block kernel (Sec. 3.2.5 octree-to-block decomposition): CTA x steps the complete
   // sibling group grp[first + x] (8 consecutive octants) as one 13^3-node block
@@ -126,6 +128,27 @@ struct ProlongArgs {
   int gts;
   LevelConst lc[32];
   StageTerms om[4];
+};
+
+// Stage inputs of finer sources (Fig. unzip, fine -> coarse injection) for one stage:
+// every listed octant is a finer leaf some coarser octant's padding map reads; its stage
+// inputs at its 64 even nodes (the points a coarser octant's padded block can hold) are
+// formed once, with the coarse <- fine time correction of eq. fc_1 under LTS (FP64), or
+// copied from the stage inputs under GTS, into inj[first + item][nf][64].
+struct InjectArgs {
+  DevTree tree;
+  const int* list;       // octants to process (level order): finer-source list entries [first, first + count)
+  int first, count;
+  void* inj;
+  const double* u[2];
+  const float* us[2];
+  const void* K;
+  const void* Uin;
+  long long fstride;
+  int nf, stage, gts, mixed;
+  unsigned cur_mask;
+  LevelConst lc[32];
+  StageTerms om1;        // this stage's correction terms for a finer source (relation 1)
 };
 
 // axis orders of the three interpolation passes of the prolongation
@@ -194,12 +217,15 @@ struct MapArgs {
 struct BatchInst {
   StageArgs st[4];       // per stage
   ProlongArgs pr[4];     // per stage
+  InjectArgs in[4];      // per stage
   SyncArgs zip, hang;    // reconcile of the state at the end of a macro step
   const int* up_list;
   const int* hang_list;
+  const int* dn_list;    // finer sources of the padding maps (level order)
   int off[34];           // level offsets (level order)
   int up_off[34];        // per-level ranges of up_list
   int hang_off[34];      // per-level ranges of hang_list
+  int dn_off[34];        // per-level ranges of dn_list
   int n, nf, p, lmin, lmax;
   long long nsub_macro;  // substeps per macro step, 2^(lmax - lmin)
   // schedule state
@@ -217,10 +243,11 @@ struct BatchArgs {
   int n;
   int* stage_pre;        // [4][kMaxBatch + 1]: prefix sums of the active octants of each stage
   int* prol_pre;         // [4][kMaxBatch + 1]: prefix sums of the octants to prolong
+  int* inj_pre;          // [4][kMaxBatch + 1]: prefix sums of the finer sources to inject
   int* zip_pre;          // [kMaxBatch + 1]: octants of instances that reconcile this round
   int* hang_pre;         // [kMaxLevel + 2][kMaxBatch + 1]: their hanging-node octants per level
-  int* next_item;        // [2][4]: next unclaimed work item of the prolong / stage launch of each stage,
-                         // zeroed by batch_round_begin
+  int* next_item;        // [3][4]: next unclaimed work item of the prolong / stage / injection work of
+                         // each stage, zeroed by batch_round_begin
 };
 
 cudaError_t prepare_batch_kernels();  // outside any stream capture
@@ -252,6 +279,10 @@ cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
 cudaError_t launch_init(const InitArgs& a, cudaStream_t s);
 cudaError_t launch_maps(const MapArgs& a, cudaStream_t s);
 cudaError_t launch_padmap(const DevTree& t, unsigned char* out, int* err, cudaStream_t s);
+cudaError_t launch_finemark(const DevTree& t, const unsigned char* padmap, unsigned char* mark, cudaStream_t s);
+cudaError_t launch_slotmap(const DevTree& t, const int* up_slot, const int* dn_slot, int nf, int* out, int* err,
+                           cudaStream_t s);
+cudaError_t launch_inject(const InjectArgs& a, cudaStream_t s);
 cudaError_t launch_widen(const float* in, double* out, long long n, cudaStream_t s);
 cudaError_t launch_narrow(const double* in, float* out, long long n, cudaStream_t s);
 

@@ -123,3 +123,31 @@ def test_batch_rejects_mixed_streams_or_precision(lt):
     b = lt.Plan(lt.Octree(w["spec"]), dict(w["prob"], precision=1))
     with pytest.raises(lt.LtsError):
         lt.Batch([a, b])
+
+
+@pytest.mark.parametrize("mode", [("persistent", 3), ("per-stage", None)])
+def test_mixed_precision_batch_equals_instances_alone(lt, mode):
+    """Mixed-precision plans (FP32 stages, FP64 state) batched in either mode end where
+    they end alone."""
+    ws = [W.advection_gauss(l_min=2, l_max=4), W.wave_planar(l_min=2, l_max=4),
+          W.wave_shell(l_min=3, l_max=5, half=4.0, radius=1.5, width=0.2)]
+    for w in ws:
+        w["prob"]["precision"] = 1
+    substeps = [8, 12, 4]
+    alone, batched = [], []
+    for w, n in zip(ws, substeps):
+        a = lt.Plan(lt.Octree(w["spec"]), w["prob"])
+        b = lt.Plan(lt.Octree(w["spec"]), w["prob"])
+        a.set_initial(0.0)
+        b.set_initial(0.0)
+        a.run_substeps(n)
+        alone.append(a)
+        batched.append(b)
+    batch = lt.Batch(batched)
+    if mode[0] == "persistent":
+        batch.set_mode(True, mode[1])
+    batch.run(substeps)
+    batch.wait()
+    for a, b in zip(alone, batched):
+        ua, ub = a.get_state(), b.get_state()
+        assert np.abs(ua - ub).max() <= 1e-12 * np.abs(ua).max()
