@@ -230,6 +230,31 @@ __device__ void load_neighbours(const DevTree& t, int b, NbrView& nv) {
 // u + dt * sum_t w_t K_(j_t), in FP64 (eq. rk_schemes with the corrected weights
 // of eqs. fc_1 / fc_2)
 //
+// FP32 -> FP64 by bit manipulation, exact like the hardware conversion, on the integer
+// pipes: on GB300 conversions execute on the small FP64 pipe, which the mixed-precision
+// kernels also need for their FP64 accumulations.  Subnormal, infinite and NaN inputs take
+// the hardware conversion.
+__device__ __forceinline__ double widen(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned e = (u >> 23) & 255u;
+  if (e - 1u < 254u) {  // normal: exponent rebiased 127 -> 1023, mantissa 23 -> 52 bits
+    const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0xfffffu);
+    return __hiloint2double(int(hi), int(u << 29));
+  }
+  if ((u & 0x7fffffffu) == 0u) return __hiloint2double(int(u & 0x80000000u), 0);  // +-0
+  return static_cast<double>(x);
+}
+
+template <typename T>
+__device__ __forceinline__ double to_double(T x) {
+  if constexpr (sizeof(T) == sizeof(float)) {
+    return widen(x);
+  } else {
+    return x;
+  }
+}
+
+//
 // C selects the load path: false, the read-only data path (data written by earlier
 // launches); true, loads through L2 (ld.global.cg) for data that the same launch may have
 // written (the persistent batch round, whose stages follow each other inside one launch).
@@ -246,7 +271,7 @@ template <typename R, bool C = false>
 __device__ __forceinline__ double corrected_value(const double* __restrict__ u, const R* __restrict__ k0,
                                                   long long kstride, const StageTerms& t, double dt) {
   double acc = 0.0;
-  for (int q = 0; q < t.n; ++q) acc = fma(t.w[q], static_cast<double>(ld_in<C>(k0 + t.j[q] * kstride)), acc);
+  for (int q = 0; q < t.n; ++q) acc = fma(t.w[q], to_double(ld_in<C>(k0 + t.j[q] * kstride)), acc);
   return fma(dt, acc, ld_in<C>(u));
 }
 
@@ -574,7 +599,7 @@ __device__ __forceinline__ EpilogueOut stage_epilogue(const StageArgs& A, const 
       float acc = 0.0f;
       for (int q = 0; q < p - 1; ++q) acc = fmaf(A.cf.dtw_upd[lb][q], float(K[(long long)q * kstride + o]), acc);
       acc = fmaf(A.cf.dtw_upd[lb][p - 1], float(kvf), acc);
-      out.unew = u0[o] + static_cast<double>(acc);
+      out.unew = u0[o] + widen(acc);
       out.unew_s = static_cast<float>(out.unew);
     }
   }
@@ -959,7 +984,9 @@ __device__ void stage_octant(StageSmem<NF, R, 1>& S, const StageArgs& A, const i
 // threads and 10 CTAs per SM (13%); FP64 with 320 threads and 6 CTAs per SM (1%: the
 // 23 nodes of a second pass); persistent CTAs stepping their octants with two tile
 // buffers, the next octant's gathers in flight during the current one's right-hand sides
-// (FP64 25%: 3 CTAs per SM fit; mixed 27%: the slot table's loads stall the whole CTA).
+// (FP64 25%: 3 CTAs per SM fit; mixed 27%: the slot table's loads stall the whole CTA);
+// mixed precision with two octants per CTA, their maps, slot tables and gathers in
+// flight together (12%: the second octant's slot registers spill at 32 registers).
 template <typename R> struct StageShape {
   static constexpr int kTPB = kThreads;
   static constexpr int kMinBlocks = 5;
@@ -1537,7 +1564,7 @@ __global__ void update_kernel(UpdateArgs A) {
       // FP32 increment accumulated into FP64 u
       float acc = 0.0f;
       for (int q = 0; q < A.p; ++q) acc = fmaf(A.dtwf[q], float(K[q * kstride + e]), acc);
-      const double un = A.u[cur][e] + static_cast<double>(acc);
+      const double un = A.u[cur][e] + widen(acc);
       A.u[cur ^ 1][e] = un;
       A.us[cur ^ 1][e] = static_cast<float>(un);
     }
