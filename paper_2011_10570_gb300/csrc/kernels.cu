@@ -485,6 +485,143 @@ __device__ __noinline__ void radiative_rhs(const R* const* T, const StageArgs& A
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP64 wave right-hand side by exact integer stencil sums.  The 4th-order Laplacian and
+// the Kreiss-Oliger operator have integer coefficients (in units of 1/(12 h^2) and of the
+// dissipation constant), so at each node the stencil inputs of a field are put on a common
+// 2^(E - 1075) grid, E the largest biased exponent among them: input x becomes the integer
+// sign(x) trunc(|x| 2^(1075 - E)), |.| < 2^53, exact for every input in E's binade and
+// truncated below it (each to within 2^-52 of the largest input, the size of an FP64
+// operation's rounding).  Sums and integer combinations are then exact in 64 bits (|.| <
+// 192 x 2^53 < 2^61) and each result is rounded once to FP64.  GB300 issues integer
+// operations at 32 times its FP64 rate (64 lanes per clock and SM against 2), but a
+// conversion costs about a dozen of them; the work is split so that both pipes carry
+// about the same load: chi's Laplacian and dissipation (its 19 stencil inputs) and phi's
+// dissipation terms at distance 0 and 1 (7 inputs) are exact integer sums, phi's pair sums
+// at distance 2 and 3 are FP64 additions (12 of the 41 FP64 operations of a wave node
+// stay on the FP64 pipe).  The result depends only on the node's own stencil inputs, so
+// every kernel that evaluates a node (stage, block, batch; LTS or GTS) gets the same bits.
+// Fields whose largest input lies outside [2^-968, 2^500) (other than all zero), or that
+// hold an infinity or NaN, take the floating-point evaluation instead; subnormal inputs
+// beside normal ones lie below a grid unit and truncate to zero.
+// ---------------------------------------------------------------------------
+
+// exponent field (bits 20..30 of the high word, in place) of the double at w
+__device__ __forceinline__ unsigned fix_expbits(const double* w) {
+  return reinterpret_cast<const unsigned*>(w)[1] & 0x7ff00000u;
+}
+
+// An exact sum of inputs on the grid 2^(E - 1075): the magnitudes truncated onto the grid
+// with their signs applied as one's complements (x ^ s, s = 0 or -1), plus the count of
+// negative inputs, which completes the two's complements.
+struct FixSum {
+  long long ones = 0;
+  int neg = 0;
+  __device__ __forceinline__ long long value() const { return ones + neg; }
+};
+
+// adds x (exponent field <= em, E = em >> 20 in [55, 1523]) to a: sign(x) trunc(|x| 2^(1075 - E)).
+// The implicit bit is set for every input: a zero or subnormal input lies at least E >= 55
+// binades below the grid's top and is shifted out all the same (a -0 adds ~0 + 1 = 0).
+__device__ __forceinline__ void fix_add(FixSum& a, double x, unsigned em) {
+  const unsigned hi = static_cast<unsigned>(__double2hiint(x));
+  const unsigned lo = static_cast<unsigned>(__double2loint(x));
+  const unsigned long long m = (static_cast<unsigned long long>((hi & 0xfffffu) | 0x100000u) << 32) | lo;
+  const unsigned sh = (em - (hi & 0x7ff00000u)) >> 20;
+  unsigned long long q;
+  asm("shr.b64 %0, %1, %2;" : "=l"(q) : "l"(m), "r"(sh));  // amounts above 64 clamp to 64: 0
+  a.ones += static_cast<long long>(q) ^ static_cast<long long>(static_cast<int>(hi) >> 31);
+  a.neg += static_cast<int>(hi >> 31);
+}
+
+// n 2^(E - 1075) rounded once to FP64 (n = 0, or E in [55, 1523] and |n| < 2^62: a normal
+// result, no overflow)
+__device__ __forceinline__ double fix_value(long long n, unsigned em) {
+  if (n == 0) return 0.0;
+  const double d = __ll2double_rn(n);
+  return __hiloint2double(__double2hiint(d) + ((static_cast<int>(em >> 20) - 1075) << 20), __double2loint(d));
+}
+
+// largest exponent field among a node's stencil inputs of one field: the centre and its
+// axis neighbours at distance 1..R
+template <int SY, int SZ, int R>
+__device__ __forceinline__ unsigned fix_emax(const double* T, int c0) {
+  unsigned e = fix_expbits(T + c0);
+#pragma unroll
+  for (int m = 1; m <= R; ++m) {
+    e = max(e, max(fix_expbits(T + c0 - m), fix_expbits(T + c0 + m)));
+    e = max(e, max(fix_expbits(T + c0 - m * SY), fix_expbits(T + c0 + m * SY)));
+    e = max(e, max(fix_expbits(T + c0 - m * SZ), fix_expbits(T + c0 + m * SZ)));
+  }
+  return e;
+}
+
+// the symmetric pair sums at distance m along the three axes, on the grid of em
+template <int SY, int SZ>
+__device__ __forceinline__ long long fix_ring(const double* T, int c0, int m, unsigned em) {
+  FixSum a;
+  fix_add(a, T[c0 - m], em);
+  fix_add(a, T[c0 + m], em);
+  fix_add(a, T[c0 - m * SY], em);
+  fix_add(a, T[c0 + m * SY], em);
+  fix_add(a, T[c0 - m * SZ], em);
+  fix_add(a, T[c0 + m * SZ], em);
+  return a.value();
+}
+
+__device__ __forceinline__ long long fix_one(double x, unsigned em) {
+  FixSum a;
+  fix_add(a, x, em);
+  return a.value();
+}
+
+// every one of those inputs (distance 1..R) is +-0
+template <int SY, int SZ, int R>
+__device__ __noinline__ bool fix_all_zero(const double* T, int c0) {
+  auto bits = [&](int o) {
+    const int* w = reinterpret_cast<const int*>(T + c0 + o);
+    return (w[1] & 0x7fffffff) | w[0];
+  };
+  int any = bits(0);
+#pragma unroll
+  for (int m = 1; m <= R; ++m) any |= bits(-m) | bits(m) | bits(-m * SY) | bits(m * SY) | bits(-m * SZ) | bits(m * SZ);
+  return any == 0;
+}
+
+// the grid of the largest exponent field em represents those inputs exactly enough:
+// E = em >> 20 in [55, 1523] (subnormal inputs then lie below one grid unit), or every input
+// zero
+template <int SY, int SZ, int R>
+__device__ __forceinline__ bool fix_range(unsigned em, const double* T, int c0) {
+  return (em >= (55u << 20) && em <= (1523u << 20)) || (em == 0 && fix_all_zero<SY, SZ, R>(T, c0));
+}
+
+// the wave right-hand side (chi, phi) at tile index c0 of the FP64 tiles Tc (chi) and Tp
+// (phi); false when an input's size is out of the exact range (nothing written)
+template <int SY, int SZ>
+__device__ __forceinline__ bool wave_rhs_exact(const double* Tc, const double* Tp, int c0, double kos,
+                                               double inv12h2, double& kchi, double& kphi) {
+  const unsigned ec = fix_emax<SY, SZ, 3>(Tc, c0);
+  const unsigned ep = fix_emax<SY, SZ, 1>(Tp, c0);
+  if (!(fix_range<SY, SZ, 3>(ec, Tc, c0) && fix_range<SY, SZ, 1>(ep, Tp, c0))) return false;
+  const double f0v = Tp[c0];
+  long long lap = 0, koc = 0, kop = 0;  // a field whose inputs are all zero has zero sums
+  if (ec != 0) {
+    const long long c = fix_one(Tc[c0], ec);
+    const long long c1 = fix_ring<SY, SZ>(Tc, c0, 1, ec);
+    const long long c2 = fix_ring<SY, SZ>(Tc, c0, 2, ec);
+    lap = 16 * c1 - c2 - 90 * c;
+    koc = fix_ring<SY, SZ>(Tc, c0, 3, ec) - 6 * c2 + 15 * c1 - 60 * c;
+  }
+  if (ep != 0) kop = 15 * fix_ring<SY, SZ>(Tp, c0, 1, ep) - 60 * fix_one(f0v, ep);
+  // phi's rings at distance 2 and 3 in FP64
+  const double F2 = (Tp[c0 - 2] + Tp[c0 + 2]) + (Tp[c0 - 2 * SY] + Tp[c0 + 2 * SY]) + (Tp[c0 - 2 * SZ] + Tp[c0 + 2 * SZ]);
+  const double F3 = (Tp[c0 - 3] + Tp[c0 + 3]) + (Tp[c0 - 3 * SY] + Tp[c0 + 3 * SY]) + (Tp[c0 - 3 * SZ] + Tp[c0 + 3 * SZ]);
+  kchi = fma(kos, fix_value(koc, ec), f0v);
+  kphi = fma(kos, fix_value(kop, ep) + fma(-6.0, F2, F3), fix_value(lap, ec) * inv12h2);
+  return true;
+}
+
 // right-hand side at one node from its padded tile: advection (4th-order D1) or the
 // wave equation (4th-order Laplacian), plus Kreiss-Oliger dissipation; symmetric pair
 // sums at distance 1, 2, 3 are shared by the derivative and the dissipation
@@ -508,6 +645,9 @@ __device__ __forceinline__ void rhs_node(const R* const* Tt, int c0, const Stage
   } else {
     const R* Tc = Tt[0];
     const R* Tp = Tt[NF - 1];
+    if constexpr (sizeof(R) == sizeof(double) && NF == 2) {
+      if (wave_rhs_exact<SY, SZ>(Tc, Tp, c0, kos, inv12h2, kv[0], kv[1])) return;
+    }
     const R c0v = Tc[c0], f0v = Tp[c0];
     const R C1 = (Tc[c0 - 1] + Tc[c0 + 1]) + (Tc[c0 - SY] + Tc[c0 + SY]) + (Tc[c0 - SZ] + Tc[c0 + SZ]);
     const R C2 = (Tc[c0 - 2] + Tc[c0 + 2]) + (Tc[c0 - 2 * SY] + Tc[c0 + 2 * SY]) + (Tc[c0 - 2 * SZ] + Tc[c0 + 2 * SZ]);
@@ -1367,6 +1507,7 @@ struct ProlongSmem {
   R X2[NF][13 * 13 * 7];  // [ra][rb][jc]
   R E[3][4];              // symmetric-part weights of the mirrored pairs (1, 11), (3, 9), (5, 7)
   R O[3][3];              // antisymmetric-part weights
+  R W[6][7];              // Lagrange weights of the odd positions 1, 3, ..., 11 (row k >> 1)
 };
 
 
@@ -1390,25 +1531,57 @@ __device__ __forceinline__ int class_hi(unsigned m) { return (m & 4u) ? 12 : ((m
 // Even positions are nodes (copies).  Odd positions come in mirrored pairs (k, 12 - k):
 // the Lagrange weights satisfy W[12 - k][j] = W[k][6 - j], so with s_j = v_j + v_{6-j}
 // and d_j = v_j - v_{6-j} the pair is E + O and E - O, E = sum_j E[p][j] s_j (s_3 = v_3)
-// and O = sum_j O[p][j] d_j: 33 operations for a whole line instead of 42.
+// and O = sum_j O[p][j] d_j: 9 operations for the pair once the 6 sums and differences
+// are formed, against 7 for one position as a direct dot product with W.  The form is
+// chosen per pair from the set all (a superset of cls, uniform over the CTA's lines of a
+// pass, so that a warp's lines take one path): pairs needed whole take the symmetric form
+// when there are at least two of them, every other odd position the direct one; a whole
+// line costs 33 operations instead of 42, a one-sided face slab 14 instead of 22.
 template <typename R, typename Put>
-__device__ __forceinline__ void interp_line(const R (&v)[7], int r0, int n, unsigned cls, const R (*E)[4],
-                                            const R (*O)[3], Put put) {
-  auto needed = [&](int r) { return r >= r0 && r < r0 + n && ((cls >> half_class(r)) & 1u); };
+__device__ __forceinline__ void interp_line(const R (&v)[7], int r0, int n, unsigned cls, unsigned all,
+                                            const R (*E)[4], const R (*O)[3], const R (*W)[7], Put put) {
+  auto in_set = [&](int r, unsigned set) { return r >= r0 && r < r0 + n && ((set >> half_class(r)) & 1u); };
+  auto needed = [&](int r) { return in_set(r, cls); };
 #pragma unroll
   for (int r = 0; r <= 12; r += 2)
     if (needed(r)) put(r, v[r >> 1]);
-  const R s0 = v[0] + v[6], s1 = v[1] + v[5], s2 = v[2] + v[4];
-  const R d0 = v[0] - v[6], d1 = v[1] - v[5], d2 = v[2] - v[4];
+  bool pair[3];
+  int pairs = 0;
+#pragma unroll
+  for (int pr = 0; pr < 3; ++pr) {
+    pair[pr] = in_set(2 * pr + 1, all) && in_set(11 - 2 * pr, all);
+    pairs += pair[pr];
+  }
+  if (pairs < 2) {
+#pragma unroll
+    for (int pr = 0; pr < 3; ++pr) pair[pr] = false;
+  }
+  auto direct = [&](int r) {
+    const R* w = W[r >> 1];
+    R x = w[0] * v[0];
+#pragma unroll
+    for (int j = 1; j < 7; ++j) x = fma(w[j], v[j], x);
+    put(r, x);
+  };
+  R s0 = 0, s1 = 0, s2 = 0, d0 = 0, d1 = 0, d2 = 0;
+  if (pairs >= 2) {
+    s0 = v[0] + v[6], s1 = v[1] + v[5], s2 = v[2] + v[4];
+    d0 = v[0] - v[6], d1 = v[1] - v[5], d2 = v[2] - v[4];
+  }
 #pragma unroll
   for (int pr = 0; pr < 3; ++pr) {
     const int k = 2 * pr + 1;
     const bool nk = needed(k), nm = needed(12 - k);
-    if (!(nk || nm)) continue;
-    const R e = fma(E[pr][0], s0, fma(E[pr][1], s1, fma(E[pr][2], s2, E[pr][3] * v[3])));
-    const R o = fma(O[pr][0], d0, fma(O[pr][1], d1, O[pr][2] * d2));
-    if (nk) put(k, e + o);
-    if (nm) put(12 - k, e - o);
+    if (pair[pr]) {
+      if (!(nk || nm)) continue;
+      const R e = fma(E[pr][0], s0, fma(E[pr][1], s1, fma(E[pr][2], s2, E[pr][3] * v[3])));
+      const R o = fma(O[pr][0], d0, fma(O[pr][1], d1, O[pr][2] * d2));
+      if (nk) put(k, e + o);
+      if (nm) put(12 - k, e - o);
+    } else {
+      if (nk) direct(k);
+      if (nm) direct(12 - k);
+    }
   }
 }
 
@@ -1455,6 +1628,9 @@ __device__ void prolong_octant(ProlongSmem<NF, R>& S, const ProlongArgs& A, cons
       const int j = q - 4;
       S.O[pr][j] = R(0.5 * (c_W[k][j] - c_W[k][6 - j]));
     }
+  } else if (tid >= 32 && tid < 32 + 42) {  // the odd rows for the direct evaluation
+    const int q = tid - 32;
+    S.W[q / 7][q % 7] = R(c_W[2 * (q / 7) + 1][q % 7]);
   }
   const int cur = (A.cur_mask >> lb) & 1;
   const R* Uin = static_cast<const R*>(A.Uin);
@@ -1481,7 +1657,7 @@ __device__ void prolong_octant(ProlongSmem<NF, R>& S, const ProlongArgs& A, cons
 #pragma unroll
     for (int q = 0; q < 7; ++q) v[q] = S.V[f][7 * bc + q];
     R* x1 = S.X1[f] + bc;
-    interp_line<R>(v, a0, na, ma, S.E, S.O, [&](int r, R val) { x1[r * 49] = val; });
+    interp_line<R>(v, a0, na, ma, ma, S.E, S.O, S.W, [&](int r, R val) { x1[r * 49] = val; });
   }
   __syncthreads();
   // pass 2 (axis b): one thread per line (f, ra, jc), X2[ra][rb][jc]
@@ -1497,7 +1673,7 @@ __device__ void prolong_octant(ProlongSmem<NF, R>& S, const ProlongArgs& A, cons
 #pragma unroll
     for (int q = 0; q < 7; ++q) v[q] = x1[q];
     R* x2 = S.X2[f] + ra * 13 * 7 + jc;
-    interp_line<R>(v, b0, nb, cls, S.E, S.O, [&](int r, R val) { x2[r * 7] = val; });
+    interp_line<R>(v, b0, nb, cls, mb, S.E, S.O, S.W, [&](int r, R val) { x2[r * 7] = val; });
   }
   __syncthreads();
   // pass 3 (axis c): one thread per line (f, ra, rb), every position of the set written
@@ -1518,7 +1694,7 @@ __device__ void prolong_octant(ProlongSmem<NF, R>& S, const ProlongArgs& A, cons
 #pragma unroll
     for (int q = 0; q < 7; ++q) v[q] = x2[q];
     R* o = out + f * kNT + ra * soa + rb * sob;
-    interp_line<R>(v, c0, nc, cls, S.E, S.O, [&](int r, R val) { o[r * soc] = val; });
+    interp_line<R>(v, c0, nc, cls, mc, S.E, S.O, S.W, [&](int r, R val) { o[r * soc] = val; });
   }
 }
 

@@ -5,6 +5,8 @@
 * FP64 fields within a relative L-infinity error of 1e-12 of the oracle, for LTS
   (Alg. 2) and GTS (Alg. 1), advection and wave, exact and radiative boundaries;
 * LTS == GTS bitwise on a one-level tree (Alg. 2 reduces to Alg. 1);
+* FP64 wave right-hand sides (exact integer stencil sums) on data spanning 10^-300 to
+  10^200, each node within a few units of 2^-52 of its own stencil scale;
 * at the full wave configuration (levels 4..9, 154,400 octants): the octree, the
   o2o map, sampled padding maps, and the first two LTS substeps at sampled octants
   (the oracle runs only the dependency cone of the sample).
@@ -170,6 +172,61 @@ def test_deep_narrow_tree(lt, orc):
     plan.run_substeps(3)
     sol.lts_substeps(3)
     assert rel_linf(plan.get_state(), sol.state()) <= TOL
+
+
+def stencil_scale(tile):
+    """largest |input| among each node's 19 stencil points (centre and the 6 x 3 axis
+    neighbours), over both fields: [343] in node order (i fastest) from a padded tile
+    [nf][13][13][13] in (k, j, i) order"""
+    a = np.abs(tile).max(axis=0)
+    c = slice(3, 10)
+    m = a[c, c, c].copy()
+    for s in (1, 2, 3):
+        for lo in (3 - s, 3 + s):
+            sl = slice(lo, lo + 7)
+            m = np.maximum(m, a[sl, c, c])
+            m = np.maximum(m, a[c, sl, c])
+            m = np.maximum(m, a[c, c, sl])
+    return m.reshape(-1)
+
+
+def test_fp64_wave_rhs_on_wide_range_data(lt, orc):
+    """FP64 wave right-hand sides partly come from exact integer stencil sums on a per-node
+    grid (floating point for magnitudes outside [2^-968, 2^500), infinities and NaNs).
+    State with a magnitude class per octant and field (1 down to 1e-300, up to 1e200, zero,
+    subnormal), random signs, scattered zeros and subnormals: every node's first stage
+    agrees with the oracle's FP64 evaluation to a few units of 2^-52 of the node's own
+    stencil scale, not of the global maximum (Sec. 4 wave equation, KO dissipation)."""
+    w = W.wave_shell(l_min=2, l_max=4, half=4.0, radius=1.5, width=0.2)
+    gt, plan, ot, sol = both(lt, orc, w)
+    st = plan.stats()
+    n = st["n_octants"]
+    rng = np.random.default_rng(11)
+    mags = np.array([1.0, 1e-5, 1e-20, 1e-100, 1e-290, 1e-300, 1e140, 1e200, 0.0, 4e-320])
+    cls = rng.integers(0, len(mags), size=(2, n))
+    u = rng.standard_normal((2, n, 343)) * mags[cls][:, :, None]
+    u[rng.random(u.shape) < 0.1] = 0.0
+    sub = rng.random(u.shape) < 0.02
+    u[sub] = 3e-320 * np.where(rng.random(int(sub.sum())) < 0.5, -1.0, 1.0)
+    plan.set_state(u)
+    sol.set_state(u)
+    scale = np.stack([stencil_scale(sol.tile(b)) for b in range(n)])  # [n][343]
+    plan.run_substeps(1)
+    sol.lts_substeps(1)
+    _, lev = gt.export()
+    half = w["spec"]["hi"]
+    h = 2.0 * half / (6.0 * 2.0 ** lev)
+    kos = w["prob"]["ko_sigma"] / (64.0 * h)
+    # bound of the operators' coefficients acting on the inputs: Laplacian and dissipation
+    # (192 = the sums of the integer weights' magnitudes), the radiative gradient at the
+    # boundary (|x| <= half * sqrt(3), 18 / (12 h), plus 2 / r)
+    coef = 192.0 * (1.0 / (12.0 * h * h) + kos) + 3.0 * half * 18.0 / (12.0 * h) + 4.0
+    kg, ko = plan.get_stage(0), sol.stage(0)
+    err = np.abs(kg - ko) / (coef[None, :, None] * scale[None] + 1e-320)
+    assert np.isfinite(kg).all()
+    assert err.max() <= 64 * 2.0 ** -52
+    # octants of tiny and of huge magnitudes are both present and checked on their own scale
+    assert (scale < 1e-280).any() and (scale > 1e180).any()
 
 
 def test_invalid_calls_fail_loudly(lt):
