@@ -495,15 +495,15 @@ __device__ __noinline__ void radiative_rhs(const R* const* T, const StageArgs& A
 // operation's rounding).  Sums and integer combinations are then exact in 64 bits (|.| <
 // 192 x 2^53 < 2^61) and each result is rounded once to FP64.  GB300 issues integer
 // operations at 32 times its FP64 rate (64 lanes per clock and SM against 2), but a
-// conversion costs about a dozen of them; the work is split so that both pipes carry
-// about the same load: chi's Laplacian and dissipation (its 19 stencil inputs) and phi's
-// dissipation terms at distance 0 and 1 (7 inputs) are exact integer sums, phi's pair sums
-// at distance 2 and 3 are FP64 additions (12 of the 41 FP64 operations of a wave node
-// stay on the FP64 pipe).  The result depends only on the node's own stencil inputs, so
-// every kernel that evaluates a node (stage, block, batch; LTS or GTS) gets the same bits.
-// Fields whose largest input lies outside [2^-968, 2^500) (other than all zero), or that
-// hold an infinity or NaN, take the floating-point evaluation instead; subnormal inputs
-// beside normal ones lie below a grid unit and truncate to zero.
+// conversion costs about a dozen of them, so the work is split between the two pipes:
+// chi's Laplacian and dissipation (its 19 stencil inputs) are exact integer sums, phi's
+// dissipation stays in FP64 (18 of the 41 FP64 operations of a wave node); of the splits
+// that move whole pair sums between the pipes, this one measured fastest.  The result
+// depends only on the node's own stencil inputs, so every kernel that evaluates a node
+// (stage, block, batch; LTS or GTS) gets the same bits.  Nodes whose largest chi input lies
+// outside [2^-968, 2^500) (other than all zero), or whose chi inputs hold an infinity or
+// NaN, take the floating-point evaluation instead; subnormal inputs beside normal ones lie
+// below a grid unit and truncate to zero.
 // ---------------------------------------------------------------------------
 
 // exponent field (bits 20..30 of the high word, in place) of the double at w
@@ -597,15 +597,15 @@ __device__ __forceinline__ bool fix_range(unsigned em, const double* T, int c0) 
 }
 
 // the wave right-hand side (chi, phi) at tile index c0 of the FP64 tiles Tc (chi) and Tp
-// (phi); false when an input's size is out of the exact range (nothing written)
+// (phi): chi's Laplacian and dissipation as exact integer sums, phi's dissipation in FP64
+// (the association of the floating-point evaluation); false when chi's inputs are out of the
+// exact range (nothing written)
 template <int SY, int SZ>
 __device__ __forceinline__ bool wave_rhs_exact(const double* Tc, const double* Tp, int c0, double kos,
                                                double inv12h2, double& kchi, double& kphi) {
   const unsigned ec = fix_emax<SY, SZ, 3>(Tc, c0);
-  const unsigned ep = fix_emax<SY, SZ, 1>(Tp, c0);
-  if (!(fix_range<SY, SZ, 3>(ec, Tc, c0) && fix_range<SY, SZ, 1>(ep, Tp, c0))) return false;
-  const double f0v = Tp[c0];
-  long long lap = 0, koc = 0, kop = 0;  // a field whose inputs are all zero has zero sums
+  if (!fix_range<SY, SZ, 3>(ec, Tc, c0)) return false;
+  long long lap = 0, koc = 0;  // inputs all zero: zero sums
   if (ec != 0) {
     const long long c = fix_one(Tc[c0], ec);
     const long long c1 = fix_ring<SY, SZ>(Tc, c0, 1, ec);
@@ -613,12 +613,13 @@ __device__ __forceinline__ bool wave_rhs_exact(const double* Tc, const double* T
     lap = 16 * c1 - c2 - 90 * c;
     koc = fix_ring<SY, SZ>(Tc, c0, 3, ec) - 6 * c2 + 15 * c1 - 60 * c;
   }
-  if (ep != 0) kop = 15 * fix_ring<SY, SZ>(Tp, c0, 1, ep) - 60 * fix_one(f0v, ep);
-  // phi's rings at distance 2 and 3 in FP64
+  const double f0v = Tp[c0];
+  const double F1 = (Tp[c0 - 1] + Tp[c0 + 1]) + (Tp[c0 - SY] + Tp[c0 + SY]) + (Tp[c0 - SZ] + Tp[c0 + SZ]);
   const double F2 = (Tp[c0 - 2] + Tp[c0 + 2]) + (Tp[c0 - 2 * SY] + Tp[c0 + 2 * SY]) + (Tp[c0 - 2 * SZ] + Tp[c0 + 2 * SZ]);
   const double F3 = (Tp[c0 - 3] + Tp[c0 + 3]) + (Tp[c0 - 3 * SY] + Tp[c0 + 3 * SY]) + (Tp[c0 - 3 * SZ] + Tp[c0 + 3 * SZ]);
+  const double kop = fma(-60.0, f0v, fma(15.0, F1, fma(-6.0, F2, F3)));
   kchi = fma(kos, fix_value(koc, ec), f0v);
-  kphi = fma(kos, fix_value(kop, ep) + fma(-6.0, F2, F3), fix_value(lap, ec) * inv12h2);
+  kphi = fma(kos, kop, fix_value(lap, ec) * inv12h2);
   return true;
 }
 
