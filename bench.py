@@ -31,8 +31,13 @@ UNIT = "node-updates/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x flops/FMA x max clock
 # DRAM bytes (read + write) per node-stage of stage_kernel<2, double> / <2, float>, from ncu
 # captures of one stage launch on the levels 4..8 wave case; None whenever the kernel changes
-STAGE_DRAM_BYTES_PER_NODE_STAGE = 97.0
-STAGE_DRAM_BYTES_PER_NODE_STAGE_MIXED = 54.3
+STAGE_DRAM_BYTES_PER_NODE_STAGE = 88.7
+STAGE_DRAM_BYTES_PER_NODE_STAGE_MIXED = 48.4
+# FP64-pipe operations per node-stage of stage_kernel<2, double> on the wave equation:
+# phi's dissipation 18 (15 pair-sum additions, 3 FMAs), the Laplacian's scaling and the
+# two stage FMAs 3, two integer-to-FP64 conversions 2, the RK epilogue 3.5 on average;
+# chi's 19 stencil inputs are summed exactly on the integer pipes
+FP64_PIPE_OPS_PER_NODE_STAGE = 26.5
 
 
 def measured_peaks():
@@ -515,8 +520,11 @@ def main():
             line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                               "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                               "flops_per_node_stage": fl,
-                              "flops_note": "counted from the kernel's formulas, FMA = 2 (an estimate of 65 "
-                                            "per node-stage gives frac %.3f)" % (achieved * 65 / fl / FP64_PEAK_TFLOPS),
+                              "flops_note": "FP64-equivalent operations counted from the kernel's formulas, FMA = 2 "
+                                            "(an estimate of 65 per node-stage gives frac %.3f); chi's stencil sums "
+                                            "run as exact integer arithmetic on the integer pipes, so frac is the "
+                                            "FP64-equivalent rate against the FP64 pipe's peak, and "
+                                            "fp64_pipe_frac the pipe's own load" % (achieved * 65 / fl / FP64_PEAK_TFLOPS),
                               "frac_vs_fma_probe": achieved / 1.20,
                               "fma_probe_note": "1.20 TFLOP/s: an FP64 FMA loop measured on a GB300 of this pool",
                               "traffic_source": "ncu dram bytes per node-stage (levels 4..8 capture) x node-stages per launch",
@@ -524,11 +532,9 @@ def main():
                               "hbm_gbs_algorithmic": ks["bytes"] / (ks["ms"] / 1e3) / 1e9,
                               "hbm_peak_gbs": hbm_peak,
                               "dram_gbs_measured_bytes": dram_gbs,
-                              # FP64 pipe operations (an FMA or an add is one) per node-stage of the
-                              # wave: right-hand side 41, RK4 epilogue 3.5 on average; the pipe
-                              # completes 2 per clock per SM
-                              "fp64_ops_per_node_stage": 44.5,
-                              "fp64_pipe_frac": 44.5 * ks["node_stages"] / (ks["ms"] / 1e3) / (152 * 2 * 2.070e9),
+                              "fp64_ops_per_node_stage": FP64_PIPE_OPS_PER_NODE_STAGE,
+                              "fp64_pipe_frac": FP64_PIPE_OPS_PER_NODE_STAGE * ks["node_stages"] / (ks["ms"] / 1e3) /
+                                                (152 * 2 * 2.070e9),
                               "stage_share_of_step": ks["ms"] / ms}
     if gts:
         line["gts"] = gts
