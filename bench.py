@@ -396,6 +396,7 @@ def main():
     # device-resident timed region (CUDA events on the plan's stream)
     plan.set_profiling(True)
     plan.kernel_stats(reset=True)
+    plan.prolong_stats(reset=True)
     launches0 = plan.stats()["kernel_launches"]
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if pg:
@@ -410,6 +411,7 @@ def main():
     ms = ev0.elapsed_time(ev1)
     launches = plan.stats()["kernel_launches"] - launches0
     ks = plan.kernel_stats(reset=True)
+    ps = plan.prolong_stats(reset=True)
     plan.set_profiling(False)
     if pg:
         t = torch.tensor([ms], dtype=torch.float64)
@@ -536,6 +538,23 @@ def main():
                               "fp64_pipe_frac": FP64_PIPE_OPS_PER_NODE_STAGE * ks["node_stages"] / (ks["ms"] / 1e3) /
                                                 (152 * 2 * 2.070e9),
                               "stage_share_of_step": ks["ms"] / ms}
+    if ps["launches"] and "roofline" in line:
+        # the second kernel of the step: the prolongation, FP64-equivalent flops as directly
+        # evaluated over its live event-timed launches
+        pro = {"launches": ps["launches"], "ms_per_launch": ps["ms"] / ps["launches"],
+               "sources_per_launch": ps["sources"] / ps["launches"], "share_of_step": ps["ms"] / ms}
+        if args.precision == "fp64":
+            p_tf = ps["flops"] / (ps["ms"] / 1e3) / 1e12
+            pro.update({"kernel": "prolong_kernel<2, double>", "bound": "alu", "achieved": p_tf, "unit": "TFLOP/s",
+                        "peak": FP64_PEAK_TFLOPS, "frac": p_tf / FP64_PEAK_TFLOPS,
+                        "note": "flops: the interpolation's multiply-adds of the plan's cost model (7 per odd "
+                                "half-node position) and the time-corrected inputs, FMA = 2; the kernel evaluates "
+                                "mirrored pairs with fewer FP64 operations, so frac is an FP64-equivalent rate"})
+        else:
+            pro.update({"kernel": "prolong_kernel<2, float>",
+                        "note": "FP32 interpolation after FP64 time corrections: bound by instruction issue "
+                                "(ncu), no single-pipe peak applies"})
+        line["roofline"]["prolong"] = pro
     if gts:
         line["gts"] = gts
     if not args.no_serve and rank == 0:

@@ -234,6 +234,19 @@ lts_status lts_set_blocking(lts_plan* plan, int on);
 lts_status lts_set_profiling(lts_plan* plan, int on);
 lts_status lts_kernel_stats(lts_plan* plan, int64_t* launches, double* ms, double* flops, double* bytes,
                             int64_t* node_stages, int reset);
+/* The same for the prolongation launches (coarse -> fine padding, Fig. unzip: the coarser
+ * sources' stage inputs corrected in time by eqs. fc_1 / fc_2 and interpolated to the
+ * half-node positions their finer neighbours read), bracketed by events while profiling is
+ * on: the number of launches, their summed device time (ms), the coarser sources they
+ * prolonged, and their FP64-equivalent flops as directly evaluated (FMA = 2): per source
+ * and field the interpolation's multiply-adds of the plan's pass-order cost model (7 per
+ * odd half-node position of each pass), and under LTS the corrected inputs at its 343
+ * nodes (one multiply-add per correction term and one for the step).  The kernel itself
+ * evaluates mirrored position pairs with fewer operations, so the rate is an equivalent.
+ * Out-pointers may be null.  Errors: LTS_EINVAL (null plan); a device fault recorded
+ * earlier is returned. */
+lts_status lts_prolong_stats(lts_plan* plan, int64_t* launches, double* ms, double* flops, int64_t* sources,
+                             int reset);
 
 /* ---- batches: many independent solves advanced together (NEXT-2) ------------------ */
 /* A batch advances several plans together in rounds: in each round every plan with

@@ -102,6 +102,13 @@ struct lts_plan {
   std::vector<int64_t> event_nodes;
   int64_t prof_launches = 0, prof_node_stages = 0;
   double prof_ms = 0.0;
+  // prolongation launches under profiling: events, FP64-equivalent flops and sources
+  std::vector<int64_t> up_cost;  // prefix sums over up_list of the interpolation multiply-adds per field
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pevents;
+  std::vector<double> pevent_flops;
+  std::vector<int64_t> pevent_sources;
+  int64_t pprof_launches = 0, pprof_sources = 0;
+  double pprof_ms = 0.0, pprof_flops = 0.0;
   double w_lts = 0.0, w_gts = 0.0;
 };
 
@@ -145,6 +152,11 @@ void release(lts_plan* P) {
     cudaEventDestroy(ev.second);
   }
   P->events.clear();
+  for (auto& ev : P->pevents) {
+    cudaEventDestroy(ev.first);
+    cudaEventDestroy(ev.second);
+  }
+  P->pevents.clear();
   for (void* ptr : P->allocations) {
     if (P->prob.dev_free)
       P->prob.dev_free(ptr, P->prob.alloc_ctx);
@@ -295,7 +307,7 @@ lts_status sync_fields(lts_plan* P, void* vb0, void* vb1, unsigned sel, int elem
 // 7 x 7 source lines at each odd position of its axis, pass 2 7 lines per odd
 // position of the plane it needs, pass 3 every odd point of the set, 7 multiply-adds
 // each; a class spans 4 / 5 / 4 positions, two of them odd.
-uint32_t prolong_plan_word(uint32_t cls) {
+uint32_t prolong_plan_word(uint32_t cls, int64_t* cost_out = nullptr) {
   static const int kN[3] = {4, 5, 4}, kOdd[3] = {2, 2, 2};
   int64_t best_cost = INT64_MAX;
   uint32_t best = 0;
@@ -331,6 +343,7 @@ uint32_t prolong_plan_word(uint32_t cls) {
       best = m | uint32_t(o) << 27;
     }
   }
+  if (cost_out) *cost_out = best_cost;
   return best;
 }
 
@@ -454,8 +467,30 @@ lts_status launch_prolong_for(lts_plan* P, const ltsoct::StageArgs& sa, int lsta
   a.mixed = sa.mixed;
   for (int l = 0; l < 32; ++l) a.lc[l] = sa.lc[l];
   for (int r = 0; r < 4; ++r) a.om[r] = sa.om[r];
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (P->profiling) {
+    CK(cudaEventCreate(&e0), "cudaEventCreate");
+    CK(cudaEventCreate(&e1), "cudaEventCreate");
+    CK(cudaEventRecord(e0, P->stream), "cudaEventRecord");
+  }
   CK(ltsoct::launch_prolong(a, P->stream), "prolongation kernel launch");
   P->launches++;
+  if (P->profiling) {
+    CK(cudaEventRecord(e1, P->stream), "cudaEventRecord");
+    P->pevents.emplace_back(e0, e1);
+    // FP64-equivalent work as directly evaluated: the interpolation's multiply-adds (the
+    // plan's cost model, 7 per odd position) and the corrected stage inputs (one
+    // multiply-add per stage term and one for the step, 343 nodes), 2 flops each
+    double fma = double(P->nf) * double(P->up_cost[first + count] - P->up_cost[first]);
+    if (!sa.gts) {
+      for (int l = lo; l <= hi; ++l) {
+        const int rel = l >= lstar ? 2 : 3;
+        fma += double(P->up_off[l + 1] - P->up_off[l]) * P->nf * kNV * (sa.om[rel].n + 1);
+      }
+    }
+    P->pevent_flops.push_back(2.0 * fma);
+    P->pevent_sources.push_back(count);
+  }
   return LTS_OK;
 }
 
@@ -786,8 +821,12 @@ lts_status lts_plan_create(const lts_octree* tree, const lts_problem* prob, lts_
     if (!cls) continue;
     P->up_slot[b] = int32_t(P->up_list.size());
     P->up_list.push_back(int32_t(b));
-    P->up_box.push_back(int32_t(prolong_plan_word(cls)));
+    int64_t cost = 0;
+    P->up_box.push_back(int32_t(prolong_plan_word(cls, &cost)));
+    if (P->up_cost.empty()) P->up_cost.push_back(0);
+    P->up_cost.push_back(P->up_cost.back() + cost);
   }
+  if (P->up_cost.empty()) P->up_cost.push_back(0);
   for (int l = 0; l <= 32; ++l) {
     P->up_off[l + 1] = P->up_off[l];
     while (P->up_off[l + 1] < int64_t(P->up_list.size()) && P->octs[P->up_list[P->up_off[l + 1]]].l == l)
@@ -1290,6 +1329,35 @@ lts_status lts_kernel_stats(lts_plan* P, int64_t* launches, double* ms, double* 
     P->prof_launches = 0;
     P->prof_node_stages = 0;
     P->prof_ms = 0.0;
+  }
+  return LTS_OK;
+}
+
+lts_status lts_prolong_stats(lts_plan* P, int64_t* launches, double* ms, double* flops, int64_t* sources,
+                             int reset) {
+  if (!P) return fail(LTS_EINVAL, "lts_prolong_stats: null plan");
+  lts_status dst = check_device_error(P);
+  if (dst != LTS_OK) return dst;
+  for (size_t i = 0; i < P->pevents.size(); ++i) {
+    float t = 0.0f;
+    CK(cudaEventElapsedTime(&t, P->pevents[i].first, P->pevents[i].second), "cudaEventElapsedTime");
+    P->pprof_ms += t;
+    P->pprof_launches++;
+    P->pprof_flops += P->pevent_flops[i];
+    P->pprof_sources += P->pevent_sources[i];
+    cudaEventDestroy(P->pevents[i].first);
+    cudaEventDestroy(P->pevents[i].second);
+  }
+  P->pevents.clear();
+  P->pevent_flops.clear();
+  P->pevent_sources.clear();
+  if (launches) *launches = P->pprof_launches;
+  if (ms) *ms = P->pprof_ms;
+  if (flops) *flops = P->pprof_flops;
+  if (sources) *sources = P->pprof_sources;
+  if (reset) {
+    P->pprof_launches = P->pprof_sources = 0;
+    P->pprof_ms = P->pprof_flops = 0.0;
   }
   return LTS_OK;
 }

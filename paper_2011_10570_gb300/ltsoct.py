@@ -56,7 +56,8 @@ class Stats(C.Structure):
 EXPORTS = ["octree_build", "octree_size", "octree_export", "octree_destroy", "lts_plan_create", "lts_plan_destroy",
            "lts_plan_stats", "lts_set_initial", "lts_set_state", "lts_get_state", "lts_get_stage",
            "lts_run_substeps", "lts_advance", "gts_steps", "gts_advance", "lts_export_o2o", "lts_export_pad_map",
-           "lts_export_node_map", "lts_export_pad_map_static", "lts_set_blocking", "lts_set_profiling", "lts_kernel_stats", "lts_batch_create", "lts_batch_destroy", "lts_batch_run",
+           "lts_export_node_map", "lts_export_pad_map_static", "lts_set_blocking", "lts_set_profiling",
+           "lts_kernel_stats", "lts_prolong_stats", "lts_batch_create", "lts_batch_destroy", "lts_batch_run",
            "lts_batch_set_grid", "lts_batch_stats", "lts_batch_create_slots", "lts_batch_attach",
            "lts_batch_detach", "lts_batch_set_mode", "lts_batch_wait", "lts_batch_probe_barrier", "lts_strerror",
            "lts_last_error"]
@@ -101,6 +102,8 @@ def load(path=None):
         "lts_set_profiling": ([vp, C.c_int], st),
         "lts_kernel_stats": ([vp, C.POINTER(i64), C.POINTER(C.c_double), C.POINTER(C.c_double),
                               C.POINTER(C.c_double), C.POINTER(i64), C.c_int], st),
+        "lts_prolong_stats": ([vp, C.POINTER(i64), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                               C.POINTER(i64), C.c_int], st),
         "lts_batch_create": ([C.POINTER(vp), C.c_int, C.POINTER(vp)], st),
         "lts_batch_destroy": ([vp], None),
         "lts_batch_run": ([vp, C.POINTER(i64), C.c_int], st),
@@ -330,6 +333,13 @@ class Plan:
         _check(_lib.lts_kernel_stats(self.h, C.byref(n), C.byref(ms), C.byref(fl), C.byref(by), C.byref(ns),
                                      1 if reset else 0), "lts_kernel_stats")
         return dict(launches=n.value, ms=ms.value, flops=fl.value, bytes=by.value, node_stages=ns.value)
+
+    def prolong_stats(self, reset=True):
+        n, src = C.c_int64(), C.c_int64()
+        ms, fl = C.c_double(), C.c_double()
+        _check(_lib.lts_prolong_stats(self.h, C.byref(n), C.byref(ms), C.byref(fl), C.byref(src),
+                                      1 if reset else 0), "lts_prolong_stats")
+        return dict(launches=n.value, ms=ms.value, flops=fl.value, sources=src.value)
 
 
 class Batch:

@@ -374,3 +374,28 @@ def test_blocking_is_bit_identical(lt, name, mk):
     for p in (a, b):
         p.gts_steps(2)
     assert np.array_equal(a.get_state(), b.get_state())
+
+
+def test_profiling_counts_stage_and_prolongation_launches(lt):
+    """lts_kernel_stats / lts_prolong_stats: one substep with every level active is 4 RK
+    stages, each one stage launch and one prolongation launch over every coarser source;
+    LTS counts the time-corrected inputs in the prolongation's flops, GTS does not."""
+    w = W.wave_shell(l_min=3, l_max=6, half=4.0, radius=1.5, width=0.2)
+    plan = lt.Plan(lt.Octree(w["spec"]), w["prob"])
+    plan.set_initial(0.0)
+    plan.set_profiling(True)
+    plan.kernel_stats(reset=True)
+    plan.prolong_stats(reset=True)
+    plan.run_substeps(1)
+    ks, ps = plan.kernel_stats(reset=True), plan.prolong_stats(reset=True)
+    st = plan.stats()
+    assert ks["launches"] == 4 and ks["node_stages"] == 4 * st["n_octants"] * 343
+    assert ps["launches"] == 4 and ps["ms"] > 0 and ps["sources"] > 0 and ps["sources"] % 4 == 0
+    assert 0 < ps["sources"] // 4 < st["n_octants"]
+    lts_flops = ps["flops"]
+    plan.gts_steps(1)
+    gs = plan.prolong_stats(reset=True)
+    plan.set_profiling(False)
+    assert gs["launches"] == 4 and gs["sources"] == ps["sources"]
+    # the interpolation alone under GTS: fewer flops than with the time corrections
+    assert 0 < gs["flops"] < lts_flops
