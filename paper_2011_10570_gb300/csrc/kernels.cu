@@ -376,26 +376,26 @@ constexpr unsigned kExterior = 1u << 15;  // exterior flag of the 16-bit codes o
 //                                -> base + q
 // q being the point's tile index (i + 3) + 13 (j + 3) + 169 (k + 3); base is fixed per
 // slot and octant (the plan's slot map, slotmap_kernel).
-__device__ __forceinline__ void tile_ijk(int q, int& i, int& j, int& k) {
-  k = q / 169;
-  const int rem = q - 169 * k;
-  j = rem / 13;
-  i = rem - 13 * j;
-  i -= 3;
-  j -= 3;
-  k -= 3;
-}
-
-// element of point q in the source array of its slot, from the slot's packed base << 2 | kind
-__device__ __forceinline__ long long slot_element(int packed, int kind, int q) {
-  const long long base = packed >> 2;
-  if (kind == kKindCoarser) return base + q;
-  int i, j, k;
-  tile_ijk(q, i, j, k);
-  return base + (kind == kKindFiner ? i + 4 * j + 16 * k : i + 7 * j + 49 * k);
-}
 
 constexpr int kPer = (kNT + kThreads - 1) / kThreads;  // padded points per thread of a stage CTA
+
+// A stage CTA's thread t gathers the points of one column (i, j) of the 13^3 tile: column
+// t mod 169, tile levels 0..6 for t < 169 and 7..12 for 169 <= t < 338 (threads from 338 on
+// take none), so that its point r is q0 + 169 r, at lin7 = l7 + 49 r and lin4 = l4 + 16 r
+// in the source numberings above: one division per thread instead of one per
+// point, and consecutive threads still read consecutive points.
+struct TileColumn {
+  int q0, l7, l4, n;  // first point, its offsets, points taken
+  __device__ __forceinline__ explicit TileColumn(int t) {
+    const int h = t >= 169 ? 1 : 0, c = t - 169 * h;
+    const int j = c / 13, i = c - 13 * j, k0 = 7 * h;
+    q0 = c + 169 * k0;
+    l7 = (i - 3) + 7 * (j - 3) + 49 * (k0 - 3);
+    l4 = (i - 3) + 4 * (j - 3) + 16 * (k0 - 3);
+    n = t >= 338 ? 0 : 7 - h;
+  }
+};
+static_assert(kPer == 7 && kThreads >= 338, "the tile-column assignment covers 13^3 points with 338 threads");
 
 // exterior padded point of octant (anchor me, edge eb): outside the domain
 __device__ __forceinline__ bool exterior_point(int4 me, int eb, int q) {
@@ -782,8 +782,7 @@ __device__ __forceinline__ int stage_item(const StageArgs& A, int it) {
   return A.list ? __ldg(A.list + A.first + it) : A.first + it;
 }
 
-// padding-map bytes of this thread's points of octant b (points tid + r * TPB),
-// four to a register
+// padding-map bytes of this thread's points of octant b (TileColumn), four to a register
 constexpr int kSlw = (kPer + 3) / 4;
 struct Slots {
   unsigned w[kSlw];
@@ -792,12 +791,14 @@ struct Slots {
 
 template <int TPB>
 __device__ __forceinline__ void load_slots(const StageArgs& A, int b, Slots& sl) {
+  static_assert(TPB >= 338, "TileColumn needs 338 threads");
   const unsigned char* __restrict__ pm = A.padmap + (long long)b * kNT;
+  const TileColumn tc(threadIdx.x);
 #pragma unroll
   for (int i = 0; i < kSlw; ++i) sl.w[i] = 0u;
 #pragma unroll
   for (int r = 0; r < kPer; ++r) {
-    const int q = threadIdx.x + r * TPB;
+    const int q = r < tc.n ? tc.q0 + 169 * r : kNT;
     const unsigned v = q < kNT ? unsigned(__ldg(pm + q)) : kSlotNone;
     sl.w[r >> 2] |= v << (8 * (r & 3));
   }
@@ -823,7 +824,7 @@ __device__ __forceinline__ void stage_slots(StageSmem<NF, R, NB>& S, int nb, con
 
 // The slot map of one octant (once per plan): for each slot of its neighbour view, the
 // kind of its leaf (same level, coarser, finer, none) and the base offset of the array
-// the stage kernel reads it from (see slot_element): the stage inputs (same level), the
+// the stage kernel reads it from (the numberings above kPer): the stage inputs (same level), the
 // prolonged inputs of a coarser source (slot up_slot[leaf]), or the injected inputs of a
 // finer source (slot dn_slot[leaf]; a finer leaf that no padding map reads has none).
 __global__ void __launch_bounds__(256) slotmap_kernel(const DevTree T, const int* __restrict__ up_slot,
@@ -923,22 +924,24 @@ __device__ void stage_gather(StageSmem<NF, R, NB>& S, int nb, const StageArgs& A
   const R* st_in = A.stage == 0 ? state_array<R>(u0, us0) : static_cast<const R*>(A.Uin);
   const R* up_all = static_cast<const R*>(A.up);
   const R* inj_all = static_cast<const R*>(A.inj);
+  const TileColumn tc(threadIdx.x);
 #pragma unroll
   for (int r = 0; r < kPer; ++r) {
-    const int q = threadIdx.x + r * TPB;
-    if (q >= kNT) break;
+    if (r >= tc.n) break;
+    const int q = tc.q0 + 169 * r;
     const int packed = S.slot[nb][sl[r]];
     const int kind = packed & 3;
+    const long long base = packed >> 2;  // + q, lin7 or lin4 by kind
     if (kind == kKindCoarser) {
-      const R* up = up_all + slot_element(packed, kind, q);
+      const R* up = up_all + (base + q);
 #pragma unroll
       for (int f = 0; f < NF; ++f) async_copy(&S.T[nb][f][q], up + f * kNT);
     } else if (kind == kKindSame) {
-      const R* src = st_in + slot_element(packed, kind, q);
+      const R* src = st_in + (base + tc.l7 + 49 * r);
 #pragma unroll
       for (int f = 0; f < NF; ++f) async_copy(&S.T[nb][f][q], src + f * A.fstride);
     } else if (kind == kKindFiner) {
-      const R* src = inj_all + slot_element(packed, kind, q);
+      const R* src = inj_all + (base + tc.l4 + 16 * r);
 #pragma unroll
       for (int f = 0; f < NF; ++f) async_copy(&S.T[nb][f][q], src + f * 64);
     } else {
