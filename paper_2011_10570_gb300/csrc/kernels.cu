@@ -1512,6 +1512,8 @@ struct ProlongSmem {
   R E[3][4];              // symmetric-part weights of the mirrored pairs (1, 11), (3, 9), (5, 7)
   R O[3][3];              // antisymmetric-part weights
   R W[6][7];              // Lagrange weights of the odd positions 1, 3, ..., 11 (row k >> 1)
+  int Ec[3][4];           // integer pair weights of the exact FP64 lines (interp_line_exact)
+  int Oc[3][3];
 };
 
 
@@ -1530,6 +1532,115 @@ __device__ __forceinline__ int half_class(int r) { return r <= 3 ? 0 : (r >= 9 ?
 __device__ __forceinline__ int class_lo(unsigned m) { return (m & 1u) ? 0 : ((m & 2u) ? 4 : 9); }
 __device__ __forceinline__ int class_hi(unsigned m) { return (m & 4u) ? 12 : ((m & 2u) ? 8 : 3); }
 
+// ---------------------------------------------------------------------------
+// FP64 prolongation lines by exact integer sums.  With D = 46080 = 2^6 x 720 every Lagrange
+// weight of the 7 -> 13 interpolation is an integer over D (c_rj = D W_rj; at odd r,
+// c_rj = C(6, j) (-1)^(6 - j) prod_{m != j} (r - 2m)), and sum_j |c_rj| <= 196,470 < 2^17.6.
+// A line's 7 values are put on a grid 8 bits below their largest biased exponent E
+// (x = floor(M 2^(e - E + 8)), |x| < 2^61: exact for the inputs within 2^8 of the largest,
+// each within 2^-60 of the largest), a mirrored pair of odd positions is formed exactly as
+// (E' +- O') / 2 from the sums and differences of mirrored values (products of 32-bit halves
+// on the FMA pipe, mad.wide; sums below 2^49.4 per half), kept as floor(. / 2^18) < 2^62.3
+// and rounded to FP64 with the scale 2^(E - 1065) / (2 D): within a unit of the last place of
+// the line's largest weighted term, as the floating-point evaluation, with two FP64
+// operations per odd position instead of 5.5.
+// Even positions are copies.  Lines whose largest value lies outside [2^-968, 2^876) (other
+// than all zero), or is an infinity or NaN, take the floating-point evaluation.
+// ---------------------------------------------------------------------------
+
+// x = M 2^(e - 1075) exactly: (M, e) = (0, 0) for +-0, (+-fraction, 1) for subnormal numbers,
+// (+-(2^52 + fraction), biased exponent) for normal ones; infinities and NaNs (their bits,
+// 2047)
+__device__ __forceinline__ long long fix_split(double x, unsigned& e) {
+  const unsigned hi = static_cast<unsigned>(__double2hiint(x));
+  const unsigned lo = static_cast<unsigned>(__double2loint(x));
+  const unsigned eb = (hi >> 20) & 0x7ffu;
+  const unsigned fh = hi & 0xfffffu;
+  if (eb == 0x7ffu) {
+    e = 0x7ffu;
+    return __double_as_longlong(x);
+  }
+  e = eb != 0u ? eb : ((fh | lo) != 0u ? 1u : 0u);
+  const long long m =
+      static_cast<long long>((static_cast<unsigned long long>(fh | (eb != 0u ? 0x100000u : 0u)) << 32) | lo);
+  return static_cast<int>(hi) < 0 ? -m : m;
+}
+
+// the exponent fix_split gives x
+__device__ __forceinline__ unsigned fix_exp_of(double x) {
+  const unsigned hi = static_cast<unsigned>(__double2hiint(x));
+  const unsigned eb = (hi >> 20) & 0x7ffu;
+  if (eb != 0u) return eb;
+  return ((hi & 0xfffffu) | static_cast<unsigned>(__double2loint(x))) != 0u ? 1u : 0u;
+}
+
+// floor(m / 2^sh); amounts above 64 clamp to 64 (0 or -1)
+__device__ __forceinline__ long long fix_shr(long long m, unsigned sh) {
+  long long r;
+  asm("shr.s64 %0, %1, %2;" : "=l"(r) : "l"(m), "r"(sh));
+  return r;
+}
+
+// a * b + c, 32 x 32 -> 64 bits (one FMA-pipe instruction)
+__device__ __forceinline__ long long mad_wide(int a, int b, long long c) {
+  long long d;
+  asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+  return d;
+}
+
+// floor((h 2^31 + l) / 2^k), 1 <= k <= 31
+__device__ __forceinline__ long long hl_shift(long long h, long long l, int k) { return (h << (31 - k)) + (l >> k); }
+
+// the halves of |v| < 2^62: v = h 2^31 + l, 0 <= l < 2^31
+__device__ __forceinline__ int fix_hi(long long v) { return static_cast<int>(v >> 31); }
+__device__ __forceinline__ int fix_lo(long long v) { return static_cast<int>(v & 0x7fffffffll); }
+
+// One line of the interpolation as above: the 7 node values v to the half-node positions
+// r in [r0, r0 + n) whose class is in cls; put(r, value).  Ec and Oc are the integer pair
+// weights (sums and differences of the pair's weights over D, Ec_3 = 2 c_k3).  False, with
+// nothing written, for a line out of range.
+template <typename Put>
+__device__ __forceinline__ bool interp_line_exact(const double (&v)[7], int r0, int n, unsigned cls,
+                                                  const int (*Ec)[4], const int (*Oc)[3], Put put) {
+  auto needed = [&](int r) { return r >= r0 && r < r0 + n && ((cls >> half_class(r)) & 1u); };
+  unsigned em = fix_exp_of(v[0]);
+#pragma unroll
+  for (int j = 1; j < 7; ++j) em = max(em, fix_exp_of(v[j]));
+  if (!(em == 0u || (em >= 55u && em <= 1900u))) return false;
+#pragma unroll
+  for (int r = 0; r <= 12; r += 2)
+    if (needed(r)) put(r, v[r >> 1]);
+  long long x[7];
+#pragma unroll
+  for (int j = 0; j < 7; ++j) {
+    unsigned e;
+    const long long m = fix_split(v[j], e);
+    x[j] = fix_shr(m * 256, em - e);
+  }
+  const long long s[3] = {x[0] + x[6], x[1] + x[5], x[2] + x[4]};
+  const long long d[3] = {x[0] - x[6], x[1] - x[5], x[2] - x[4]};
+  // 2^(18 - 8 + E - 1075) / (2 D): a power of two times the rounded 1 / 92160 (exact product)
+  const double scale = __hiloint2double((static_cast<int>(em == 0u ? 55u : em) - 42) << 20, 0) * (1.0 / 92160.0);
+#pragma unroll
+  for (int pr = 0; pr < 3; ++pr) {
+    const int kk = 2 * pr + 1;
+    const bool nk = needed(kk), nm = needed(12 - kk);
+    if (!(nk || nm)) continue;
+    long long eh = mad_wide(Ec[pr][3], fix_hi(x[3]), 0), el = mad_wide(Ec[pr][3], fix_lo(x[3]), 0);
+    long long oh = 0, ol = 0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      eh = mad_wide(Ec[pr][j], fix_hi(s[j]), eh);
+      el = mad_wide(Ec[pr][j], fix_lo(s[j]), el);
+      oh = mad_wide(Oc[pr][j], fix_hi(d[j]), oh);
+      ol = mad_wide(Oc[pr][j], fix_lo(d[j]), ol);
+    }
+    if (nk) put(kk, __ll2double_rn(hl_shift(eh + oh, el + ol, 18)) * scale);
+    if (nm) put(12 - kk, __ll2double_rn(hl_shift(eh - oh, el - ol, 18)) * scale);
+  }
+  return true;
+}
+
 // One line of the interpolation: the 7 node values v of a line to the half-node
 // positions r in [r0, r0 + n) whose class is in the 3-bit set cls; put(r, value).
 // Even positions are nodes (copies).  Odd positions come in mirrored pairs (k, 12 - k):
@@ -1543,7 +1654,11 @@ __device__ __forceinline__ int class_hi(unsigned m) { return (m & 4u) ? 12 : ((m
 // line costs 33 operations instead of 42, a one-sided face slab 14 instead of 22.
 template <typename R, typename Put>
 __device__ __forceinline__ void interp_line(const R (&v)[7], int r0, int n, unsigned cls, unsigned all,
-                                            const R (*E)[4], const R (*O)[3], const R (*W)[7], Put put) {
+                                            const R (*E)[4], const R (*O)[3], const R (*W)[7], const int (*Ec)[4],
+                                            const int (*Oc)[3], Put put) {
+  if constexpr (sizeof(R) == sizeof(double)) {
+    if (interp_line_exact(v, r0, n, cls, Ec, Oc, put)) return;
+  }
   auto in_set = [&](int r, unsigned set) { return r >= r0 && r < r0 + n && ((set >> half_class(r)) & 1u); };
   auto needed = [&](int r) { return in_set(r, cls); };
 #pragma unroll
@@ -1635,6 +1750,14 @@ __device__ void prolong_octant(ProlongSmem<NF, R>& S, const ProlongArgs& A, cons
   } else if (tid >= 32 && tid < 32 + 42) {  // the odd rows for the direct evaluation
     const int q = tid - 32;
     S.W[q / 7][q % 7] = R(c_W[2 * (q / 7) + 1][q % 7]);
+  } else if (tid >= 96 && tid < 96 + 21) {  // integer pair weights (46080 W is an integer)
+    const int pr = (tid - 96) / 7, q = (tid - 96) % 7, k = 2 * pr + 1;
+    if (q < 4) {
+      S.Ec[pr][q] = __double2int_rn(46080.0 * (q < 3 ? c_W[k][q] + c_W[k][6 - q] : 2.0 * c_W[k][3]));
+    } else {
+      const int j = q - 4;
+      S.Oc[pr][j] = __double2int_rn(46080.0 * (c_W[k][j] - c_W[k][6 - j]));
+    }
   }
   const int cur = (A.cur_mask >> lb) & 1;
   const R* Uin = static_cast<const R*>(A.Uin);
@@ -1661,7 +1784,7 @@ __device__ void prolong_octant(ProlongSmem<NF, R>& S, const ProlongArgs& A, cons
 #pragma unroll
     for (int q = 0; q < 7; ++q) v[q] = S.V[f][7 * bc + q];
     R* x1 = S.X1[f] + bc;
-    interp_line<R>(v, a0, na, ma, ma, S.E, S.O, S.W, [&](int r, R val) { x1[r * 49] = val; });
+    interp_line<R>(v, a0, na, ma, ma, S.E, S.O, S.W, S.Ec, S.Oc, [&](int r, R val) { x1[r * 49] = val; });
   }
   __syncthreads();
   // pass 2 (axis b): one thread per line (f, ra, jc), X2[ra][rb][jc]
@@ -1677,7 +1800,7 @@ __device__ void prolong_octant(ProlongSmem<NF, R>& S, const ProlongArgs& A, cons
 #pragma unroll
     for (int q = 0; q < 7; ++q) v[q] = x1[q];
     R* x2 = S.X2[f] + ra * 13 * 7 + jc;
-    interp_line<R>(v, b0, nb, cls, mb, S.E, S.O, S.W, [&](int r, R val) { x2[r * 7] = val; });
+    interp_line<R>(v, b0, nb, cls, mb, S.E, S.O, S.W, S.Ec, S.Oc, [&](int r, R val) { x2[r * 7] = val; });
   }
   __syncthreads();
   // pass 3 (axis c): one thread per line (f, ra, rb), every position of the set written
@@ -1698,7 +1821,7 @@ __device__ void prolong_octant(ProlongSmem<NF, R>& S, const ProlongArgs& A, cons
 #pragma unroll
     for (int q = 0; q < 7; ++q) v[q] = x2[q];
     R* o = out + f * kNT + ra * soa + rb * sob;
-    interp_line<R>(v, c0, nc, cls, mc, S.E, S.O, S.W, [&](int r, R val) { o[r * soc] = val; });
+    interp_line<R>(v, c0, nc, cls, mc, S.E, S.O, S.W, S.Ec, S.Oc, [&](int r, R val) { o[r * soc] = val; });
   }
 }
 
