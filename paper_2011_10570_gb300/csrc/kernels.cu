@@ -980,7 +980,7 @@ __device__ void inject_octant(const InjectArgs& A, const int b, const int slot) 
 }
 
 template <int NF, typename R>
-__global__ void __launch_bounds__(128) inject_kernel(const __grid_constant__ InjectArgs A) {
+__global__ void __launch_bounds__(128, 16) inject_kernel(const __grid_constant__ InjectArgs A) {
   for (int item = blockIdx.x; item < A.count; item += gridDim.x)
     inject_octant<NF, R>(A, __ldg(A.list + item), A.first + item);
 }
