@@ -102,9 +102,13 @@ typedef struct {
   int bc;
   int ic;
   double ic_params[32];
-  int precision;       /* 0: FP64 throughout.  1: mixed -- RK stages, stage inputs, the padded
-                          block and the right-hand side in FP32; the state, the RK update and
-                          the time corrections (eqs. fc_1, fc_2) in FP64 */
+  int precision;       /* 0: FP64 throughout; where the coefficients are integers (the wave
+                          equation's Laplacian and dissipation of chi, the coarse -> fine
+                          interpolation lines) the sums are exact in 64-bit integers and each
+                          result is rounded once to FP64, within the error bound of the FP64
+                          evaluation.  1: mixed -- RK stages, stage inputs, the padded block and
+                          the right-hand side in FP32; the state, the RK update and the time
+                          corrections (eqs. fc_1, fc_2) in FP64 */
   void* stream;        /* cudaStream_t; NULL = default stream */
   void* (*dev_alloc)(size_t bytes, void* ctx);  /* optional device allocator */
   void (*dev_free)(void* ptr, void* ctx);
