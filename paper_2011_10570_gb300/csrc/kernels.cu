@@ -2268,7 +2268,7 @@ __global__ void __launch_bounds__(kThreads, 4) batch_stage_kernel(const __grid_c
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) batch_prolong_kernel(const __grid_constant__ BatchArgs B, int stage) {
+__global__ void __launch_bounds__(256, 4) batch_prolong_kernel(const __grid_constant__ BatchArgs B, int stage) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ ProlongArgs args;
   __shared__ int s_item;
@@ -2293,7 +2293,7 @@ __global__ void __launch_bounds__(256) batch_prolong_kernel(const __grid_constan
 }
 
 template <typename R>
-__global__ void __launch_bounds__(128) batch_inject_kernel(const __grid_constant__ BatchArgs B, int stage) {
+__global__ void __launch_bounds__(128, 16) batch_inject_kernel(const __grid_constant__ BatchArgs B, int stage) {
   __shared__ InjectArgs args;
   __shared__ int s_item;
   const int* pre = B.inj_pre + stage * (kMaxBatch + 1);
