@@ -270,6 +270,7 @@ __device__ __forceinline__ T ld_in(const T* p) {
 template <typename R, bool C = false>
 __device__ __forceinline__ double corrected_value(const double* __restrict__ u, const R* __restrict__ k0,
                                                   long long kstride, const StageTerms& t, double dt) {
+  if (t.n == 0) return ld_in<C>(u);  // no correction (stage 0 of a source in its own step)
   double acc = 0.0;
   for (int q = 0; q < t.n; ++q) acc = fma(t.w[q], to_double(ld_in<C>(k0 + t.j[q] * kstride)), acc);
   return fma(dt, acc, ld_in<C>(u));
