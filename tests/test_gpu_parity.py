@@ -6,7 +6,8 @@
   (Alg. 2) and GTS (Alg. 1), advection and wave, exact and radiative boundaries;
 * LTS == GTS bitwise on a one-level tree (Alg. 2 reduces to Alg. 1);
 * FP64 wave right-hand sides (exact integer stencil sums) on data spanning 10^-300 to
-  10^200, each node within a few units of 2^-52 of its own stencil scale;
+  10^200, each node within a few units of 2^-52 of its own stencil scale; NaN and infinite
+  inputs non-finite at exactly the oracle's nodes;
 * at the full wave configuration (levels 4..9, 154,400 octants): the octree, the
   o2o map, sampled padding maps, and the first two LTS substeps at sampled octants
   (the oracle runs only the dependency cone of the sample).
@@ -227,6 +228,32 @@ def test_fp64_wave_rhs_on_wide_range_data(lt, orc):
     assert err.max() <= 64 * 2.0 ** -52
     # octants of tiny and of huge magnitudes are both present and checked on their own scale
     assert (scale < 1e-280).any() and (scale > 1e180).any()
+
+
+def test_fp64_nonfinite_inputs_propagate(lt, orc):
+    """A NaN or an infinity in the state is never turned into a finite value by the exact
+    integer paths (stencil sums, prolongation lines): nodes whose inputs reach one take the
+    floating-point formula, so the GPU's first RK stage is non-finite at exactly the nodes
+    where the oracle's is."""
+    w = W.wave_shell(l_min=2, l_max=4, half=4.0, radius=1.5, width=0.2)
+    gt, plan, ot, sol = both(lt, orc, w)
+    n = plan.stats()["n_octants"]
+    rng = np.random.default_rng(5)
+    u = rng.standard_normal((2, n, 343))
+    picks = rng.choice(n, size=6, replace=False)
+    for t, b in enumerate(picks):
+        node = 3 + 7 * 3 + 49 * 3 if t % 2 == 0 else int(rng.integers(0, 343))
+        u[t % 2, b, node] = (np.nan, np.inf, -np.inf)[t % 3]
+    plan.set_state(u)
+    sol.set_state(u)
+    plan.run_substeps(1)
+    sol.lts_substeps(1)
+    for j in range(2):
+        kg, ko = plan.get_stage(j), sol.stage(j)
+        fg, fo = np.isfinite(kg), np.isfinite(ko)
+        assert (~fo).any()
+        assert np.array_equal(fg, fo), j
+        assert np.abs(kg[fo] - ko[fo]).max() <= 1e-9 * np.abs(ko[fo]).max()
 
 
 def test_invalid_calls_fail_loudly(lt):
