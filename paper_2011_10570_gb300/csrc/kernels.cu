@@ -604,6 +604,12 @@ __device__ __forceinline__ bool fix_range(unsigned em, const double* T, int c0) 
 template <int SY, int SZ>
 __device__ __forceinline__ bool wave_rhs_exact(const double* Tc, const double* Tp, int c0, double kos,
                                                double inv12h2, double& kchi, double& kphi) {
+  // phi's dissipation first (FP64 pipe), then chi's integer sums
+  const double f0v = Tp[c0];
+  const double F1 = (Tp[c0 - 1] + Tp[c0 + 1]) + (Tp[c0 - SY] + Tp[c0 + SY]) + (Tp[c0 - SZ] + Tp[c0 + SZ]);
+  const double F2 = (Tp[c0 - 2] + Tp[c0 + 2]) + (Tp[c0 - 2 * SY] + Tp[c0 + 2 * SY]) + (Tp[c0 - 2 * SZ] + Tp[c0 + 2 * SZ]);
+  const double F3 = (Tp[c0 - 3] + Tp[c0 + 3]) + (Tp[c0 - 3 * SY] + Tp[c0 + 3 * SY]) + (Tp[c0 - 3 * SZ] + Tp[c0 + 3 * SZ]);
+  const double kop = fma(-60.0, f0v, fma(15.0, F1, fma(-6.0, F2, F3)));
   const unsigned ec = fix_emax<SY, SZ, 3>(Tc, c0);
   if (!fix_range<SY, SZ, 3>(ec, Tc, c0)) return false;
   long long lap = 0, koc = 0;  // inputs all zero: zero sums
@@ -614,11 +620,6 @@ __device__ __forceinline__ bool wave_rhs_exact(const double* Tc, const double* T
     lap = 16 * c1 - c2 - 90 * c;
     koc = fix_ring<SY, SZ>(Tc, c0, 3, ec) - 6 * c2 + 15 * c1 - 60 * c;
   }
-  const double f0v = Tp[c0];
-  const double F1 = (Tp[c0 - 1] + Tp[c0 + 1]) + (Tp[c0 - SY] + Tp[c0 + SY]) + (Tp[c0 - SZ] + Tp[c0 + SZ]);
-  const double F2 = (Tp[c0 - 2] + Tp[c0 + 2]) + (Tp[c0 - 2 * SY] + Tp[c0 + 2 * SY]) + (Tp[c0 - 2 * SZ] + Tp[c0 + 2 * SZ]);
-  const double F3 = (Tp[c0 - 3] + Tp[c0 + 3]) + (Tp[c0 - 3 * SY] + Tp[c0 + 3 * SY]) + (Tp[c0 - 3 * SZ] + Tp[c0 + 3 * SZ]);
-  const double kop = fma(-60.0, f0v, fma(15.0, F1, fma(-6.0, F2, F3)));
   kchi = fma(kos, fix_value(koc, ec), f0v);
   kphi = fma(kos, kop, fix_value(lap, ec) * inv12h2);
   return true;
