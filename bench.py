@@ -31,7 +31,7 @@ UNIT = "node-updates/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x flops/FMA x max clock
 # DRAM bytes (read + write) per node-stage of stage_kernel<2, double> / <2, float>, from ncu
 # captures of one stage launch on the levels 4..8 wave case; None whenever the kernel changes
-STAGE_DRAM_BYTES_PER_NODE_STAGE = 88.1
+STAGE_DRAM_BYTES_PER_NODE_STAGE = 88.3
 STAGE_DRAM_BYTES_PER_NODE_STAGE_MIXED = 48.3
 # FP64-pipe operations per node-stage of stage_kernel<2, double> on the wave equation:
 # phi's dissipation 18 (15 pair-sum additions, 3 FMAs), the Laplacian's scaling and the
