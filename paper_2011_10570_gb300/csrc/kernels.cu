@@ -1591,7 +1591,9 @@ __device__ __forceinline__ long long mad_wide(int a, int b, long long c) {
 }
 
 // floor((h 2^31 + l) / 2^k), 1 <= k <= 31
-__device__ __forceinline__ long long hl_shift(long long h, long long l, int k) { return (h << (31 - k)) + (l >> k); }
+__device__ __forceinline__ long long hl_shift(long long h, long long l, int k) {
+  return h * (1ll << (31 - k)) + (l >> k);  // (a product: h may be negative)
+}
 
 // the halves of |v| < 2^62: v = h 2^31 + l, 0 <= l < 2^31
 __device__ __forceinline__ int fix_hi(long long v) { return static_cast<int>(v >> 31); }
