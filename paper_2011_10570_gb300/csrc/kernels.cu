@@ -666,16 +666,6 @@ __device__ __forceinline__ void rhs_node(const R* const* Tt, int c0, const Stage
   }
 }
 
-// a node of the state as a stage input: FP64 u, or in mixed precision its FP32 copy
-template <typename R>
-__device__ __forceinline__ R state_in(const double* __restrict__ u, const float* __restrict__ us, long long o) {
-  if constexpr (sizeof(R) == sizeof(double)) {
-    return __ldg(u + o);
-  } else {
-    return __ldg(us + o);
-  }
-}
-
 // the state as stage input array: FP64 u, or in mixed precision its FP32 copy
 template <typename R>
 __device__ __forceinline__ const R* state_array(const double* u, const float* us) {
