@@ -1122,7 +1122,8 @@ __device__ void stage_octant(StageSmem<NF, R, 1>& S, const StageArgs& A, const i
 // buffers, the next octant's gathers in flight during the current one's right-hand sides
 // (FP64 25%: 3 CTAs per SM fit; mixed 27%: the slot table's loads stall the whole CTA);
 // mixed precision with two octants per CTA, their maps, slot tables and gathers in
-// flight together (12%: the second octant's slot registers spill at 32 registers).
+// flight together (12%: the second octant's slot registers spill at 32 registers); FP64
+// at 4 CTAs per SM with 40 registers, its spills nearly gone (6%).
 template <typename R> struct StageShape {
   static constexpr int kTPB = kThreads;
   static constexpr int kMinBlocks = 5;
